@@ -1,0 +1,365 @@
+"""Benchmark: lattice updates per second of the binary capillary, 16384 x 256 (H = 200).
+
+One "step" is one time step of the whole LB update (stencils, equilibria,
+collision, streaming, walls) over the 16384 x 256 binary capillary, with the
+FP64 reductions (mass, sum of phi, l(t)) every 100 steps, as in a filling run.
+The state (2 x 302 MB in FP32) is larger than L2, so no flush is needed between
+steps.  MLUPS counts fluid nodes only (solid wall rows are not updated).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica of the capillary (one capillary
+does not shard without a halo exchange; the value is the sum over ranks and the
+time is the maximum over ranks).  --impl reference times the FP64 CPU oracle, as
+it stands, on a bounded sample of the same workload (one time step of the
+1024 x 64 crop per bench step) on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "MLUPS (fluid-node lattice updates per second), binary capillary 16384x256"
+RED_EVERY = 100
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lb_device.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_0911_0459_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d[kind]
+        if e.get("kernel_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(sample_steps=300):
+    """The FP64 oracle on the 1024 x 64 crop of the same capillary (single thread)."""
+    import oracle
+    cap = W.config_binary_crop_1024x64()
+    o = oracle.Oracle(cap).init_default()
+    o.step(2)
+    t0 = time.perf_counter()
+    o.step(sample_steps)
+    dt = time.perf_counter() - t0
+    fluid = int((o.node_kinds() < 2).sum())
+    return {"value": fluid * sample_steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_steps} steps of the 1024x64 crop (H=50, same parameters), FP64, 1 thread",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    cap = W.config_binary_crop_1024x64()
+    o = oracle.Oracle(cap).init_default()
+    fluid = int((o.node_kinds() < 2).sum())
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = fluid * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "binary_16384x256 sampled as its 1024x64 crop (H=50, ratio 50, 45 deg); "
+                                   "one time step of the crop per bench step"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of the 1024x64 crop, FP64, 1 thread"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(lat, torch, K, red_every):
+    """K steps with reductions every red_every steps; returns (total_ms, step_ms, launches)."""
+    s = lat.stream
+    evs = []
+    launches = 0
+    done = 0
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(s)
+    while done < K:
+        n = min(red_every, K - done)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        lat.step(n)
+        b.record(s)
+        evs.append((a, b))
+        launches += n
+        done += n
+        lat.filled_length()
+        launches += 2
+    t_end.record(s)
+    torch.cuda.synchronize()
+    total = t_start.elapsed_time(t_end)
+    step_ms = sum(a.elapsed_time(b) for a, b in evs)
+    return total, step_ms, launches
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default=None, help="BX,YC: fixed step-kernel tile instead of autotuning")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev"])
+    ap.add_argument("--profile", action="store_true",
+                    help="only the large capillary: warm-up then --steps steps (for ncu captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, Lattice
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cap = W.config_binary_16384x256(STORAGE_F32 if args.storage == "f32" else STORAGE_F16DEV)
+    lat = Lattice.from_workload(cap)
+    if args.tile:
+        tx, ty = (int(v) for v in args.tile.split(","))
+        lat.set_tile(tx, ty)
+    else:
+        tx, ty, us_tuned = lat.autotune()
+    fluid = lat.fluid_nodes
+    if args.profile:
+        lat.step(args.warmup)
+        lat.step(args.steps)
+        lat.filled_length()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "steps": args.steps, "tile": [tx, ty]}), flush=True)
+        lat.close()
+        return
+    lat.step(args.warmup)
+    lat.filled_length()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        total_ms, step_ms, launches = timed_steps(lat, torch, args.steps, RED_EVERY)
+    torch.cuda.synchronize()
+    barrier()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = world * fluid * args.steps / (total_max * 1e-3) / 1e6
+    l_end = lat.filled_length()
+
+    # roofline of the step kernel: algorithmic bytes = fluid nodes x 18 planes x 4 B x (read + write)
+    bytes_per_lu = 144.0
+    per_launch_ms = step_ms / args.steps
+    achieved = fluid * bytes_per_lu / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = ncu_traffic("binary_f32")
+
+    # end to end through the C ABI with pinned host buffers: upload fields, K steps, download fields
+    shape = (cap.ny, cap.nx)
+    pinned = [torch.empty(shape, dtype=torch.float64, pin_memory=True) for _ in range(8)]
+    rho0, ux0, uy0, phi0 = W.initial_fields(cap)
+    for dst, src in zip(pinned[:4], (rho0, ux0, uy0, phi0)):
+        dst.numpy()[:] = src
+    host_in = [p.numpy() for p in pinned[:4]]
+    host_out = [p.numpy() for p in pinned[4:]]
+    from paper_0911_0459_gb300 import lb as lbmod
+    import ctypes
+    L = lbmod.library()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    lat.init_fields(*host_in)
+    lat.step(args.steps)
+    st = L.lb_fields(lat.h, *[a.ctypes.data_as(ctypes.c_void_p) for a in host_out])
+    assert st == 0
+    e2e_s = time.perf_counter() - t0
+    tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_s = float(tt.item())
+    e2e = {"value": world * fluid * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 4 * 8 * cap.nx * cap.ny / args.steps,
+           "d2h_bytes_per_step": 4 * 8 * cap.nx * cap.ny / args.steps,
+           "what": "lb_init_fields(host) + lb_step(K) + lb_fields(host), pinned buffers"}
+
+    # secondary numbers on the same GPU (not the headline)
+    secondary = {}
+    try:
+        c16 = W.config_binary_16384x256(STORAGE_F16DEV)
+        l16 = Lattice.from_workload(c16)
+        l16.autotune()
+        l16.step(8)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(l16.stream)
+        l16.step(512)
+        b.record(l16.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 512
+        secondary["fp16dev_16384x256"] = {"MLUPS": l16.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                                          "bytes_per_lu": 76, "GBps": l16.fluid_nodes * 76 / (ms * 1e-3) / 1e9}
+        l16.close()
+        c1 = W.config_lg_256x32()
+        l1 = Lattice.from_workload(c1)
+        l1.autotune()
+        l1.step(64)
+        torch.cuda.synchronize()
+        a.record(l1.stream)
+        l1.step(1984)
+        b.record(l1.stream)
+        torch.cuda.synchronize()
+        secondary["lg_256x32_fp64_us_per_step"] = 1e3 * a.elapsed_time(b) / 1984
+        l1.close()
+    except Exception as ex:  # secondary numbers never block the headline line
+        secondary["error"] = repr(ex)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "binary_16384x256: H=200 tube over x in [512, 16384), gas 128 cols, "
+                                   "viscosity ratio 50 (0.83/0.0166), theta 45 deg, FP32 storage",
+                       "nodes": cap.nx * cap.ny, "fluid_nodes": fluid, "tile": [tx, ty],
+                       "reductions_every": RED_EVERY,
+                       "l2": "no flush: state 2 x 302 MB > 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "step_kernel<binary, FP32>", "bytes_per_lu": bytes_per_lu,
+                         "peak_source": f"{peak_kind} copy bandwidth",
+                         "us_per_launch": 1e3 * per_launch_ms},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "l_end": l_end["l"],
+            "secondary": secondary,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

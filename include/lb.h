@@ -1,0 +1,176 @@
+/*
+ * lb.h -- C ABI of the GB300 lattice Boltzmann library for capillary filling.
+ *
+ * The library advances the D2Q9 free-energy multiple-relaxation-time lattice
+ * Boltzmann scheme of Pooley, Kusumaatmaja & Yeomans, "Modelling capillary
+ * filling dynamics using lattice Boltzmann simulations", for two models:
+ *   - the van der Waals liquid-gas model (one distribution f; Sec. 2, Eq. (pt),
+ *     p0 = rho T / (1 - b rho) - a rho^2), and
+ *   - the binary model (f for the density, g for the order parameter phi;
+ *     Sec. 3.1, Eq. (chempot), Eq. (latbolt2), viscosity nu(phi) of Eq. (nu)),
+ * with the evolution of Eq. (latbolt), the matrices M and S and the equilibria
+ * of Appendix A, the stencils of Eq. (best), bounce-back walls whose boundary
+ * nodes are set to rest after streaming, and a prescribed wall gradient
+ * d_n rho|_b or d_n phi|_b that sets the contact angle (Sec. 2.2).
+ *
+ * Conventions for every call:
+ *   - Every function returns lb_status (or nothing); no C++ exception crosses
+ *     this boundary.  On failure lb_last_error() describes the cause.
+ *   - Host arrays are row-major (ny, nx) doubles, x contiguous; population
+ *     arrays are plane-major (9, ny, nx).  The caller owns them; the library
+ *     only reads or writes them during the call.
+ *   - Device memory belongs to the context.  It is obtained through the
+ *     optional lb_alloc callbacks, or cudaMalloc when none are given, and is
+ *     released by lb_destroy.
+ *   - Work is issued on the stream passed to lb_create (a cudaStream_t, NULL for
+ *     the default stream).  lb_step returns without waiting; every call that
+ *     returns data to the host waits for the stream.
+ *   - After LB_ERR_NONFINITE or LB_ERR_TIMEOUT the context accepts only
+ *     lb_fields, lb_get_populations, lb_last_error and lb_destroy.
+ *
+ * Geometry (Sec. 2.2, Fig. 1b): the grid is periodic in x and y.  The tube
+ * occupies the columns [tube_x0, tube_x0 + tube_len) (mod nx); inside them the
+ * rows [tube_y0, tube_y0 + tube_h) (mod ny) are fluid and the other rows are
+ * solid, so one block of solid forms both walls through the y-wrap.  Columns
+ * outside the tube are reservoirs, periodic in y.  tube_len = 0: no solid at
+ * all; tube_len = nx: walls along the whole length.  Valid geometries have
+ * tube_h >= 2, a solid thickness ny - tube_h >= 1 and, when 0 < tube_len < nx,
+ * at least 2 reservoir columns.
+ */
+#ifndef LB_GB300_H
+#define LB_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+  LB_OK = 0,
+  LB_ERR_ARG = 1,       /* invalid argument; nothing was changed */
+  LB_ERR_CUDA = 2,      /* a CUDA call failed; see lb_last_error */
+  LB_ERR_NONFINITE = 3, /* a reduction found a NaN or Inf in the state */
+  LB_ERR_TIMEOUT = 4,   /* a device-side wait gave up (batched persistent kernel) */
+  LB_ERR_STATE = 5,     /* call not allowed in the context's current state */
+  LB_ERR_NOMEM = 6      /* device allocation failed */
+} lb_status;
+
+typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
+
+/* Storage of the distributions.  Arithmetic is FP64 for LB_STORAGE_F64 and FP32
+ * otherwise.  LB_STORAGE_F16DEV keeps f_i - w_i rho0 (w = 4/9, 1/9, 1/36,
+ * rho0 = 1) and g_1..g_8 in FP16 and g_0 in FP32. */
+typedef enum { LB_STORAGE_F64 = 0, LB_STORAGE_F32 = 1, LB_STORAGE_F16DEV = 2 } lb_storage;
+
+typedef struct {
+  int nx, ny;
+} lb_grid;
+
+typedef struct {
+  int tube_x0, tube_len; /* tube columns [tube_x0, tube_x0 + tube_len) mod nx */
+  int tube_y0, tube_h;   /* fluid band [tube_y0, tube_y0 + tube_h) mod ny inside the tube */
+  int gas_cols;          /* default initial state: gas in x < gas_cols (Sec. 2.2 reservoirs) */
+  double wall_grad;      /* d_n rho|_b (liquid-gas) or d_n phi|_b (binary), n = inward normal */
+} lb_walls;
+
+typedef struct {
+  int model;               /* lb_model */
+  int storage;             /* lb_storage */
+  double kappa, a, b, T;   /* liquid-gas: kappa = 0.02, a = 9/49, b = 2/21, T = 0.56 (Sec. 2) */
+  double A, M;             /* binary: A (= kappa = 0.04, Sec. 3.1) and mobility M (Eq. diff) */
+  double nu_l, nu_g;       /* binary: bulk kinematic viscosities of Eq. (nu) */
+  double nu;               /* liquid-gas kinematic viscosity; omega = 2/(6 nu + 1) (App. A) */
+  double lambda_scale;     /* lambda of Eq. (equilibrium) = lambda_scale * local nu */
+  double rho_l, rho_g;     /* liquid-gas: densities of the default initial state and of the
+                              l(t) threshold (rho_l + rho_g)/2 */
+  int l0;                  /* default initial state: liquid in [gas_cols, tube_x0 + l0) */
+} lb_params;
+
+/* Optional device allocator.  malloc_fn returns device memory of at least bytes
+ * bytes usable on stream, or NULL; free_fn releases it. */
+typedef struct {
+  void *(*malloc_fn)(size_t bytes, void *stream, void *user);
+  void (*free_fn)(void *ptr, void *stream, void *user);
+  void *user;
+} lb_alloc;
+
+/* Create a lattice and set the default initial state (Sec. 2.2: u = 0, liquid
+ * in [gas_cols, tube_x0 + l0), gas elsewhere, tanh profiles of width 2 for the
+ * liquid-gas model and sqrt(2) for phi, f = f^eq and g = g^eq of Appendix A).
+ * stream is a cudaStream_t or NULL.  *out is set only on LB_OK. */
+lb_status lb_create(const lb_grid *grid, const lb_walls *walls, const lb_params *params,
+                    const lb_alloc *alloc, void *stream, lb_ctx **out);
+
+/* Release every device buffer and the context.  NULL is ignored. */
+void lb_destroy(lb_ctx *ctx);
+
+/* Reset the state to equilibrium with the given macroscopic host fields
+ * ((ny, nx) doubles; phi may be NULL for the liquid-gas model and is required
+ * for the binary model).  Values at solid nodes are ignored.  Sets time to 0. */
+lb_status lb_init_fields(lb_ctx *ctx, const double *rho, const double *ux, const double *uy,
+                         const double *phi);
+
+/* Advance n >= 0 time steps of Eq. (latbolt) (and Eq. (latbolt2)): stencils,
+ * equilibria, collision, streaming with bounce-back, rest of boundary nodes.
+ * Asynchronous on the context's stream. */
+lb_status lb_step(lb_ctx *ctx, long n);
+
+/* Copy the macroscopic fields rho, u = j/rho and phi to host arrays ((ny, nx)
+ * doubles, any may be NULL; phi is 0 for the liquid-gas model).  Boundary nodes
+ * report u after the rest rule.  Solid nodes report 0.  Waits for the stream. */
+lb_status lb_fields(lb_ctx *ctx, double *rho, double *ux, double *uy, double *phi);
+
+/* FP64 reductions (Sec. 1 defines l): l_centre = distance from tube_x0 to the
+ * first sign change of phi (binary) or rho - (rho_l + rho_g)/2 (liquid-gas)
+ * along the tube's middle row (mean of the two middle rows for even tube_h),
+ * linearly interpolated, 0 if the inlet is already gas and tube_len if there is
+ * no change; l_vol = sum over tube nodes of the liquid fraction / tube_h;
+ * mass = sum of rho and phi_sum = sum of phi over fluid nodes.  Any pointer may
+ * be NULL.  Returns LB_ERR_NONFINITE (and poisons the context) if mass or
+ * phi_sum is not finite.  Waits for the stream. */
+lb_status lb_filled_length(lb_ctx *ctx, double *l_centre, double *l_vol, double *mass,
+                           double *phi_sum);
+
+/* Copy the populations to host arrays (9, ny, nx) of doubles (g may be NULL;
+ * it is left untouched for the liquid-gas model).  rested != 0 applies the
+ * boundary-node rest rule of Sec. 2.2 to f on the way out; rested = 0 returns
+ * the stored state exactly (the library applies that rule when it next reads a
+ * boundary node).  Waits for the stream. */
+lb_status lb_get_populations(lb_ctx *ctx, double *f, double *g, int rested);
+
+/* Replace the populations (plane-major host doubles, rounded to the storage
+ * type).  g is required for the binary model.  Solid nodes are ignored. */
+lb_status lb_set_populations(lb_ctx *ctx, const double *f, const double *g);
+
+/* Wait for all work issued on the context's stream. */
+lb_status lb_sync(lb_ctx *ctx);
+
+/* Time steps taken since the last initialisation. */
+long lb_time(const lb_ctx *ctx);
+
+/* Fluid (non-solid) node count. */
+long lb_fluid_nodes(const lb_ctx *ctx);
+
+/* Choose the tile of the step kernel: tile_x threads per block along x (64,
+ * 128 or 256) and tile_y rows per block (1 .. ny).  Invalidates the captured
+ * step graph. */
+lb_status lb_set_tile(lb_ctx *ctx, int tile_x, int tile_y);
+lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
+
+/* Time each candidate tile on this lattice (the state is saved and restored)
+ * and keep the fastest.  Returns the choice and its time per step in
+ * microseconds.  Waits for the stream. */
+lb_status lb_autotune(lb_ctx *ctx, int *tile_x, int *tile_y, double *us_per_step);
+
+/* Description of the last error on ctx (or of the last failed lb_create when
+ * ctx is NULL).  Never NULL. */
+const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_GB300_H */

@@ -34,7 +34,8 @@
  *             in the opposite direction; afterwards every boundary node (a fluid
  *             node with at least one solid node among its 8 neighbours) has its
  *             momentum removed with f_i -= w_i e_i . j (density unchanged).  The
- *             g populations get the bounce-back only.
+ *             g populations get the bounce-back only.  The initial state built
+ *             from macroscopic fields obeys the same rest rule at boundary nodes.
  *   wetting : in the stencils a solid neighbour s = r + d of a fluid node r takes
  *             a ghost value: d = (dx, 0) -> v(r - (dx, 0)) (neutral mirror);
  *             d = (0, dy) -> v(r - (0, dy)) - 2h; diagonal -> v(r + (dx, -dy)) - 2h
@@ -473,6 +474,7 @@ int orc_init_fields(void *h, const double *rho, const double *ux, const double *
     double geq[9] = {0};
     node_equilibria(s, k, fk, geq, &om);
     memcpy(gk, geq, sizeof geq);
+    if (s->bnd[k]) rest_node(fk); /* the initial state obeys the wall rule too */
   }
   s->t = 0;
   return ORC_OK;

@@ -1,0 +1,254 @@
+// Auxiliary kernels: equilibrium initialisation from macroscopic fields, field
+// and population export/import, and the FP64 reductions behind
+// lb_filled_length (mass, sum of phi, filled volume, meniscus position l).
+#pragma once
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+// Gather the 3x3 neighbourhood of a double field around fluid node (x, y).
+template <typename A>
+__device__ __forceinline__ void gather_field(const Geom& G, const double* __restrict__ v, int x, int y, A out[3][3]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int xx = wrapi(x + i - 1, G.nx), yy = wrapi(y + j - 1, G.ny);
+      out[j][i] = is_solid(G, xx, yy) ? A(0) : A(v[(size_t)yy * G.nx + xx]);
+    }
+}
+
+// f = f^eq and g = g^eq of the given fields (stencils with the wall ghosts).
+template <int MODEL, class S>
+__global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const double* __restrict__ rho_in,
+                            const double* __restrict__ ux_in, const double* __restrict__ uy_in,
+                            const double* __restrict__ phi_in) {
+  using A = typename S::A;
+  constexpr bool BIN = MODEL == MODEL_BINARY;
+  const size_t N = (size_t)G.nx * G.ny;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    if (is_solid(G, x, y)) {
+      for (int i = 0; i < 9; ++i) {
+        S::sf(B.f, N, n, i, A(0));
+        if (BIN) S::sg(B.g, B.g0, N, n, i, A(0));
+      }
+      continue;
+    }
+    bool sol[3][3], bnd;
+    neighbour_solids(G, x, y, sol, bnd);
+    A vr[3][3], vp[3][3];
+    gather_field(G, rho_in, x, y, vr);
+    if (BIN) gather_field(G, phi_in, x, y, vp);
+    if (bnd) {
+      apply_ghosts(vr, sol, BIN ? A(0) : P.h);
+      if (BIN) apply_ghosts(vp, sol, P.h);
+    }
+    A rdx, rdy, rlap;
+    stencil3(vr, rdx, rdy, rlap);
+    const A rho = vr[1][1], ux = A(ux_in[n]), uy = A(uy_in[n]);
+    const A jx = rho * ux, jy = rho * uy;
+    A fe[9], ge[9];
+    if (BIN) {
+      A pdx, pdy, plap;
+      stencil3(vp, pdx, pdy, plap);
+      const A phi = vp[1][1], phi2 = phi * phi;
+      const A p0 = rho * A(1.0 / 3.0) + P.Acoef * (A(-0.5) * phi2 + A(0.75) * phi2 * phi2);
+      const A mu = P.Acoef * (phi2 * phi - phi) - P.kappa * plap;
+      const A nu = local_nu_binary(P, phi);
+      feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * phi * plap, P.kappa, pdx, pdy, rdx, rdy, P.lambda_scale * nu, fe);
+      geq9<A>(phi, ux, uy, A(2) * P.M * mu, ge);
+    } else {
+      const A p0 = rho * P.T / (A(1) - P.b * rho) - P.a * rho * rho;
+      feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * rho * rlap, P.kappa, rdx, rdy, rdx, rdy, P.lambda_scale * P.nu, fe);
+    }
+    for (int i = 0; i < 9; ++i) {
+      S::sf(B.f, N, n, i, fe[i]);
+      if (BIN) S::sg(B.g, B.g0, N, n, i, ge[i]);
+    }
+  }
+}
+
+template <int MODEL, class S>
+__device__ __forceinline__ bool node_state(const Geom& G, const Buf<S>& B, size_t N, int x, int y, bool rested,
+                                           typename S::A f[9], typename S::A g[9]) {
+  if (is_solid(G, x, y)) return false;
+  load_node<MODEL, S>(B, N, (size_t)y * G.nx + x, f, g);
+  if (rested) {
+    bool sol[3][3], bnd;
+    neighbour_solids(G, x, y, sol, bnd);
+    if (bnd) rest(f);
+  }
+  return true;
+}
+
+// rho, u = j / rho, phi per node (boundary nodes after the rest rule).
+template <int MODEL, class S>
+__global__ void fields_kernel(Geom G, Buf<S> B, double* __restrict__ rho, double* __restrict__ ux,
+                              double* __restrict__ uy, double* __restrict__ phi) {
+  using A = typename S::A;
+  const size_t N = (size_t)G.nx * G.ny;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    A f[9], g[9];
+    if (!node_state<MODEL, S>(G, B, N, x, y, true, f, g)) {
+      rho[n] = ux[n] = uy[n] = phi[n] = 0.0;
+      continue;
+    }
+    const A r = sum9(f);
+    rho[n] = (double)r;
+    ux[n] = (double)(momx(f) / r);
+    uy[n] = (double)(momy(f) / r);
+    phi[n] = MODEL == MODEL_BINARY ? (double)sum9(g) : 0.0;
+  }
+}
+
+template <int MODEL, class S>
+__global__ void pops_out_kernel(Geom G, Buf<S> B, int rested, double* __restrict__ fo, double* __restrict__ go) {
+  using A = typename S::A;
+  const size_t N = (size_t)G.nx * G.ny;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    A f[9], g[9];
+    const bool fl = node_state<MODEL, S>(G, B, N, x, y, rested != 0, f, g);
+    for (int i = 0; i < 9; ++i) {
+      fo[i * N + n] = fl ? (double)f[i] : 0.0;
+      if (MODEL == MODEL_BINARY && go) go[i * N + n] = fl ? (double)g[i] : 0.0;
+    }
+  }
+}
+
+template <int MODEL, class S>
+__global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, const double* __restrict__ gi) {
+  using A = typename S::A;
+  const size_t N = (size_t)G.nx * G.ny;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    const bool sol = is_solid(G, x, y);
+    for (int i = 0; i < 9; ++i) {
+      S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]));
+      if (MODEL == MODEL_BINARY) S::sg(B.g, B.g0, N, n, i, sol ? A(0) : A(gi[i * N + n]));
+    }
+  }
+}
+
+// ------------------------------------------------------------- reductions
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_PARTS = 3;  // mass, phi sum, tube liquid volume
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block partial sums in FP64 (the state may be FP32/FP16; every node value is
+// widened before it is added).  partials[b * RED_PARTS + k].
+template <int MODEL, class S>
+__global__ void __launch_bounds__(RED_THREADS) reduce_partials_kernel(Geom G, Buf<S> B, double rho_l, double rho_g,
+                                                                      double* __restrict__ partials) {
+  using A = typename S::A;
+  const size_t N = (size_t)G.nx * G.ny;
+  double acc[RED_PARTS] = {0.0, 0.0, 0.0};
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    if (is_solid(G, x, y)) continue;
+    A f[9], g[9];
+    load_node<MODEL, S>(B, N, n, f, g);
+    double r = 0.0, p = 0.0;
+    for (int i = 0; i < 9; ++i) r += (double)f[i];
+    if (MODEL == MODEL_BINARY)
+      for (int i = 0; i < 9; ++i) p += (double)g[i];
+    acc[0] += r;
+    acc[1] += p;
+    if (G.tube_len > 0 && col_in_tube(G, x) && row_in_band(G, y))
+      acc[2] += MODEL == MODEL_BINARY ? 0.5 * (p + 1.0) : (r - rho_g) / (rho_l - rho_g);
+  }
+  __shared__ double sh[RED_PARTS][RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < RED_PARTS; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < RED_PARTS) {
+    double s = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[threadIdx.x][w];
+    partials[blockIdx.x * RED_PARTS + threadIdx.x] = s;
+  }
+}
+
+// Centre-line value of the tube at tube column k: phi (binary) or rho - threshold.
+template <int MODEL, class S>
+__device__ __forceinline__ double centre_value(const Geom& G, const Buf<S>& B, size_t N, int k, double thr) {
+  using A = typename S::A;
+  int ya, yb;
+  if (G.tube_h & 1) {
+    ya = yb = wrapi(G.tube_y0 + (G.tube_h - 1) / 2, G.ny);
+  } else {
+    ya = wrapi(G.tube_y0 + G.tube_h / 2 - 1, G.ny);
+    yb = wrapi(G.tube_y0 + G.tube_h / 2, G.ny);
+  }
+  const int x = wrapi(G.tube_x0 + k, G.nx);
+  double va = 0.0, vb = 0.0;
+  A f[9], g[9];
+  load_node<MODEL, S>(B, N, (size_t)ya * G.nx + x, f, g);
+  for (int i = 0; i < 9; ++i) va += MODEL == MODEL_BINARY ? (double)g[i] : (double)f[i];
+  load_node<MODEL, S>(B, N, (size_t)yb * G.nx + x, f, g);
+  for (int i = 0; i < 9; ++i) vb += MODEL == MODEL_BINARY ? (double)g[i] : (double)f[i];
+  return 0.5 * (va + vb) - thr;
+}
+
+// One block: sums the partials in a fixed order (deterministic) and finds the
+// first sign change of the centre line scanning from the inlet.
+// out = {l_centre, l_vol, mass, phi_sum}.
+template <int MODEL, class S>
+__global__ void __launch_bounds__(1024) reduce_final_kernel(Geom G, Buf<S> B, double thr, int nparts,
+                                                           const double* __restrict__ partials,
+                                                           double* __restrict__ out) {
+  const size_t N = (size_t)G.nx * G.ny;
+  __shared__ int first;
+  __shared__ double tot[RED_PARTS];
+  if (threadIdx.x == 0) first = INT_MAX;
+  if (threadIdx.x < RED_PARTS) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partials[b * RED_PARTS + threadIdx.x];
+    tot[threadIdx.x] = s;
+  }
+  __syncthreads();
+  const int L = G.tube_len;
+  // candidate k: c(k) > 0 and c(k+1) <= 0, or k == 0 with c(0) <= 0 (inlet already gas)
+  for (int k = threadIdx.x; k < L; k += blockDim.x) {
+    const double c0 = centre_value<MODEL, S>(G, B, N, k, thr);
+    bool hit = false;
+    if (k == 0 && !(c0 > 0.0)) hit = true;
+    if (!hit && k + 1 < L && c0 > 0.0) hit = !(centre_value<MODEL, S>(G, B, N, k + 1, thr) > 0.0);
+    if (hit) atomicMin(&first, k);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    if (L <= 0) {
+      l = 0.0;
+    } else if (first == INT_MAX) {
+      l = (double)L;
+    } else {
+      const int k = first;
+      const double c0 = centre_value<MODEL, S>(G, B, N, k, thr);
+      if (k == 0 && !(c0 > 0.0)) {
+        l = 0.0;
+      } else {
+        const double c1 = centre_value<MODEL, S>(G, B, N, k + 1, thr);
+        l = k + c0 / (c0 - c1);
+      }
+    }
+    out[0] = l;
+    out[1] = L > 0 ? tot[2] / G.tube_h : 0.0;
+    out[2] = tot[0];
+    out[3] = tot[1];
+  }
+}
+
+}  // namespace lbk

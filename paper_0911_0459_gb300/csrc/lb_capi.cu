@@ -1,0 +1,560 @@
+// Host library behind include/lb.h: context, device memory, stream, CUDA-graph
+// replay of the step kernel, reductions, tile autotuner.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "lb.h"
+#include "lb_ops.h"
+
+using namespace lbk;
+
+namespace {
+
+constexpr int kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
+constexpr int kRedParts = 152 * 4;
+
+thread_local char g_create_err[512] = "";
+
+}  // namespace
+
+struct lb_ctx {
+  lb_grid grid;
+  lb_walls walls;
+  lb_params prm;
+  cudaStream_t stream;
+  cudaStream_t cap;  // private stream used only to capture graphs
+  lb_alloc alloc;
+  int have_alloc;
+  OpsFn ops;
+  OpBufs buf[2];
+  int cur;
+  long t;
+  long fluid;
+  double* partials;
+  double* red_out;
+  int tile_x, tile_y;
+  cudaGraphExec_t gexec;
+  int poisoned;
+  char err[512];
+  std::vector<void*> owned;
+};
+
+static void set_err(lb_ctx* c, const char* fmt, ...) {
+  char* dst = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      set_err(c, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return LB_ERR_CUDA;                                                                 \
+    }                                                                                     \
+  } while (0)
+
+static void* dev_alloc(lb_ctx* c, size_t bytes) {
+  void* p = NULL;
+  if (c->have_alloc) {
+    p = c->alloc.malloc_fn(bytes, (void*)c->stream, c->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = NULL;
+  }
+  return p;
+}
+
+static void dev_free(lb_ctx* c, void* p) {
+  if (!p) return;
+  if (c->have_alloc)
+    c->alloc.free_fn(p, (void*)c->stream, c->alloc.user);
+  else
+    cudaFree(p);
+}
+
+static void* dev_alloc_owned(lb_ctx* c, size_t bytes) {
+  void* p = dev_alloc(c, bytes);
+  if (p) c->owned.push_back(p);
+  return p;
+}
+
+static OpsFn pick_ops(int model, int storage) {
+  if (model == LB_MODEL_LIQUID_GAS) {
+    if (storage == LB_STORAGE_F64) return ops_lg_f64;
+    if (storage == LB_STORAGE_F32) return ops_lg_f32;
+    return NULL;
+  }
+  if (model == LB_MODEL_BINARY) {
+    if (storage == LB_STORAGE_F64) return ops_bin_f64;
+    if (storage == LB_STORAGE_F32) return ops_bin_f32;
+    if (storage == LB_STORAGE_F16DEV) return ops_bin_f16;
+  }
+  return NULL;
+}
+
+static int is_solid_h(const lb_ctx* c, int x, int y) {
+  const lb_walls& w = c->walls;
+  if (w.tube_len <= 0) return 0;
+  int dx = ((x - w.tube_x0) % c->grid.nx + c->grid.nx) % c->grid.nx;
+  int dy = ((y - w.tube_y0) % c->grid.ny + c->grid.ny) % c->grid.ny;
+  return dx < w.tube_len && dy >= w.tube_h;
+}
+
+static OpArgs base_args(const lb_ctx* c) {
+  OpArgs a;
+  memset(&a, 0, sizeof a);
+  a.nx = c->grid.nx;
+  a.ny = c->grid.ny;
+  a.tube_x0 = c->walls.tube_x0;
+  a.tube_len = c->walls.tube_len;
+  a.tube_y0 = c->walls.tube_y0;
+  a.tube_h = c->walls.tube_h;
+  const lb_params& p = c->prm;
+  a.kappa = p.kappa; a.a = p.a; a.b = p.b; a.T = p.T;
+  a.Acoef = p.A; a.M = p.M; a.nu_l = p.nu_l; a.nu_g = p.nu_g;
+  a.nu = p.nu; a.lambda_scale = p.lambda_scale; a.h = c->walls.wall_grad;
+  a.rho_l = p.rho_l; a.rho_g = p.rho_g;
+  a.thr = p.model == LB_MODEL_LIQUID_GAS ? 0.5 * (p.rho_l + p.rho_g) : 0.0;
+  a.bx = c->tile_x;
+  a.yc = c->tile_y;
+  return a;
+}
+
+static lb_status launch_one(lb_ctx* c, cudaStream_t s, int from) {
+  OpArgs a = base_args(c);
+  a.src = c->buf[from];
+  a.dst = c->buf[1 - from];
+  CK(c->ops(OP_STEP, a, s));
+  return LB_OK;
+}
+
+static void drop_graph(lb_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = NULL;
+}
+
+static lb_status build_graph(lb_ctx* c) {
+  drop_graph(c);
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  lb_status st = LB_OK;
+  for (int k = 0; k < kGraphSteps && st == LB_OK; ++k) st = launch_one(c, c->cap, k & 1);
+  cudaGraph_t g = NULL;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (st != LB_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  CK(e);
+  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return LB_OK;
+}
+
+static size_t state_bytes(int model, int storage, size_t N, size_t* fb, size_t* gb, size_t* g0b) {
+  size_t el = storage == LB_STORAGE_F64 ? 8 : (storage == LB_STORAGE_F32 ? 4 : 2);
+  *fb = 9 * N * el;
+  *gb = model == LB_MODEL_BINARY ? (storage == LB_STORAGE_F16DEV ? 8 : 9) * N * el : 0;
+  *g0b = (model == LB_MODEL_BINARY && storage == LB_STORAGE_F16DEV) ? N * 4 : 0;
+  return *fb + *gb + *g0b;
+}
+
+static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* p, lb_ctx* c) {
+  if (!g || !w || !p) return set_err(c, "NULL argument"), LB_ERR_ARG;
+  if (g->nx < 3 || g->ny < 3) return set_err(c, "grid must be at least 3x3"), LB_ERR_ARG;
+  if ((long)g->nx * g->ny > (1L << 31) - 1) return set_err(c, "grid too large"), LB_ERR_ARG;
+  if (!pick_ops(p->model, p->storage)) return set_err(c, "unsupported model/storage pair"), LB_ERR_ARG;
+  if (w->tube_len < 0 || w->tube_len > g->nx) return set_err(c, "tube_len outside [0, nx]"), LB_ERR_ARG;
+  if (w->tube_len > 0) {
+    if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny)
+      return set_err(c, "tube origin outside the grid"), LB_ERR_ARG;
+    if (w->tube_h < 2 || w->tube_h >= g->ny) return set_err(c, "need 2 <= tube_h < ny"), LB_ERR_ARG;
+    if (w->tube_len < g->nx && g->nx - w->tube_len < 2)
+      return set_err(c, "need at least 2 reservoir columns"), LB_ERR_ARG;
+  }
+  if (!isfinite(w->wall_grad)) return set_err(c, "wall_grad not finite"), LB_ERR_ARG;
+  if (p->model == LB_MODEL_LIQUID_GAS) {
+    if (!(p->nu > 0)) return set_err(c, "nu must be > 0 (omega in (0, 2))"), LB_ERR_ARG;
+    if (!(p->b > 0) || !(p->T > 0) || !(p->kappa >= 0)) return set_err(c, "invalid van der Waals parameters"), LB_ERR_ARG;
+    if (!(p->rho_l > p->rho_g) || !(p->rho_l * p->b < 1.0))
+      return set_err(c, "need rho_g < rho_l < 1/b"), LB_ERR_ARG;
+  } else {
+    if (!(p->nu_l > 0) || !(p->nu_g > 0)) return set_err(c, "nu_l, nu_g must be > 0"), LB_ERR_ARG;
+    if (!(p->A > 0) || !(p->kappa > 0) || !(p->M >= 0)) return set_err(c, "invalid binary parameters"), LB_ERR_ARG;
+  }
+  return LB_OK;
+}
+
+static lb_status upload_and_init(lb_ctx* c, const double* rho, const double* ux, const double* uy,
+                                 const double* phi) {
+  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+  double* d = (double*)dev_alloc(c, 4 * N * sizeof(double));
+  if (!d) return set_err(c, "device allocation of %zu bytes failed", 4 * N * sizeof(double)), LB_ERR_NOMEM;
+  lb_status st = LB_OK;
+  const double* src[4] = {rho, ux, uy, phi};
+  for (int k = 0; k < 4 && st == LB_OK; ++k) {
+    cudaError_t e = src[k] ? cudaMemcpyAsync(d + k * N, src[k], N * sizeof(double), cudaMemcpyHostToDevice, c->stream)
+                           : cudaMemsetAsync(d + k * N, 0, N * sizeof(double), c->stream);
+    if (e != cudaSuccess) {
+      set_err(c, "upload failed: %s", cudaGetErrorString(e));
+      st = LB_ERR_CUDA;
+    }
+  }
+  if (st == LB_OK) {
+    OpArgs a = base_args(c);
+    a.dst = c->buf[0];
+    a.in0 = d;
+    a.in1 = d + N;
+    a.in2 = d + 2 * N;
+    a.in3 = d + 3 * N;
+    cudaError_t e = c->ops(OP_INIT, a, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      set_err(c, "init failed: %s", cudaGetErrorString(e));
+      st = LB_ERR_CUDA;
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  dev_free(c, d);
+  if (st == LB_OK) {
+    c->cur = 0;
+    c->t = 0;
+    c->poisoned = 0;
+  }
+  return st;
+}
+
+static lb_status default_state(lb_ctx* c) {
+  const int nx = c->grid.nx, ny = c->grid.ny;
+  const size_t N = (size_t)nx * ny;
+  std::vector<double> rho(N), z(N, 0.0), phi(N);
+  const lb_params& p = c->prm;
+  const double wdt = p.model == LB_MODEL_LIQUID_GAS ? 2.0 : sqrt(2.0);
+  const double xa = c->walls.gas_cols, xb = (double)c->walls.tube_x0 + p.l0;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const double chi = 0.5 * (tanh((x - xa) / wdt) - tanh((x - xb) / wdt));
+      const size_t n = (size_t)y * nx + x;
+      const int sol = is_solid_h(c, x, y);
+      if (p.model == LB_MODEL_LIQUID_GAS) {
+        rho[n] = sol ? 0.0 : p.rho_g + (p.rho_l - p.rho_g) * chi;
+        phi[n] = 0.0;
+      } else {
+        rho[n] = sol ? 0.0 : 1.0;
+        phi[n] = sol ? 0.0 : 2.0 * chi - 1.0;
+      }
+    }
+  return upload_and_init(c, rho.data(), z.data(), z.data(), phi.data());
+}
+
+extern "C" {
+
+lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params* params, const lb_alloc* alloc,
+                    void* stream, lb_ctx** out) {
+  lb_ctx* c = NULL;
+  if (!out) return set_err(NULL, "out is NULL"), LB_ERR_ARG;
+  *out = NULL;
+  lb_status st = validate(grid, walls, params, NULL);
+  if (st != LB_OK) return st;
+  if (alloc && (!alloc->malloc_fn || !alloc->free_fn)) return set_err(NULL, "incomplete allocator"), LB_ERR_ARG;
+  c = new (std::nothrow) lb_ctx();
+  if (!c) return set_err(NULL, "out of host memory"), LB_ERR_NOMEM;
+  c->grid = *grid;
+  c->walls = *walls;
+  c->prm = *params;
+  c->stream = (cudaStream_t)stream;
+  c->have_alloc = alloc != NULL;
+  if (alloc) c->alloc = *alloc;
+  c->ops = pick_ops(params->model, params->storage);
+  c->tile_x = 128;
+  c->tile_y = grid->ny < 16 ? grid->ny : 16;
+  c->gexec = NULL;
+  c->err[0] = 0;
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    set_err(NULL, "cudaStreamCreate failed: %s", cudaGetErrorString(cudaGetLastError()));
+    delete c;
+    return LB_ERR_CUDA;
+  }
+  const size_t N = (size_t)grid->nx * grid->ny;
+  size_t fb, gb, g0b;
+  state_bytes(params->model, params->storage, N, &fb, &gb, &g0b);
+  for (int k = 0; k < 2; ++k) {
+    c->buf[k].f = dev_alloc_owned(c, fb);
+    c->buf[k].g = gb ? dev_alloc_owned(c, gb) : NULL;
+    c->buf[k].g0 = g0b ? (float*)dev_alloc_owned(c, g0b) : NULL;
+    if (!c->buf[k].f || (gb && !c->buf[k].g) || (g0b && !c->buf[k].g0)) {
+      set_err(NULL, "device allocation of the state (%zu bytes) failed", 2 * (fb + gb + g0b));
+      lb_destroy(c);
+      return LB_ERR_NOMEM;
+    }
+  }
+  c->partials = (double*)dev_alloc_owned(c, kRedParts * 3 * sizeof(double));
+  c->red_out = (double*)dev_alloc_owned(c, 4 * sizeof(double));
+  if (!c->partials || !c->red_out) {
+    set_err(NULL, "device allocation failed");
+    lb_destroy(c);
+    return LB_ERR_NOMEM;
+  }
+  long fluid = 0;
+  for (int y = 0; y < grid->ny; ++y)
+    for (int x = 0; x < grid->nx; ++x) fluid += !is_solid_h(c, x, y);
+  c->fluid = fluid;
+  st = default_state(c);
+  if (st != LB_OK) {
+    snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+    lb_destroy(c);
+    return st;
+  }
+  *out = c;
+  return LB_OK;
+}
+
+void lb_destroy(lb_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->cap) cudaStreamSynchronize(c->cap);
+  drop_graph(c);
+  for (void* p : c->owned) dev_free(c, p);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+lb_status lb_init_fields(lb_ctx* c, const double* rho, const double* ux, const double* uy, const double* phi) {
+  if (!c || !rho || !ux || !uy) return c ? (set_err(c, "NULL field"), LB_ERR_ARG) : LB_ERR_ARG;
+  if (c->prm.model == LB_MODEL_BINARY && !phi) return set_err(c, "phi is required for the binary model"), LB_ERR_ARG;
+  return upload_and_init(c, rho, ux, uy, c->prm.model == LB_MODEL_BINARY ? phi : NULL);
+}
+
+lb_status lb_step(lb_ctx* c, long n) {
+  if (!c) return LB_ERR_ARG;
+  if (n < 0) return set_err(c, "negative step count"), LB_ERR_ARG;
+  if (c->poisoned) return set_err(c, "context holds a non-finite or timed-out state"), LB_ERR_STATE;
+  long rem = n;
+  if (rem > 0 && c->cur == 1) {
+    lb_status st = launch_one(c, c->stream, 1);
+    if (st) return st;
+    c->cur = 0;
+    c->t++;
+    rem--;
+  }
+  if (rem >= kGraphSteps) {
+    if (!c->gexec) {
+      lb_status st = build_graph(c);
+      if (st) return st;
+    }
+    while (rem >= kGraphSteps) {
+      CK(cudaGraphLaunch(c->gexec, c->stream));
+      rem -= kGraphSteps;
+      c->t += kGraphSteps;
+    }
+  }
+  while (rem > 0) {
+    lb_status st = launch_one(c, c->stream, c->cur);
+    if (st) return st;
+    c->cur ^= 1;
+    c->t++;
+    rem--;
+  }
+  return LB_OK;
+}
+
+lb_status lb_fields(lb_ctx* c, double* rho, double* ux, double* uy, double* phi) {
+  if (!c) return LB_ERR_ARG;
+  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+  double* d = (double*)dev_alloc(c, 4 * N * sizeof(double));
+  if (!d) return set_err(c, "device allocation failed"), LB_ERR_NOMEM;
+  OpArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.out0 = d;
+  a.out1 = d + N;
+  a.out2 = d + 2 * N;
+  a.out3 = d + 3 * N;
+  lb_status st = LB_OK;
+  cudaError_t e = c->ops(OP_FIELDS, a, c->stream);
+  double* dst[4] = {rho, ux, uy, phi};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    if (dst[k]) e = cudaMemcpyAsync(dst[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    set_err(c, "lb_fields: %s", cudaGetErrorString(e));
+    st = LB_ERR_CUDA;
+  }
+  dev_free(c, d);
+  return st;
+}
+
+lb_status lb_filled_length(lb_ctx* c, double* l_centre, double* l_vol, double* mass, double* phi_sum) {
+  if (!c) return LB_ERR_ARG;
+  OpArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.nparts = kRedParts;
+  a.partials = c->partials;
+  a.red_out = c->red_out;
+  CK(c->ops(OP_RED_PARTIALS, a, c->stream));
+  CK(c->ops(OP_RED_FINAL, a, c->stream));
+  double h[4];
+  CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (l_centre) *l_centre = h[0];
+  if (l_vol) *l_vol = h[1];
+  if (mass) *mass = h[2];
+  if (phi_sum) *phi_sum = h[3];
+  if (!isfinite(h[2]) || !isfinite(h[3])) {
+    c->poisoned = 1;
+    set_err(c, "non-finite mass or phi sum at step %ld", c->t);
+    return LB_ERR_NONFINITE;
+  }
+  return LB_OK;
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f, double* g, int rested) {
+  if (!c || !f) return c ? (set_err(c, "f is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
+  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+  const int bin = c->prm.model == LB_MODEL_BINARY;
+  double* d = (double*)dev_alloc(c, (bin ? 18 : 9) * N * sizeof(double));
+  if (!d) return set_err(c, "device allocation failed"), LB_ERR_NOMEM;
+  OpArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.flag = rested;
+  a.out0 = d;
+  a.out1 = bin ? d + 9 * N : NULL;
+  cudaError_t e = c->ops(OP_POPS_OUT, a, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && bin && g)
+    e = cudaMemcpyAsync(g, d + 9 * N, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = e2;
+  dev_free(c, d);
+  if (e != cudaSuccess) return set_err(c, "lb_get_populations: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  return LB_OK;
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
+  if (!c || !f) return c ? (set_err(c, "f is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
+  const int bin = c->prm.model == LB_MODEL_BINARY;
+  if (bin && !g) return set_err(c, "g is required for the binary model"), LB_ERR_ARG;
+  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+  double* d = (double*)dev_alloc(c, (bin ? 18 : 9) * N * sizeof(double));
+  if (!d) return set_err(c, "device allocation failed"), LB_ERR_NOMEM;
+  cudaError_t e = cudaMemcpyAsync(d, f, 9 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && bin) e = cudaMemcpyAsync(d + 9 * N, g, 9 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  OpArgs a = base_args(c);
+  a.dst = c->buf[0];
+  a.in0 = d;
+  a.in1 = bin ? d + 9 * N : NULL;
+  if (e == cudaSuccess) e = c->ops(OP_POPS_IN, a, c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = e2;
+  dev_free(c, d);
+  if (e != cudaSuccess) return set_err(c, "lb_set_populations: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  c->cur = 0;
+  c->poisoned = 0;
+  return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx* c) {
+  if (!c) return LB_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  return LB_OK;
+}
+
+long lb_time(const lb_ctx* c) { return c ? c->t : -1; }
+
+long lb_fluid_nodes(const lb_ctx* c) { return c ? c->fluid : -1; }
+
+lb_status lb_set_tile(lb_ctx* c, int tile_x, int tile_y) {
+  if (!c) return LB_ERR_ARG;
+  if (tile_x != 64 && tile_x != 128 && tile_x != 256) return set_err(c, "tile_x must be 64, 128 or 256"), LB_ERR_ARG;
+  if (tile_y < 1 || tile_y > c->grid.ny) return set_err(c, "tile_y must be in [1, ny]"), LB_ERR_ARG;
+  if (tile_x != c->tile_x || tile_y != c->tile_y) {
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+  }
+  c->tile_x = tile_x;
+  c->tile_y = tile_y;
+  return LB_OK;
+}
+
+lb_status lb_get_tile(const lb_ctx* c, int* tile_x, int* tile_y) {
+  if (!c) return LB_ERR_ARG;
+  if (tile_x) *tile_x = c->tile_x;
+  if (tile_y) *tile_y = c->tile_y;
+  return LB_OK;
+}
+
+lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) {
+  if (!c) return LB_ERR_ARG;
+  if (c->poisoned) return LB_ERR_STATE;
+  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+  size_t fb, gb, g0b;
+  const size_t total = state_bytes(c->prm.model, c->prm.storage, N, &fb, &gb, &g0b);
+  CK(cudaStreamSynchronize(c->stream));
+  // save the current state so that tuning leaves it untouched
+  char* save = (char*)dev_alloc(c, total);
+  if (!save) return set_err(c, "device allocation failed"), LB_ERR_NOMEM;
+  const OpBufs cur = c->buf[c->cur];
+  lb_status st = LB_OK;
+  cudaError_t e = cudaMemcpyAsync(save, cur.f, fb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && gb) e = cudaMemcpyAsync(save + fb, cur.g, gb, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && g0b) e = cudaMemcpyAsync(save + fb + gb, cur.g0, g0b, cudaMemcpyDeviceToDevice, c->stream);
+  const int cand_x[3] = {64, 128, 256};
+  const int cand_y[6] = {2, 4, 8, 16, 32, 64};
+  int best_x = c->tile_x, best_y = c->tile_y;
+  float best = 1e30f;
+  cudaEvent_t e0 = NULL, e1 = NULL;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int reps = 10;
+  for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
+    for (int iy = 0; iy < 6 && e == cudaSuccess && st == LB_OK; ++iy) {
+      if (cand_y[iy] > c->grid.ny) continue;
+      c->tile_x = cand_x[ix];
+      c->tile_y = cand_y[iy];
+      int from = c->cur;
+      for (int k = 0; k < 2 && st == LB_OK; ++k, from ^= 1) st = launch_one(c, c->stream, from);
+      e = cudaEventRecord(e0, c->stream);
+      for (int k = 0; k < reps && st == LB_OK; ++k, from ^= 1) st = launch_one(c, c->stream, from);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_x = cand_x[ix];
+        best_y = cand_y[iy];
+      }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // restore
+  cudaError_t er = cudaMemcpyAsync(cur.f, save, fb, cudaMemcpyDeviceToDevice, c->stream);
+  if (er == cudaSuccess && gb) er = cudaMemcpyAsync(cur.g, save + fb, gb, cudaMemcpyDeviceToDevice, c->stream);
+  if (er == cudaSuccess && g0b) er = cudaMemcpyAsync(cur.g0, save + fb + gb, g0b, cudaMemcpyDeviceToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  dev_free(c, save);
+  c->tile_x = best_x;
+  c->tile_y = best_y;
+  drop_graph(c);
+  if (st != LB_OK) return st;
+  if (e != cudaSuccess || er != cudaSuccess)
+    return set_err(c, "lb_autotune: %s", cudaGetErrorString(e != cudaSuccess ? e : er)), LB_ERR_CUDA;
+  if (tile_x) *tile_x = best_x;
+  if (tile_y) *tile_y = best_y;
+  if (us_per_step) *us_per_step = 1000.0 * best / reps;
+  return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* c) { return c ? c->err : g_create_err; }
+
+}  // extern "C"

@@ -1,0 +1,443 @@
+// Device code of the fused D2Q9 free-energy MRT step (stencils + equilibria +
+// collision + streaming + walls) for sm_103a.
+//
+// Layout: structure of arrays, plane i of f at f + i*N (N = nx*ny), node (x, y)
+// at y*nx + x.  A CTA owns BX consecutive columns and a band of rows; it walks
+// up the band with a 4-slot ring of rho/phi rows in shared memory (the 3x3
+// stencils of Eq. (best) need rows y-1, y, y+1) while the populations of the
+// next two rows are already in flight in registers.  Post-collision populations
+// are pushed to r + e_i in the other buffer; a push into a solid node returns
+// to the source node in the opposite direction (bounce-back, Sec. 2.2).  The
+// stored state is the post-streaming state before the boundary-node rest rule;
+// that rule (Sec. 2.2) is applied when a boundary node is next read, which
+// leaves rho unchanged and therefore leaves the stencils unchanged.
+//
+// Collision: with S = diag(0,1,1,0,1,0,1,w,w) (App. A) every mode except the
+// two stress modes pxx, pxy relaxes fully, so f - M^-1 S M (f - f^eq) equals
+// f^eq + (1 - w) M^-1 (0,...,0, dm_xx, dm_xy) with dm the stress-mode
+// non-equilibrium; the columns of M^-1 for those modes are (row of M)/4.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbk {
+
+enum { MODEL_LG = 0, MODEL_BINARY = 1 };
+
+struct Geom {
+  int nx, ny;
+  int tube_x0, tube_len;  // tube columns [x0, x0 + len) mod nx; len == 0: no solid
+  int tube_y0, tube_h;    // fluid band [y0, y0 + h) mod ny inside the tube
+};
+
+template <typename A>
+struct Phys {
+  A kappa, a, b, T;    // van der Waals (Sec. 2)
+  A Acoef, M;          // phi^4 coefficient and mobility (Sec. 3.1)
+  A nu_l, nu_g;        // Eq. (nu)
+  A nu;                // liquid-gas viscosity
+  A lambda_scale;      // lambda = lambda_scale * nu_local
+  A h;                 // wall gradient of the wetted field
+};
+
+// ------------------------------------------------------------------ storage
+
+// Rest weights of the standard D2Q9 equilibrium, used as the offset of the
+// FP16 deviation storage: f_i is stored as f_i - WSTD_i * rho0 with rho0 = 1.
+__device__ __forceinline__ float wstd(int i) {
+  return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+
+struct SF64 {
+  using T = double;
+  using A = double;
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) { return __ldg(f + i * N + n); }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
+    return __ldg(g + i * N + n);
+  }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
+};
+
+struct SF32 {
+  using T = float;
+  using A = float;
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) { return __ldg(f + i * N + n); }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
+    return __ldg(g + i * N + n);
+  }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
+};
+
+struct SF16 {
+  using T = __half;
+  using A = float;
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) {
+    return __half2float(__ldg(f + i * N + n)) + wstd(i);
+  }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) {
+    f[i * N + n] = __float2half_rn(v - wstd(i));
+  }
+  // g_1..g_8 in FP16 planes 0..7; g_0 (which carries phi) in an FP32 plane.
+  __device__ static A lg(const T* __restrict__ g, const float* __restrict__ g0, size_t N, size_t n, int i) {
+    return i == 0 ? __ldg(g0 + n) : __half2float(__ldg(g + (i - 1) * N + n));
+  }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__ g0, size_t N, size_t n, int i, A v) {
+    if (i == 0)
+      g0[n] = v;
+    else
+      g[(i - 1) * N + n] = __float2half_rn(v);
+  }
+};
+
+template <class S>
+struct Buf {
+  typename S::T* f;
+  typename S::T* g;
+  float* g0;
+};
+
+// ----------------------------------------------------------------- geometry
+
+__device__ __forceinline__ bool col_in_tube(const Geom& G, int x) {
+  int d = x - G.tube_x0;
+  if (d < 0) d += G.nx;
+  return d < G.tube_len;
+}
+__device__ __forceinline__ bool row_in_band(const Geom& G, int y) {
+  int d = y - G.tube_y0;
+  if (d < 0) d += G.ny;
+  return d < G.tube_h;
+}
+__device__ __forceinline__ bool is_solid(const Geom& G, int x, int y) {
+  return G.tube_len > 0 && col_in_tube(G, x) && !row_in_band(G, y);
+}
+__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Solid flags of the 3x3 neighbourhood of (x, y), s[j][i] <-> offset (i-1, j-1).
+__device__ __forceinline__ void neighbour_solids(const Geom& G, int x, int y, bool s[3][3], bool& any) {
+  bool tc[3], rb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    tc[k] = G.tube_len > 0 && col_in_tube(G, wrapi(x + k - 1, G.nx));
+    rb[k] = row_in_band(G, wrapi(y + k - 1, G.ny));
+  }
+  any = false;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      s[j][i] = tc[i] && !rb[j];
+      any = any || s[j][i];
+    }
+}
+
+// Ghost values for solid neighbours (wetting condition of Sec. 2.2): mirror
+// through the fluid node; across a y-facing wall the mirror value is lowered by
+// 2h so that the centred normal derivative equals h.  Mirror nodes are fluid
+// for every geometry the host accepts.
+template <typename A>
+__device__ __forceinline__ void apply_ghosts(A v[3][3], const bool s[3][3], A h) {
+  A out[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      out[j][i] = v[j][i];
+      if (!s[j][i]) continue;
+      if (j == 1)
+        out[j][i] = v[1][2 - i];                       // end face: neutral
+      else if (i == 1)
+        out[j][i] = v[2 - j][1] - A(2) * h;            // wall row
+      else if (!s[2 - j][i])
+        out[j][i] = v[2 - j][i] - A(2) * h;            // corner, y-mirror
+      else
+        out[j][i] = v[j][2 - i];                       // corner, x-mirror
+    }
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[j][i] = out[j][i];
+}
+
+// Eq. (best): isotropic gradient and Laplacian on the 3x3 neighbourhood.
+template <typename A>
+__device__ __forceinline__ void stencil3(const A v[3][3], A& dx, A& dy, A& lap) {
+  dx = ((v[0][2] - v[0][0]) + A(4) * (v[1][2] - v[1][0]) + (v[2][2] - v[2][0])) * A(1.0 / 12.0);
+  dy = ((v[2][0] + A(4) * v[2][1] + v[2][2]) - (v[0][0] + A(4) * v[0][1] + v[0][2])) * A(1.0 / 12.0);
+  lap = ((v[0][0] + v[0][2] + v[2][0] + v[2][2]) + A(4) * (v[0][1] + v[1][0] + v[1][2] + v[2][1]) -
+         A(20) * v[1][1]) * A(1.0 / 6.0);
+}
+
+// ------------------------------------------------------------- equilibria
+
+// f^eq_1..8 of Eq. (equilibrium), grouped by direction; f^eq_0 = rho - sum.
+template <typename A>
+__device__ __forceinline__ void feq9(A rho, A jx, A jy, A ux, A uy, A P0, A kap, A gpx, A gpy, A grx,
+                                     A gry, A lam, A fe[9]) {
+  const A udr = ux * grx + uy * gry;
+  const A Txx = jx * ux + lam * (A(2) * ux * grx + udr);
+  const A Tyy = jy * uy + lam * (A(2) * uy * gry + udr);
+  const A Txy = jx * uy + lam * (ux * gry + uy * grx);
+  const A tr3 = (Txx + Tyy) * A(1.0 / 3.0);
+  const A ax = A(1.5) * (Txx - tr3);
+  const A ay = A(1.5) * (Tyy - tr3);
+  const A dp = A(1.5) * (Txx + Tyy + A(2) * Txy - tr3);
+  const A dm = A(1.5) * (Txx + Tyy - A(2) * Txy - tr3);
+  const A Gxx = kap * gpx * gpx, Gyy = kap * gpy * gpy, Gxy = kap * gpx * gpy;
+  const A k13 = Gxx * A(1.0 / 3.0) - Gyy * A(1.0 / 6.0);
+  const A k24 = Gyy * A(1.0 / 3.0) - Gxx * A(1.0 / 6.0);
+  const A kd = -(Gxx + Gyy) * A(1.0 / 24.0);
+  const A kxy = Gxy * A(0.25);
+  fe[1] = (P0 + jx + ax) * A(1.0 / 3.0) + k13;
+  fe[2] = (P0 - jx + ax) * A(1.0 / 3.0) + k13;
+  fe[3] = (P0 + jy + ay) * A(1.0 / 3.0) + k24;
+  fe[4] = (P0 - jy + ay) * A(1.0 / 3.0) + k24;
+  fe[5] = (P0 + jx + jy + dp) * A(1.0 / 12.0) + kd + kxy;
+  fe[6] = (P0 - jx - jy + dp) * A(1.0 / 12.0) + kd + kxy;
+  fe[7] = (P0 - jx + jy + dm) * A(1.0 / 12.0) + kd - kxy;
+  fe[8] = (P0 + jx - jy + dm) * A(1.0 / 12.0) + kd - kxy;
+  fe[0] = rho - (((fe[1] + fe[2]) + (fe[3] + fe[4])) + ((fe[5] + fe[6]) + (fe[7] + fe[8])));
+}
+
+// g^eq of Appendix A (dt = 1).
+template <typename A>
+__device__ __forceinline__ void geq9(A phi, A ux, A uy, A Q, A ge[9]) {
+  const A u2 = (ux * ux + uy * uy) * A(1.0 / 3.0);
+  const A px = phi * ux, py = phi * uy;
+  const A sx = A(1.5) * phi * (ux * ux - u2);
+  const A sy = A(1.5) * phi * (uy * uy - u2);
+  const A upp = ux + uy, ump = ux - uy;
+  const A sp = A(1.5) * phi * (upp * upp - u2);
+  const A sm = A(1.5) * phi * (ump * ump - u2);
+  ge[1] = (Q + px + sx) * A(1.0 / 3.0);
+  ge[2] = (Q - px + sx) * A(1.0 / 3.0);
+  ge[3] = (Q + py + sy) * A(1.0 / 3.0);
+  ge[4] = (Q - py + sy) * A(1.0 / 3.0);
+  ge[5] = (Q + px + py + sp) * A(1.0 / 12.0);
+  ge[6] = (Q - px - py + sp) * A(1.0 / 12.0);
+  ge[7] = (Q - px + py + sm) * A(1.0 / 12.0);
+  ge[8] = (Q + px - py + sm) * A(1.0 / 12.0);
+  ge[0] = phi - (((ge[1] + ge[2]) + (ge[3] + ge[4])) + ((ge[5] + ge[6]) + (ge[7] + ge[8])));
+}
+
+template <typename A>
+__device__ __forceinline__ A sum9(const A v[9]) {
+  return v[0] + (((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8])));
+}
+template <typename A>
+__device__ __forceinline__ A momx(const A f[9]) { return (f[1] - f[2]) + ((f[5] - f[6]) - (f[7] - f[8])); }
+template <typename A>
+__device__ __forceinline__ A momy(const A f[9]) { return (f[3] - f[4]) + ((f[5] - f[6]) + (f[7] - f[8])); }
+
+// Rest rule of Sec. 2.2 at a boundary node: f_i -= w_i e_i . j (w = 1/3, 1/12)
+// removes the momentum and keeps the density.
+template <typename A>
+__device__ __forceinline__ void rest(A f[9]) {
+  const A jx = momx(f), jy = momy(f);
+  const A a = jx * A(1.0 / 3.0), b = jy * A(1.0 / 3.0);
+  const A c = (jx + jy) * A(1.0 / 12.0), d = (jy - jx) * A(1.0 / 12.0);
+  f[1] -= a; f[2] += a; f[3] -= b; f[4] += b;
+  f[5] -= c; f[6] += c; f[7] -= d; f[8] += d;
+}
+
+// Local viscosity, Eq. (nu), with (phi + 1)/2 clamped to [0, 1].
+template <typename A>
+__device__ __forceinline__ A local_nu_binary(const Phys<A>& P, A phi) {
+  A c = (phi + A(1)) * A(0.5);
+  c = c < A(0) ? A(0) : (c > A(1) ? A(1) : c);
+  return P.nu_g + c * (P.nu_l - P.nu_g);
+}
+
+// Lattice velocities (Sec. 2.1, c = 1) as compile-time functions of i.
+__host__ __device__ constexpr int EXd(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 2 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int EYd(int i) { return (i == 3 || i == 5 || i == 7) ? 1 : ((i == 4 || i == 6 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int OPPd(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// ---------------------------------------------------------------- the step
+
+template <int MODEL, class S>
+struct StepArgs {
+  Geom G;
+  Phys<typename S::A> P;
+  Buf<S> src, dst;
+  int yc;  // rows per CTA band
+};
+
+template <int MODEL, class S, int BX>
+struct StepSmem {
+  typename S::A r[4][BX + 2];
+  typename S::A p[MODEL == MODEL_BINARY ? 4 : 1][BX + 2];
+};
+
+template <int MODEL, class S>
+__device__ __forceinline__ void load_node(const Buf<S>& B, size_t N, size_t n, typename S::A f[9],
+                                          typename S::A g[9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = S::lf(B.f, N, n, i);
+  if (MODEL == MODEL_BINARY) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = S::lg(B.g, B.g0, N, n, i);
+  }
+}
+
+// Process columns [xb, xb + BX) (clipped to nx) and rows [y0, y1) of one lattice.
+template <int MODEL, class S, int BX>
+__device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::A>& P, const Buf<S>& src,
+                                          const Buf<S>& dst, int xb, int y0, int y1,
+                                          StepSmem<MODEL, S, BX>& sm) {
+  using A = typename S::A;
+  constexpr bool BIN = MODEL == MODEL_BINARY;
+  const int nx = G.nx, ny = G.ny;
+  const size_t N = (size_t)nx * ny;
+  const int tid = threadIdx.x;
+  const int w = min(BX, nx - xb);  // columns in this tile
+  const int x = xb + tid;
+  const bool act = tid < w;
+  // halo columns: thread 0 takes the left one, thread 1 the right one
+  const int hx = tid == 0 ? wrapi(xb - 1, nx) : wrapi(xb + w, nx);
+  const int hs = tid == 0 ? 0 : w + 1;
+  const bool hal = tid < 2;
+
+  A fa[9], ga[9], fb[9], gb[9], fc[9], gc[9];  // rows y (a), y+1 (b), y+2 (c)
+  A hf[9], hg[9];
+  auto slot = [&](int r) { return (r - y0 + 1) & 3; };
+
+  // load row r (wrapped) for this thread's column into f, g, and publish rho/phi
+  auto publish = [&](int r, const A* f, const A* g, bool fluid, const A* hf_, const A* hg_, bool hfluid) {
+    const int s = slot(r);
+    if (act) {
+      sm.r[s][tid + 1] = fluid ? sum9(f) : A(0);
+      if (BIN) sm.p[s][tid + 1] = fluid ? sum9(g) : A(0);
+    }
+    if (hal) {
+      sm.r[s][hs] = hfluid ? sum9(hf_) : A(0);
+      if (BIN) sm.p[s][hs] = hfluid ? sum9(hg_) : A(0);
+    }
+  };
+  auto fetch = [&](int r, A* f, A* g, bool& fluid, bool& hfluid) {
+    const int rr = wrapi(r, ny);
+    fluid = act && !is_solid(G, x, rr);
+    if (fluid) load_node<MODEL, S>(src, N, (size_t)rr * nx + x, f, g);
+    hfluid = hal && !is_solid(G, hx, rr);
+    if (hfluid) load_node<MODEL, S>(src, N, (size_t)rr * nx + hx, hf, hg);
+  };
+
+  bool fl_a, fl_b, fl_c, hfl;
+  {
+    bool dummy;
+    A tf[9], tg[9];
+    fetch(y0 - 1, tf, tg, dummy, hfl);
+    publish(y0 - 1, tf, tg, dummy, hf, hg, hfl);
+    fetch(y0, fa, ga, fl_a, hfl);
+    publish(y0, fa, ga, fl_a, hf, hg, hfl);
+    fetch(y0 + 1, fb, gb, fl_b, hfl);
+    publish(y0 + 1, fb, gb, fl_b, hf, hg, hfl);
+  }
+  __syncthreads();
+
+  for (int y = y0; y < y1; ++y) {
+    const bool more = y + 2 <= y1;
+    if (more) fetch(y + 2, fc, gc, fl_c, hfl);
+
+    if (fl_a) {
+      const int yy = wrapi(y, ny);
+      bool sol[3][3], bnd;
+      neighbour_solids(G, x, yy, sol, bnd);
+      A vr[3][3], vp[3][3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          vr[j][i] = sm.r[slot(y - 1 + j)][tid + i];
+          if (BIN) vp[j][i] = sm.p[slot(y - 1 + j)][tid + i];
+        }
+      if (bnd) {
+        apply_ghosts(vr, sol, BIN ? A(0) : P.h);
+        if (BIN) apply_ghosts(vp, sol, P.h);
+        rest(fa);
+      }
+      A rdx, rdy, rlap;
+      stencil3(vr, rdx, rdy, rlap);
+      const A rho = vr[1][1];
+      const A jx = momx(fa), jy = momy(fa);
+      const A inv = A(1) / rho;
+      const A ux = jx * inv, uy = jy * inv;
+      A fe[9], ge[9];
+      A omega;
+      if (BIN) {
+        A pdx, pdy, plap;
+        stencil3(vp, pdx, pdy, plap);
+        const A phi = vp[1][1];
+        const A phi2 = phi * phi;
+        const A p0 = rho * A(1.0 / 3.0) + P.Acoef * (A(-0.5) * phi2 + A(0.75) * phi2 * phi2);
+        const A mu = P.Acoef * (phi2 * phi - phi) - P.kappa * plap;
+        const A nu = local_nu_binary(P, phi);
+        omega = A(2) / (A(6) * nu + A(1));
+        feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * phi * plap, P.kappa, pdx, pdy, rdx, rdy,
+                P.lambda_scale * nu, fe);
+        geq9<A>(phi, ux, uy, A(2) * P.M * mu, ge);
+      } else {
+        const A p0 = rho * P.T / (A(1) - P.b * rho) - P.a * rho * rho;
+        omega = A(2) / (A(6) * P.nu + A(1));
+        feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * rho * rlap, P.kappa, rdx, rdy, rdx, rdy,
+                P.lambda_scale * P.nu, fe);
+      }
+      // stress-mode non-equilibrium, relaxed at rate omega; all else to f^eq
+      const A c = (A(1) - omega) * A(0.25);
+      const A mxx = c * (((fa[1] + fa[2]) - (fa[3] + fa[4])) - ((fe[1] + fe[2]) - (fe[3] + fe[4])));
+      const A mxy = c * (((fa[5] + fa[6]) - (fa[7] + fa[8])) - ((fe[5] + fe[6]) - (fe[7] + fe[8])));
+      A fs[9];
+      fs[0] = fe[0];
+      fs[1] = fe[1] + mxx; fs[2] = fe[2] + mxx;
+      fs[3] = fe[3] - mxx; fs[4] = fe[4] - mxx;
+      fs[5] = fe[5] + mxy; fs[6] = fe[6] + mxy;
+      fs[7] = fe[7] - mxy; fs[8] = fe[8] - mxy;
+      // streaming with bounce-back
+      const size_t self = (size_t)yy * nx + x;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int ex = EXd(i), ey = EYd(i);
+        const int o = OPPd(i);
+        size_t dn;
+        int di;
+        if (bnd && sol[1 + ey][1 + ex]) {
+          dn = self;
+          di = o;
+        } else {
+          dn = (size_t)wrapi(yy + ey, ny) * nx + wrapi(x + ex, nx);
+          di = i;
+        }
+        S::sf(dst.f, N, dn, di, fs[i]);
+        if (BIN) S::sg(dst.g, dst.g0, N, dn, di, ge[i]);
+      }
+    }
+
+    if (more) publish(y + 2, fc, gc, fl_c, hf, hg, hfl);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      fa[i] = fb[i];
+      fb[i] = fc[i];
+      if (BIN) {
+        ga[i] = gb[i];
+        gb[i] = gc[i];
+      }
+    }
+    fl_a = fl_b;
+    fl_b = more ? fl_c : false;
+  }
+}
+
+template <int MODEL, class S, int BX>
+__global__ void __launch_bounds__(BX) step_kernel(StepArgs<MODEL, S> a) {
+  __shared__ StepSmem<MODEL, S, BX> sm;
+  const int xb = blockIdx.x * BX;
+  const int y0 = blockIdx.y * a.yc;
+  const int y1 = min(y0 + a.yc, a.G.ny);
+  step_band<MODEL, S, BX>(a.G, a.P, a.src, a.dst, xb, y0, y1, sm);
+}
+
+}  // namespace lbk

@@ -1,0 +1,45 @@
+// Host-side, type-erased interface between the C ABI (lb_capi.cu) and the
+// kernel instantiations (one translation unit per model x storage).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace lbk {
+
+enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL };
+
+struct OpBufs {
+  void* f;
+  void* g;
+  float* g0;
+};
+
+struct OpArgs {
+  // geometry
+  int nx, ny, tube_x0, tube_len, tube_y0, tube_h;
+  // physics (converted to the arithmetic type by the instantiation)
+  double kappa, a, b, T, Acoef, M, nu_l, nu_g, nu, lambda_scale, h;
+  double rho_l, rho_g, thr;
+  // buffers
+  OpBufs src, dst;
+  // step tile
+  int bx, yc;
+  // field / population / reduction arguments (device pointers)
+  const double *in0, *in1, *in2, *in3;
+  double *out0, *out1, *out2, *out3;
+  int flag;      // rested flag for OP_POPS_OUT
+  int nparts;    // reduction partial blocks
+  double* partials;
+  double* red_out;
+};
+
+typedef cudaError_t (*OpsFn)(OpKind, const OpArgs&, cudaStream_t);
+
+cudaError_t ops_lg_f64(OpKind, const OpArgs&, cudaStream_t);
+cudaError_t ops_lg_f32(OpKind, const OpArgs&, cudaStream_t);
+cudaError_t ops_bin_f64(OpKind, const OpArgs&, cudaStream_t);
+cudaError_t ops_bin_f32(OpKind, const OpArgs&, cudaStream_t);
+cudaError_t ops_bin_f16(OpKind, const OpArgs&, cudaStream_t);
+
+}  // namespace lbk

@@ -1,0 +1,81 @@
+// Launch wrappers of every kernel for one (model, storage) pair.
+#pragma once
+
+#include "lb_aux.cuh"
+#include "lb_device.cuh"
+#include "lb_ops.h"
+
+namespace lbk {
+
+template <class S>
+static Buf<S> to_buf(const OpBufs& b) {
+  return Buf<S>{(typename S::T*)b.f, (typename S::T*)b.g, b.g0};
+}
+
+static inline Geom to_geom(const OpArgs& a) {
+  return Geom{a.nx, a.ny, a.tube_x0, a.tube_len, a.tube_y0, a.tube_h};
+}
+
+template <typename A>
+static Phys<A> to_phys(const OpArgs& a) {
+  Phys<A> p;
+  p.kappa = A(a.kappa); p.a = A(a.a); p.b = A(a.b); p.T = A(a.T);
+  p.Acoef = A(a.Acoef); p.M = A(a.M); p.nu_l = A(a.nu_l); p.nu_g = A(a.nu_g);
+  p.nu = A(a.nu); p.lambda_scale = A(a.lambda_scale); p.h = A(a.h);
+  return p;
+}
+
+static inline int grid_for(size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+template <int MODEL, class S, int BX>
+static cudaError_t launch_step(const OpArgs& a, cudaStream_t s) {
+  StepArgs<MODEL, S> k;
+  k.G = to_geom(a);
+  k.P = to_phys<typename S::A>(a);
+  k.src = to_buf<S>(a.src);
+  k.dst = to_buf<S>(a.dst);
+  k.yc = a.yc;
+  dim3 grid((a.nx + BX - 1) / BX, (a.ny + a.yc - 1) / a.yc);
+  step_kernel<MODEL, S, BX><<<grid, BX, 0, s>>>(k);
+  return cudaGetLastError();
+}
+
+template <int MODEL, class S>
+cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
+  using A = typename S::A;
+  const Geom G = to_geom(a);
+  const size_t N = (size_t)a.nx * a.ny;
+  switch (op) {
+    case OP_STEP:
+      if (a.bx == 64) return launch_step<MODEL, S, 64>(a, s);
+      if (a.bx == 128) return launch_step<MODEL, S, 128>(a, s);
+      if (a.bx == 256) return launch_step<MODEL, S, 256>(a, s);
+      return cudaErrorInvalidValue;
+    case OP_INIT:
+      init_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_phys<A>(a), to_buf<S>(a.dst), a.in0, a.in1,
+                                                              a.in2, a.in3);
+      return cudaGetLastError();
+    case OP_FIELDS:
+      fields_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.out0, a.out1, a.out2, a.out3);
+      return cudaGetLastError();
+    case OP_POPS_OUT:
+      pops_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.flag, a.out0, a.out1);
+      return cudaGetLastError();
+    case OP_POPS_IN:
+      pops_in_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.dst), a.in0, a.in1);
+      return cudaGetLastError();
+    case OP_RED_PARTIALS:
+      reduce_partials_kernel<MODEL, S><<<a.nparts, RED_THREADS, 0, s>>>(G, to_buf<S>(a.src), a.rho_l, a.rho_g,
+                                                                        a.partials);
+      return cudaGetLastError();
+    case OP_RED_FINAL:
+      reduce_final_kernel<MODEL, S><<<1, 1024, 0, s>>>(G, to_buf<S>(a.src), a.thr, a.nparts, a.partials, a.red_out);
+      return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lbk

@@ -1,0 +1,6 @@
+// Kernel instantiations for one model x storage pair (compiled separately).
+#include "lb_ops_impl.cuh"
+
+namespace lbk {
+cudaError_t ops_bin_f32(OpKind op, const OpArgs& a, cudaStream_t s) { return ops_impl<MODEL_BINARY, SF32>(op, a, s); }
+}  // namespace lbk
