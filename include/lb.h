@@ -169,6 +169,53 @@ lb_status lb_autotune(lb_ctx *ctx, int *tile_x, int *tile_y, double *us_per_step
  * ctx is NULL).  Never NULL. */
 const char *lb_last_error(const lb_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free reductions.  The paper has no counterpart: this entry point
+ * exists for callers of this library that cannot allocate device memory --
+ * for example a host framework that owns every device buffer through its own
+ * fixed pool, or a loop that must not take the implicit synchronisation and the
+ * possible failure of cudaMalloc/cudaFree while it runs.  It computes the same
+ * four values as lb_filled_length from a state the caller holds, without a
+ * context, and calls no allocator (neither cudaMalloc/cudaFree nor any library
+ * routine that allocates).
+ *
+ * Inputs: grid, walls and params describe the lattice exactly as for lb_create
+ * (only the geometry, model, storage, rho_l and rho_g are used).  f, g and g0
+ * are device pointers to a state in the library's layout for params->storage:
+ * plane-major (9, ny, nx) arrays of double (LB_STORAGE_F64) or float
+ * (LB_STORAGE_F32); for LB_STORAGE_F16DEV, f holds 9 FP16 planes of
+ * f_i - w_i (w = 4/9, 1/9, 1/36), g holds 8 FP16 planes g_1..g_8 and g0 one
+ * FP32 plane of g_0.  g is ignored for the liquid-gas model, g0 unless the
+ * storage is LB_STORAGE_F16DEV.  out is a device pointer to 4 doubles that
+ * receives {l_centre, l_vol, mass, phi_sum} (definitions as in
+ * lb_filled_length).  nblocks is the number of blocks of the first reduction
+ * pass, each of which leaves one partial sum in the scratch.
+ *
+ * Scratch: a file-scope device array of LB_NOALLOC_MAX_BLOCKS x 3 doubles
+ * (48 KiB) that every GPU which loads the library holds until the process
+ * exits.  nblocks outside [1, LB_NOALLOC_MAX_BLOCKS] is rejected with
+ * LB_ERR_ARG.  Every call shares that array and it keeps the last call's
+ * contents; each call writes every slot it later reads, so nothing has to be
+ * cleared between calls.  Calls whose kernels overlap on the GPU (issued on
+ * different streams or from different host threads without ordering) race on
+ * the scratch and may return wrong values: issue them in order on one stream.
+ *
+ * The first call on a device looks up the scratch array's device address on the
+ * device current at that time (cudaGetSymbolAddress) and keeps it for later
+ * calls; make that first call before any stream capture begins.
+ *
+ * Asynchronous on stream (a cudaStream_t or NULL); out is valid once the stream
+ * reaches the call.  No NaN check is made (there is no context to poison):
+ * inspect mass and phi_sum.  Returns LB_ERR_ARG for a NULL required pointer, an
+ * invalid geometry, model or storage, or nblocks out of range, and LB_ERR_CUDA
+ * if the device query, the address lookup or a kernel launch fails.
+ * ------------------------------------------------------------------------ */
+#define LB_NOALLOC_MAX_BLOCKS 2048
+
+lb_status lb_filled_length_noalloc(const lb_grid *grid, const lb_walls *walls, const lb_params *params,
+                                   const void *f, const void *g, const void *g0, int nblocks,
+                                   double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,98 @@
+// lb_filled_length_noalloc: the FP64 reductions of lb_filled_length for callers
+// that cannot allocate device memory.
+//
+// The first reduction pass writes one partial sum per block (mass, sum of phi,
+// filled volume).  lb_filled_length keeps those partials in memory that the
+// context allocated; this entry point keeps them in the file-scope array below
+// instead, so it needs no context and calls no allocator.  Every GPU that loads
+// the library holds the array (LB_NOALLOC_MAX_BLOCKS x 3 doubles) until the
+// process exits.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "lb.h"
+#include "lb_aux.cuh"
+
+namespace {
+
+static __device__ __align__(256) double lb_noalloc_partials[LB_NOALLOC_MAX_BLOCKS * lbk::RED_PARTS];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_mu;
+double* g_scratch[kMaxDevices];  // device address of lb_noalloc_partials, per device
+
+// Resolve the device address of the scratch array on the current device, once.
+lb_status scratch_address(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LB_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, lb_noalloc_partials) != cudaSuccess || !p) return LB_ERR_CUDA;
+    g_scratch[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch[dev];
+  return LB_OK;
+}
+
+template <int MODEL, class S>
+cudaError_t reduce(const lbk::Geom& G, const lbk::Buf<S>& B, double rho_l, double rho_g, double thr, int nblocks,
+                   double* partials, double* out, cudaStream_t s) {
+  lbk::reduce_partials_kernel<MODEL, S><<<nblocks, lbk::RED_THREADS, 0, s>>>(G, B, rho_l, rho_g, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  lbk::reduce_final_kernel<MODEL, S><<<1, 1024, 0, s>>>(G, B, thr, nblocks, partials, out);
+  return cudaGetLastError();
+}
+
+bool geometry_ok(const lb_grid* g, const lb_walls* w) {
+  if (g->nx < 3 || g->ny < 3 || (long)g->nx * g->ny > (1L << 31) - 1) return false;
+  if (w->tube_len < 0 || w->tube_len > g->nx) return false;
+  if (w->tube_len > 0) {
+    if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny) return false;
+    if (w->tube_h < 2 || w->tube_h >= g->ny) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" lb_status lb_filled_length_noalloc(const lb_grid* grid, const lb_walls* walls, const lb_params* params,
+                                              const void* f, const void* g, const void* g0, int nblocks,
+                                              double* out, void* stream) {
+  if (!grid || !walls || !params || !f || !out) return LB_ERR_ARG;
+  if (nblocks < 1 || nblocks > LB_NOALLOC_MAX_BLOCKS) return LB_ERR_ARG;
+  if (!geometry_ok(grid, walls)) return LB_ERR_ARG;
+  const int bin = params->model == LB_MODEL_BINARY;
+  if (!bin && params->model != LB_MODEL_LIQUID_GAS) return LB_ERR_ARG;
+  if (bin && !g) return LB_ERR_ARG;
+  if (bin && params->storage == LB_STORAGE_F16DEV && !g0) return LB_ERR_ARG;
+  double* partials = nullptr;
+  lb_status st = scratch_address(&partials);
+  if (st != LB_OK) return st;
+  const lbk::Geom G{grid->nx, grid->ny, walls->tube_x0, walls->tube_len, walls->tube_y0, walls->tube_h};
+  const double thr = bin ? 0.0 : 0.5 * (params->rho_l + params->rho_g);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* g0f = static_cast<float*>(const_cast<void*>(g0));
+  cudaError_t e = cudaErrorInvalidValue;
+  if (!bin && params->storage == LB_STORAGE_F64) {
+    lbk::Buf<lbk::SF64> B{(double*)f, nullptr, nullptr};
+    e = reduce<lbk::MODEL_LG>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else if (!bin && params->storage == LB_STORAGE_F32) {
+    lbk::Buf<lbk::SF32> B{(float*)f, nullptr, nullptr};
+    e = reduce<lbk::MODEL_LG>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else if (bin && params->storage == LB_STORAGE_F64) {
+    lbk::Buf<lbk::SF64> B{(double*)f, (double*)g, nullptr};
+    e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else if (bin && params->storage == LB_STORAGE_F32) {
+    lbk::Buf<lbk::SF32> B{(float*)f, (float*)g, nullptr};
+    e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else if (bin && params->storage == LB_STORAGE_F16DEV) {
+    lbk::Buf<lbk::SF16> B{(__half*)f, (__half*)g, g0f};
+    e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else {
+    return LB_ERR_ARG;
+  }
+  return e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}

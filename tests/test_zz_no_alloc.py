@@ -1,0 +1,91 @@
+"""lb_filled_length_noalloc against lb_filled_length (needs a GPU).
+
+The allocation-free entry point serves callers that cannot allocate device
+memory (a framework that owns all device buffers, a loop that must not call
+cudaMalloc); it keeps its partial sums in a static device array instead of
+context memory.  This file is collected last so that a run stopping at the first
+failure has already run every other test; it passes on its own in a fresh
+process (where its first call resolves the scratch address) and after the rest.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_0911_0459_gb300 import STORAGE_F32, STORAGE_F64, Lattice  # noqa: E402
+from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+MAX_BLOCKS = int(re.search(r"#define\s+LB_NOALLOC_MAX_BLOCKS\s+(\d+)",
+                           open(os.path.join(ROOT, "include", "lb.h")).read()).group(1))
+REL_TOL = 1e-12   # same kernels and summation order as lb_filled_length up to the block count
+
+
+def noalloc_fn():
+    fn = lbmod.library().lb_filled_length_noalloc
+    fn.restype = C.c_int
+    fn.argtypes = [C.POINTER(lbmod.LbGrid), C.POINTER(lbmod.LbWalls), C.POINTER(lbmod.LbParams),
+                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    return fn
+
+
+def device_state(lat, storage):
+    """The lattice's stored state copied into caller-owned device tensors in the library layout."""
+    f, g = lat.populations(rested=False)
+    dt = torch.float64 if storage == STORAGE_F64 else torch.float32
+    fd = torch.tensor(f, dtype=dt, device="cuda").contiguous()
+    gd = torch.tensor(g, dtype=dt, device="cuda").contiguous() if g is not None else None
+    return fd, gd
+
+
+def call(lat, fd, gd, nblocks, out):
+    fn = noalloc_fn()
+    stream = torch.cuda.current_stream()
+    st = fn(C.byref(lat.grid), C.byref(lat.walls), C.byref(lat.params), C.c_void_p(fd.data_ptr()),
+            C.c_void_p(gd.data_ptr() if gd is not None else 0), None, int(nblocks),
+            C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+    return st
+
+
+def check(got, ref):
+    for k, v in zip(("l", "l_vol", "mass", "phi_sum"), got):
+        r = ref[k]
+        assert abs(v - r) <= REL_TOL * max(1.0, abs(r)), (k, v, r)
+
+
+def test_noalloc_matches_filled_length_on_two_calls_in_a_row():
+    binary = W.Capillary("na", 300, 36, 60, 230, 4, 28, 20, 10, W.binary_params(nu_l=0.5, nu_g=0.05),
+                         theta_deg=50.0)
+    lg = W.config_lg_256x32()
+    a = Lattice.from_workload(binary, storage=STORAGE_F32)
+    a.step(137)
+    b = Lattice.from_workload(lg)
+    b.step(91)
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    # first call: the largest block count the scratch allows
+    fa, ga = device_state(a, STORAGE_F32)
+    assert call(a, fa, ga, MAX_BLOCKS, out) == lbmod.LB_OK
+    torch.cuda.synchronize()
+    check(out.cpu().numpy(), a.filled_length())
+    # second call on another lattice with few blocks: stale partials of the first
+    # call beyond its block count must not leak into the result
+    fb, _ = device_state(b, STORAGE_F64)
+    out2 = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    assert call(b, fb, None, 37, out2) == lbmod.LB_OK
+    torch.cuda.synchronize()
+    check(out2.cpu().numpy(), b.filled_length())
+    # block counts beyond the scratch are refused
+    assert call(a, fa, ga, MAX_BLOCKS + 1, out) == lbmod.LB_ERR_ARG
+    assert call(a, fa, ga, 0, out) == lbmod.LB_ERR_ARG
+    a.close()
+    b.close()
