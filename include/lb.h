@@ -160,6 +160,13 @@ long lb_fluid_nodes(const lb_ctx *ctx);
 lb_status lb_set_tile(lb_ctx *ctx, int tile_x, int tile_y);
 lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
 
+/* Choose the step kernel: 0 = automatic (the staged kernel whenever nx % 8 ==
+ * 0, else the sliding-window kernel), 1 = sliding-window kernel (rows held in
+ * registers), 2 = staged kernel (rows brought into shared memory by bulk
+ * copies; needs nx % 8 == 0).  Both compute the same update bit for bit.
+ * Invalidates the captured step graph. */
+lb_status lb_set_kernel(lb_ctx *ctx, int variant);
+
 /* Time each candidate tile on this lattice (the state is saved and restored)
  * and keep the fastest.  Returns the choice and its time per step in
  * microseconds.  Waits for the stream. */

@@ -40,6 +40,8 @@ struct lb_ctx {
   double* partials;
   double* red_out;
   int tile_x, tile_y;
+  int kernel;   // 0 auto, 1 sliding window, 2 staged
+  int* errflag; // device error word written by the staged kernel
   cudaGraphExec_t gexec;
   int poisoned;
   char err[512];
@@ -127,7 +129,21 @@ static OpArgs base_args(const lb_ctx* c) {
   a.thr = p.model == LB_MODEL_LIQUID_GAS ? 0.5 * (p.rho_l + p.rho_g) : 0.0;
   a.bx = c->tile_x;
   a.yc = c->tile_y;
+  a.staged = c->kernel == 2 || (c->kernel == 0 && c->grid.nx % 8 == 0);
+  a.err = c->errflag;
   return a;
+}
+
+// After a synchronisation: a device-side wait that gave up poisons the context.
+static lb_status check_device_error(lb_ctx* c) {
+  int h = 0;
+  CK(cudaMemcpy(&h, c->errflag, sizeof h, cudaMemcpyDeviceToHost));
+  if (h) {
+    c->poisoned = 1;
+    set_err(c, "a device-side wait of the step kernel timed out (state is unreliable)");
+    return LB_ERR_TIMEOUT;
+  }
+  return LB_OK;
 }
 
 static lb_status launch_one(lb_ctx* c, cudaStream_t s, int from) {
@@ -300,7 +316,9 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
   }
   c->partials = (double*)dev_alloc_owned(c, kRedParts * 3 * sizeof(double));
   c->red_out = (double*)dev_alloc_owned(c, 4 * sizeof(double));
-  if (!c->partials || !c->red_out) {
+  c->errflag = (int*)dev_alloc_owned(c, 256);
+  if (c->errflag && cudaMemsetAsync(c->errflag, 0, 256, c->stream) != cudaSuccess) c->errflag = NULL;
+  if (!c->partials || !c->red_out || !c->errflag) {
     set_err(NULL, "device allocation failed");
     lb_destroy(c);
     return LB_ERR_NOMEM;
@@ -406,6 +424,8 @@ lb_status lb_filled_length(lb_ctx* c, double* l_centre, double* l_vol, double* m
   double h[4];
   CK(cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  lb_status dst = check_device_error(c);
+  if (dst != LB_OK) return dst;
   if (l_centre) *l_centre = h[0];
   if (l_vol) *l_vol = h[1];
   if (mass) *mass = h[2];
@@ -466,6 +486,19 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
 lb_status lb_sync(lb_ctx* c) {
   if (!c) return LB_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
+  return check_device_error(c);
+}
+
+lb_status lb_set_kernel(lb_ctx* c, int variant) {
+  if (!c) return LB_ERR_ARG;
+  if (variant < 0 || variant > 2) return set_err(c, "kernel variant must be 0, 1 or 2"), LB_ERR_ARG;
+  if (variant == 2 && c->grid.nx % 8 != 0)
+    return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
+  if (variant != c->kernel) {
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+  }
+  c->kernel = variant;
   return LB_OK;
 }
 

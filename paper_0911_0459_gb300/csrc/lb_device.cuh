@@ -52,6 +52,8 @@ __device__ __forceinline__ float wstd(int i) {
 struct SF64 {
   using T = double;
   using A = double;
+  __device__ static A pf(const T* f, int W, int c, int i) { return f[i * W + c]; }
+  __device__ static A pg(const T* g, const float*, int W, int c, int i) { return g[i * W + c]; }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) { return __ldg(f + i * N + n); }
   __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) { f[i * N + n] = v; }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
@@ -63,6 +65,8 @@ struct SF64 {
 struct SF32 {
   using T = float;
   using A = float;
+  __device__ static A pf(const T* f, int W, int c, int i) { return f[i * W + c]; }
+  __device__ static A pg(const T* g, const float*, int W, int c, int i) { return g[i * W + c]; }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) { return __ldg(f + i * N + n); }
   __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) { f[i * N + n] = v; }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
@@ -74,6 +78,11 @@ struct SF32 {
 struct SF16 {
   using T = __half;
   using A = float;
+  // plain loads (shared memory): planes of W elements
+  __device__ static A pf(const T* f, int W, int c, int i) { return __half2float(f[i * W + c]) + wstd(i); }
+  __device__ static A pg(const T* g, const float* g0, int W, int c, int i) {
+    return i == 0 ? g0[c] : __half2float(g[(i - 1) * W + c]);
+  }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) {
     return __half2float(__ldg(f + i * N + n)) + wstd(i);
   }
@@ -256,6 +265,87 @@ __host__ __device__ constexpr int EXd(int i) { return (i == 1 || i == 5 || i == 
 __host__ __device__ constexpr int EYd(int i) { return (i == 3 || i == 5 || i == 7) ? 1 : ((i == 4 || i == 6 || i == 8) ? -1 : 0); }
 __host__ __device__ constexpr int OPPd(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+// Reciprocal, correctly rounded (equal to 1/v) in both precisions.
+__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_rn(double v) { return 1.0 / v; }
+
+// Per-node update shared by both step kernels: wall ghosts and rest rule (for
+// boundary nodes), stencils, local thermodynamics, equilibria and the
+// moment-space collision.  vr/vp: 3x3 rho/phi neighbourhoods (raw values at
+// solid neighbours), fa/ga: the node's stored populations.  Outputs: fs, the
+// post-collision f, and ge = g^eq (post-collision g).
+template <int MODEL, typename A>
+__device__ __forceinline__ void collide_node(const Phys<A>& P, A vr[3][3], A vp[3][3], const bool sol[3][3],
+                                             bool bnd, A fa[9], A fs[9], A ge[9]) {
+  constexpr bool BIN = MODEL == MODEL_BINARY;
+  if (bnd) {
+    apply_ghosts(vr, sol, BIN ? A(0) : P.h);
+    if (BIN) apply_ghosts(vp, sol, P.h);
+    rest(fa);
+  }
+  A rdx, rdy, rlap;
+  stencil3(vr, rdx, rdy, rlap);
+  const A rho = vr[1][1];
+  const A jx = momx(fa), jy = momy(fa);
+  const A inv = rcp_rn(rho);
+  const A ux = jx * inv, uy = jy * inv;
+  A fe[9];
+  A omega;
+  if (BIN) {
+    A pdx, pdy, plap;
+    stencil3(vp, pdx, pdy, plap);
+    const A phi = vp[1][1];
+    const A phi2 = phi * phi;
+    const A p0 = rho * A(1.0 / 3.0) + P.Acoef * (A(-0.5) * phi2 + A(0.75) * phi2 * phi2);
+    const A mu = P.Acoef * (phi2 * phi - phi) - P.kappa * plap;
+    const A nu = local_nu_binary(P, phi);
+    omega = A(2) * rcp_rn(A(6) * nu + A(1));
+    feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * phi * plap, P.kappa, pdx, pdy, rdx, rdy, P.lambda_scale * nu, fe);
+    geq9<A>(phi, ux, uy, A(2) * P.M * mu, ge);
+  } else {
+    const A p0 = rho * P.T * rcp_rn(A(1) - P.b * rho) - P.a * rho * rho;
+    omega = A(2) * rcp_rn(A(6) * P.nu + A(1));
+    feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * rho * rlap, P.kappa, rdx, rdy, rdx, rdy, P.lambda_scale * P.nu, fe);
+  }
+  // stress-mode non-equilibrium relaxed at rate omega; every other mode to f^eq
+  const A c = (A(1) - omega) * A(0.25);
+  const A mxx = c * (((fa[1] + fa[2]) - (fa[3] + fa[4])) - ((fe[1] + fe[2]) - (fe[3] + fe[4])));
+  const A mxy = c * (((fa[5] + fa[6]) - (fa[7] + fa[8])) - ((fe[5] + fe[6]) - (fe[7] + fe[8])));
+  fs[0] = fe[0];
+  fs[1] = fe[1] + mxx; fs[2] = fe[2] + mxx;
+  fs[3] = fe[3] - mxx; fs[4] = fe[4] - mxx;
+  fs[5] = fe[5] + mxy; fs[6] = fe[6] + mxy;
+  fs[7] = fe[7] - mxy; fs[8] = fe[8] - mxy;
+}
+
+// Push streaming from node (col[1], row yy) with bounce-back into solid
+// neighbours.  rowb: y*nx of rows y-1, y, y+1 (wrapped); col: x-1, x, x+1.
+template <int MODEL, class S>
+__device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int rowb[3], const int col[3],
+                                          const bool sol[3][3], bool bnd, const typename S::A fs[9],
+                                          const typename S::A ge[9]) {
+  constexpr bool BIN = MODEL == MODEL_BINARY;
+  if (!bnd) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int dn = rowb[1 + EYd(i)] + col[1 + EXd(i)];
+      S::sf(dst.f, N, (size_t)dn, i, fs[i]);
+      if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, i, ge[i]);
+    }
+  } else {
+    const int self = rowb[1] + col[1];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int ex = EXd(i), ey = EYd(i);
+      const bool back = sol[1 + ey][1 + ex];
+      const int dn = back ? self : rowb[1 + ey] + col[1 + ex];
+      const int di = back ? OPPd(i) : i;
+      S::sf(dst.f, N, (size_t)dn, di, fs[i]);
+      if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, di, ge[i]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- the step
 
 template <int MODEL, class S>
@@ -354,65 +444,11 @@ __device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::
           vr[j][i] = sm.r[slot(y - 1 + j)][tid + i];
           if (BIN) vp[j][i] = sm.p[slot(y - 1 + j)][tid + i];
         }
-      if (bnd) {
-        apply_ghosts(vr, sol, BIN ? A(0) : P.h);
-        if (BIN) apply_ghosts(vp, sol, P.h);
-        rest(fa);
-      }
-      A rdx, rdy, rlap;
-      stencil3(vr, rdx, rdy, rlap);
-      const A rho = vr[1][1];
-      const A jx = momx(fa), jy = momy(fa);
-      const A inv = A(1) / rho;
-      const A ux = jx * inv, uy = jy * inv;
-      A fe[9], ge[9];
-      A omega;
-      if (BIN) {
-        A pdx, pdy, plap;
-        stencil3(vp, pdx, pdy, plap);
-        const A phi = vp[1][1];
-        const A phi2 = phi * phi;
-        const A p0 = rho * A(1.0 / 3.0) + P.Acoef * (A(-0.5) * phi2 + A(0.75) * phi2 * phi2);
-        const A mu = P.Acoef * (phi2 * phi - phi) - P.kappa * plap;
-        const A nu = local_nu_binary(P, phi);
-        omega = A(2) / (A(6) * nu + A(1));
-        feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * phi * plap, P.kappa, pdx, pdy, rdx, rdy,
-                P.lambda_scale * nu, fe);
-        geq9<A>(phi, ux, uy, A(2) * P.M * mu, ge);
-      } else {
-        const A p0 = rho * P.T / (A(1) - P.b * rho) - P.a * rho * rho;
-        omega = A(2) / (A(6) * P.nu + A(1));
-        feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * rho * rlap, P.kappa, rdx, rdy, rdx, rdy,
-                P.lambda_scale * P.nu, fe);
-      }
-      // stress-mode non-equilibrium, relaxed at rate omega; all else to f^eq
-      const A c = (A(1) - omega) * A(0.25);
-      const A mxx = c * (((fa[1] + fa[2]) - (fa[3] + fa[4])) - ((fe[1] + fe[2]) - (fe[3] + fe[4])));
-      const A mxy = c * (((fa[5] + fa[6]) - (fa[7] + fa[8])) - ((fe[5] + fe[6]) - (fe[7] + fe[8])));
-      A fs[9];
-      fs[0] = fe[0];
-      fs[1] = fe[1] + mxx; fs[2] = fe[2] + mxx;
-      fs[3] = fe[3] - mxx; fs[4] = fe[4] - mxx;
-      fs[5] = fe[5] + mxy; fs[6] = fe[6] + mxy;
-      fs[7] = fe[7] - mxy; fs[8] = fe[8] - mxy;
-      // streaming with bounce-back
-      const size_t self = (size_t)yy * nx + x;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int ex = EXd(i), ey = EYd(i);
-        const int o = OPPd(i);
-        size_t dn;
-        int di;
-        if (bnd && sol[1 + ey][1 + ex]) {
-          dn = self;
-          di = o;
-        } else {
-          dn = (size_t)wrapi(yy + ey, ny) * nx + wrapi(x + ex, nx);
-          di = i;
-        }
-        S::sf(dst.f, N, dn, di, fs[i]);
-        if (BIN) S::sg(dst.g, dst.g0, N, dn, di, ge[i]);
-      }
+      A fs[9], ge[9];
+      collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
+      const int rowb[3] = {wrapi(yy - 1, ny) * nx, yy * nx, wrapi(yy + 1, ny) * nx};
+      const int col[3] = {wrapi(x - 1, nx), x, wrapi(x + 1, nx)};
+      push_node<MODEL, S>(dst, N, rowb, col, sol, bnd, fs, ge);
     }
 
     if (more) publish(y + 2, fc, gc, fl_c, hf, hg, hfl);

@@ -23,8 +23,10 @@ struct OpArgs {
   double rho_l, rho_g, thr;
   // buffers
   OpBufs src, dst;
-  // step tile
+  // step tile and kernel variant (0: sliding window, 1: bulk-copy staged)
   int bx, yc;
+  int staged;
+  int* err;      // device error word (a device-side wait gave up)
   // field / population / reduction arguments (device pointers)
   const double *in0, *in1, *in2, *in3;
   double *out0, *out1, *out2, *out3;

@@ -4,6 +4,7 @@
 #include "lb_aux.cuh"
 #include "lb_device.cuh"
 #include "lb_ops.h"
+#include "lb_step_tma.cuh"
 
 namespace lbk {
 
@@ -43,6 +44,28 @@ static cudaError_t launch_step(const OpArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int MODEL, class S, int BX, int NS>
+static cudaError_t launch_staged(const OpArgs& a, cudaStream_t s) {
+  using L = TmaLayout<MODEL, S, BX, NS>;
+  static bool configured = false;  // dynamic shared memory opt-in, once per process
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(step_tma_kernel<MODEL, S, BX, NS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  TmaArgs<MODEL, S> k;
+  k.G = to_geom(a);
+  k.P = to_phys<typename S::A>(a);
+  k.src = to_buf<S>(a.src);
+  k.dst = to_buf<S>(a.dst);
+  k.yc = a.yc;
+  k.err = a.err;
+  dim3 grid((a.nx + BX - 1) / BX, (a.ny + a.yc - 1) / a.yc);
+  step_tma_kernel<MODEL, S, BX, NS><<<grid, BX + 32, L::BYTES, s>>>(k);
+  return cudaGetLastError();
+}
+
 template <int MODEL, class S>
 cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
   using A = typename S::A;
@@ -50,6 +73,13 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
   const size_t N = (size_t)a.nx * a.ny;
   switch (op) {
     case OP_STEP:
+      if (a.staged) {
+        if (a.nx % 8 != 0 || !a.err) return cudaErrorInvalidValue;
+        if (a.bx == 64) return launch_staged<MODEL, S, 64, 4>(a, s);
+        if (a.bx == 128) return launch_staged<MODEL, S, 128, 4>(a, s);
+        if (a.bx == 256) return launch_staged<MODEL, S, 256, 3>(a, s);
+        return cudaErrorInvalidValue;
+      }
       if (a.bx == 64) return launch_step<MODEL, S, 64>(a, s);
       if (a.bx == 128) return launch_step<MODEL, S, 128>(a, s);
       if (a.bx == 256) return launch_step<MODEL, S, 256>(a, s);

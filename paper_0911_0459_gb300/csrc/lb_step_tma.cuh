@@ -1,0 +1,357 @@
+// Fused step kernel with bulk-copy (TMA) staging of the populations and warp
+// specialisation.
+//
+// Same update as step_band in lb_device.cuh (stencils, equilibria, collision,
+// push streaming with bounce-back, rest-on-read), organised for sm_103a:
+//   - a CTA owns BX columns and walks up a band of rows.  One producer warp
+//     brings every row of all 18 population planes (plus 8 halo columns either
+//     side) into a shared-memory ring of NS stages with cp.async.bulk copies,
+//     signalled on a per-stage "full" mbarrier (complete_tx);
+//   - BX/32 consumer warps work independently: each keeps rho/phi of rows
+//     y-1, y, y+1 for its 32 columns in registers, takes the neighbouring
+//     columns by warp shuffles (its edge lanes sum the halo columns from the
+//     stage themselves), collides row y from the stage and pushes the result to
+//     global memory, then arrives on the stage's "empty" mbarrier;
+//   - a consumer warp keeps the populations of a row in registers from the
+//     moment it sums that row, so it releases the stage right away; the
+//     producer refills a stage once every consumer warp has released it, which
+//     keeps NS - 1 rows in flight;
+//     there is no CTA-wide barrier in the main loop;
+//   - destinations are 32-bit offsets from per-row bases; the wall tests use
+//     column flags computed once per thread and row flags once per row.
+// Requires nx % 8 == 0 (16-byte aligned rows for every storage type) and
+// BX % 32 == 0.  Halo columns at the x-wrap come from a second 16-byte-aligned
+// copy of the 8 elements at the other end of the row.
+//
+// Every mbarrier wait gives up after a time limit and records the failure in
+// the error word; the producer waits (also with a limit) for the copies it
+// issued before it exits, so no copy lands in released shared memory.
+#pragma once
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false after the time limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+// 1-D bulk copy global -> shared, completion counted on bar (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <class S>
+struct NGPlanes {
+  static constexpr int value = 9;
+};
+template <>
+struct NGPlanes<SF16> {
+  static constexpr int value = 8;
+};
+
+template <int MODEL, class S, int BX, int NS>
+struct TmaLayout {
+  using T = typename S::T;
+  using A = typename S::A;
+  static constexpr bool BIN = MODEL == MODEL_BINARY;
+  static constexpr bool F16 = sizeof(T) == 2;
+  static constexpr int W = BX + 16;                  // staged columns: xb-8 .. xb+BX+7
+  static constexpr int NF = 9;
+  static constexpr int NG = BIN ? NGPlanes<S>::value : 0;
+  static constexpr int NG0 = (BIN && F16) ? 1 : 0;   // FP32 g_0 plane of the FP16 storage
+  static constexpr size_t STAGE_T = (size_t)(NF + NG) * W * sizeof(T);
+  static constexpr size_t STAGE_G0 = (size_t)NG0 * W * sizeof(float);
+  static constexpr size_t STAGE = ((STAGE_T + STAGE_G0) + 127) / 128 * 128;
+  static constexpr size_t BYTES = NS * STAGE + 2 * NS * 8;
+};
+
+template <int MODEL, class S>
+struct TmaArgs {
+  Geom G;
+  Phys<typename S::A> P;
+  Buf<S> src, dst;
+  int yc;
+  int* err;  // set to 1 when a wait gave up
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int MODEL, class S, int BX, int NS>
+__global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) step_tma_kernel(TmaArgs<MODEL, S> a) {
+  using L = TmaLayout<MODEL, S, BX, NS>;
+  using T = typename S::T;
+  using A = typename S::A;
+  constexpr bool BIN = L::BIN;
+  constexpr int W = L::W;
+  constexpr int NWARPS = BX / 32;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * L::STAGE);
+  uint64_t* empty = full + NS;
+  auto stage_f = [&](int s) { return reinterpret_cast<T*>(smem + s * L::STAGE); };
+  auto stage_g = [&](int s) { return reinterpret_cast<T*>(smem + s * L::STAGE) + 9 * W; };
+  auto stage_g0 = [&](int s) { return reinterpret_cast<float*>(smem + s * L::STAGE + L::STAGE_T); };
+
+  const Geom& G = a.G;
+  const int nx = G.nx, ny = G.ny;
+  const size_t N = (size_t)nx * ny;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int xb = blockIdx.x * BX;
+  const int w = min(BX, nx - xb);     // multiple of 8
+  const int y0 = blockIdx.y * a.yc;
+  const int y1 = min(y0 + a.yc, ny);
+  const int nrows = y1 - y0 + 2;      // rows y0-1 .. y1 are staged
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NWARPS);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == NWARPS) {
+    // ------------------------------------------------------------ producer
+    if (lane != 0) return;
+    const int lo = xb >= 8 ? xb - 8 : 0;
+    const int hi = min(xb + BX + 8, nx);
+    const int ncols = hi - lo;
+    const bool wl = xb == 0;           // left halo wraps to the row end
+    const bool wr = xb + BX + 8 > nx;  // right halo wraps to the row start
+    const int so = lo - (xb - 8);      // stage column of global column lo
+    const int sr = nx - (xb - 8);      // stage column of the right wrap chunk
+    const uint32_t ecols = (uint32_t)(ncols + (wl ? 8 : 0) + (wr ? 8 : 0));
+    const uint32_t total = ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
+    auto planes = [&](const T* base, int nplanes, T* dst0, size_t rowoff, uint64_t* bar) {
+      for (int i = 0; i < nplanes; ++i) {
+        const T* src = base + (size_t)i * N + rowoff;
+        T* d = dst0 + i * W;
+        bulk_g2s(d + so, src + lo, (uint32_t)ncols * sizeof(T), bar);
+        if (wl) bulk_g2s(d, src + (nx - 8), 8 * sizeof(T), bar);
+        if (wr) bulk_g2s(d + sr, src, 8 * sizeof(T), bar);
+      }
+    };
+    // every staged column inside the tube: rows outside the band are all solid
+    // and their populations are never read (ghosts replace them), so they are
+    // not copied
+    int d0 = xb - 8 - G.tube_x0;
+    d0 = ((d0 % nx) + nx) % nx;
+    const bool all_tube = G.tube_len > 0 && d0 + w + 16 <= G.tube_len;
+    bool ok = true;
+    int issued = 0;
+    for (int k = 0; k < nrows && ok; ++k) {
+      const int s = k % NS;
+      if (k >= NS && !mbar_wait(&empty[s], ((k / NS) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      const int yy = wrapi(y0 - 1 + k, ny);
+      if (all_tube && !row_in_band(G, yy)) {
+        mbar_arrive(&full[s]);
+        issued = k + 1;
+        continue;
+      }
+      const size_t rowoff = (size_t)yy * nx;
+      mbar_arrive_expect_tx(&full[s], total);
+      planes(a.src.f, L::NF, stage_f(s), rowoff, &full[s]);
+      if (BIN) planes(a.src.g, L::NG, stage_g(s), rowoff, &full[s]);
+      if (L::NG0) {
+        const float* src = a.src.g0 + rowoff;
+        float* d = stage_g0(s);
+        bulk_g2s(d + so, src + lo, (uint32_t)ncols * 4u, &full[s]);
+        if (wl) bulk_g2s(d, src + (nx - 8), 32u, &full[s]);
+        if (wr) bulk_g2s(d + sr, src, 32u, &full[s]);
+      }
+      issued = k + 1;
+    }
+    if (!ok) atomicExch(a.err, 1);
+    // stay until every copy issued by this CTA has landed (bounded)
+    const unsigned long long t0 = globaltimer_ns();
+    for (int k = max(0, issued - NS); k < issued; ++k)
+      while (!mbar_try_wait(&full[k % NS], (k / NS) & 1) && globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  const int c0 = xb + warp * 32;      // first column of this warp
+  const int x = c0 + lane;
+  const bool act = x < xb + w;
+  const int sc = x - xb + 8;          // stage column of this lane's node
+  // extra column summed by the edge lanes: left neighbour of lane 0, right of lane 31
+  const int sx = lane == 0 ? sc - 1 : sc + 1;
+  const bool edge = lane == 0 || lane == 31;
+
+  auto load_pop = [&](int s, int c, A f[9], A g[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = S::pf(stage_f(s), W, c, i);
+    if (BIN) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = S::pg(stage_g(s), stage_g0(s), W, c, i);
+    }
+  };
+  // rho/phi of this lane's column (and of the edge lane's extra column) in stage s
+  // (f, g receive this lane's populations, kept for the collision of that row)
+  auto sums = [&](int s, A f[9], A g[9], A& r, A& p, A& re, A& pe) {
+    load_pop(s, sc, f, g);
+    r = sum9(f);
+    p = BIN ? sum9(g) : A(0);
+    if (edge) {
+      A fe[9], ge[9];
+      load_pop(s, sx, fe, ge);
+      re = sum9(fe);
+      pe = BIN ? sum9(ge) : A(0);
+    }
+  };
+
+  // loop-invariant column data
+  const int xm = x == 0 ? nx - 1 : x - 1;
+  const int xp = x + 1 >= nx ? 0 : x + 1;
+  const bool tubed = G.tube_len > 0;
+  bool tc[3];
+  tc[0] = tubed && act && col_in_tube(G, xm);
+  tc[1] = tubed && act && col_in_tube(G, x);
+  tc[2] = tubed && act && col_in_tube(G, xp);
+  const int col[3] = {xm, x, xp};
+  const bool warp_tube = __any_sync(0xffffffffu, tc[0] || tc[1] || tc[2]);
+
+  // rows k-1, k, k+1 of rho, phi and the edge lanes' extra column
+  A r[3] = {A(0), A(0), A(0)}, p[3] = {A(0), A(0), A(0)}, re[3] = {A(0), A(0), A(0)},
+    pe[3] = {A(0), A(0), A(0)};
+  bool failed = false;
+  A fa[9], ga[9];  // populations of the row to collide next
+  // prologue: rows y0 - 1 (k = 0, stencil halo only) and y0 (k = 1)
+  for (int k = 0; k < 2; ++k) {
+    if (!mbar_wait(&full[k], 0)) {
+      failed = true;
+      break;
+    }
+    sums(k, fa, ga, r[k + 1], p[k + 1], re[k + 1], pe[k + 1]);
+    // the populations are in registers now: the stage can be refilled
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[k]);
+  }
+
+  for (int y = y0; y < y1 && !failed; ++y) {
+    const int kc = y - y0 + 1;  // staged index of row y
+    const int sn = (kc + 1) % NS;
+    // shift the row window and add row y + 1
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      r[j] = r[j + 1]; p[j] = p[j + 1]; re[j] = re[j + 1]; pe[j] = pe[j + 1];
+    }
+    if (!mbar_wait(&full[sn], ((kc + 1) / NS) & 1)) {
+      failed = true;
+      break;
+    }
+    A fn[9], gn[9];
+    sums(sn, fn, gn, r[2], p[2], re[2], pe[2]);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[sn]);
+    // 3x3 neighbourhoods through shuffles (edge lanes use their extra column)
+    A vr[3][3], vp[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const A rl = __shfl_up_sync(0xffffffffu, r[j], 1), rr = __shfl_down_sync(0xffffffffu, r[j], 1);
+      vr[j][0] = lane == 0 ? re[j] : rl;
+      vr[j][1] = r[j];
+      vr[j][2] = lane == 31 ? re[j] : rr;
+      if (BIN) {
+        const A pl = __shfl_up_sync(0xffffffffu, p[j], 1), pr = __shfl_down_sync(0xffffffffu, p[j], 1);
+        vp[j][0] = lane == 0 ? pe[j] : pl;
+        vp[j][1] = p[j];
+        vp[j][2] = lane == 31 ? pe[j] : pr;
+      }
+    }
+    const int yy = wrapi(y, ny);
+    const int ym = yy == 0 ? ny - 1 : yy - 1;
+    const int yp = yy + 1 >= ny ? 0 : yy + 1;
+    const bool rb[3] = {row_in_band(G, ym), row_in_band(G, yy), row_in_band(G, yp)};
+    const bool fluid = act && !(tc[1] && !rb[1]);
+    // walls can touch this warp's nodes only if it has tube columns and one of the
+    // three rows leaves the band (warp-uniform)
+    const bool walls = warp_tube && !(rb[0] && rb[1] && rb[2]);
+    if (fluid) {
+      bool sol[3][3];
+      bool bnd = false;
+      if (walls) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            sol[j][i] = tc[i] && !rb[j];
+            bnd = bnd || sol[j][i];
+          }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) sol[j][i] = false;
+      }
+      A fs[9], ge[9];
+      collide_node<MODEL, A>(a.P, vr, vp, sol, bnd, fa, fs, ge);
+      const int rowb[3] = {ym * nx, yy * nx, yp * nx};
+      push_node<MODEL, S>(a.dst, N, rowb, col, sol, bnd, fs, ge);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      fa[i] = fn[i];
+      if (BIN) ga[i] = gn[i];
+    }
+  }
+  if (failed && lane == 0) atomicExch(a.err, 1);
+}
+
+}  // namespace lbk

@@ -83,6 +83,7 @@ def library():
         "lb_time": (C.c_long, [vp]),
         "lb_fluid_nodes": (C.c_long, [vp]),
         "lb_set_tile": (C.c_int, [vp, C.c_int, C.c_int]),
+        "lb_set_kernel": (C.c_int, [vp, C.c_int]),
         "lb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "lb_autotune": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "lb_last_error": (C.c_char_p, [vp]),
@@ -98,7 +99,7 @@ def library():
 def exported_symbols():
     return ["lb_create", "lb_destroy", "lb_init_fields", "lb_step", "lb_fields", "lb_filled_length",
             "lb_get_populations", "lb_set_populations", "lb_sync", "lb_time", "lb_fluid_nodes",
-            "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error"]
+            "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel"]
 
 
 class _TorchAllocator:
@@ -275,6 +276,10 @@ class Lattice:
 
     def set_tile(self, tx, ty):
         _check(library().lb_set_tile(self.h, int(tx), int(ty)), self.h)
+
+    def set_kernel(self, variant):
+        """0 automatic, 1 sliding-window kernel, 2 staged (bulk-copy) kernel."""
+        _check(library().lb_set_kernel(self.h, int(variant)), self.h)
 
     def tile(self):
         a, b = C.c_int(), C.c_int()
