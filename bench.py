@@ -113,7 +113,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lb_device.cuh",):
+    for f in ("lb_device.cuh", "lb_step_tma.cuh"):
         h.update(open(os.path.join(ROOT, "paper_0911_0459_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -132,7 +132,7 @@ def ncu_traffic(kind):
         return None
 
 
-def cpu_baseline(sample_steps=300):
+def cpu_baseline(sample_steps=1000):
     """The FP64 oracle on the 1024 x 64 crop of the same capillary (single thread)."""
     import oracle
     cap = W.config_binary_crop_1024x64()
@@ -168,6 +168,49 @@ def run_reference(args, rank, world):
                              "sample": f"{args.steps} steps of the 1024x64 crop, FP64, 1 thread"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batched_vs_sequential(torch, Lattice, steps, n=256):
+    """The seeded sweep of 256 uneven binary capillaries (H 16..128, tube 1024..8192,
+    ratios 1..100, 30..80 degrees), FP32: one persistent CUDA-graph launch per
+    sampled run for all capillaries against one lattice per capillary run in
+    turn, both with l(t) sampled 4 times over `steps` steps."""
+    from paper_0911_0459_gb300 import Batch
+    caps = W.sweep(seed=0, n=n)
+    at = [steps // 4, steps // 2, 3 * steps // 4, steps]
+    b = Batch(caps)
+    tx, ty, _ = b.autotune(steps=2)
+    b.run_sampled([2])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = b.run_sampled(at)
+    t_batch = time.perf_counter() - t0
+    fluid = b.fluid_nodes()
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    t_seq = 0.0
+    for c in caps:
+        lat = Lattice.from_workload(c)
+        lat.step(2)
+        lat.filled_length()
+        t0 = time.perf_counter()
+        prev = 0
+        for s in at:
+            lat.step(s - prev)
+            lat.filled_length()
+            prev = s
+        t_seq += time.perf_counter() - t0
+        lat.close()
+    cs_batch = n * steps / t_batch
+    cs_seq = n * steps / t_seq
+    return {"capillary_steps_per_s": cs_batch, "sequential_capillary_steps_per_s": cs_seq,
+            "speedup_vs_one_lattice_per_run": cs_batch / cs_seq,
+            "capillaries_per_s_at_20k_steps": cs_batch / 20000.0,
+            "sequential_capillaries_per_s_at_20k_steps": cs_seq / 20000.0,
+            "GLUPS_batched": fluid * steps / t_batch / 1e9, "fluid_nodes": fluid, "steps": steps,
+            "tile": [tx, ty], "l_finite": bool(np.isfinite(out).all()),
+            "what": f"{steps} steps with 4 l(t) samples, wall clock, FP32"}
 
 
 def timed_steps(lat, torch, K, red_every):
@@ -207,6 +250,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="BX,YC: fixed step-kernel tile instead of autotuning")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16dev"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep secondary metric")
+    ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--profile", action="store_true",
                     help="only the large capillary: warm-up then --steps steps (for ncu captures)")
     args = ap.parse_args()
@@ -235,6 +280,7 @@ def main():
         lat.set_tile(tx, ty)
     else:
         tx, ty, us_tuned = lat.autotune()
+    kernel_variant = lat.kernel()
     fluid = lat.fluid_nodes
     if args.profile:
         lat.step(args.warmup)
@@ -282,7 +328,12 @@ def main():
     barrier()
     t0 = time.perf_counter()
     lat.init_fields(*host_in)
-    lat.step(args.steps)
+    done = 0
+    while done < args.steps:
+        n = min(RED_EVERY, args.steps - done)
+        lat.step(n)
+        lat.filled_length()
+        done += n
     st = L.lb_fields(lat.h, *[a.ctypes.data_as(ctypes.c_void_p) for a in host_out])
     assert st == 0
     e2e_s = time.perf_counter() - t0
@@ -293,7 +344,8 @@ def main():
     e2e = {"value": world * fluid * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 4 * 8 * cap.nx * cap.ny / args.steps,
            "d2h_bytes_per_step": 4 * 8 * cap.nx * cap.ny / args.steps,
-           "what": "lb_init_fields(host) + lb_step(K) + lb_fields(host), pinned buffers"}
+           "what": "lb_init_fields(host) + K steps with lb_filled_length every 100 + lb_fields(host), "
+                   "pinned buffers, wall clock"}
 
     # secondary numbers on the same GPU (not the headline)
     secondary = {}
@@ -326,6 +378,11 @@ def main():
         l1.close()
     except Exception as ex:  # secondary numbers never block the headline line
         secondary["error"] = repr(ex)
+    if not args.no_batch:
+        try:
+            secondary["batched_sweep_256"] = batched_vs_sequential(torch, Lattice, args.batch_steps)
+        except Exception as ex:
+            secondary["batched_error"] = repr(ex)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -344,7 +401,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "step_kernel<binary, FP32>", "bytes_per_lu": bytes_per_lu,
+                         "kernel": ("step_tma_kernel" if kernel_variant == 2 else "step_kernel") +
+                                   "<binary, FP32>", "bytes_per_lu": bytes_per_lu,
                          "peak_source": f"{peak_kind} copy bandwidth",
                          "us_per_launch": 1e3 * per_launch_ms},
             "gpu_launches": launches,

@@ -166,15 +166,69 @@ lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
  * copies; needs nx % 8 == 0).  Both compute the same update bit for bit.
  * Invalidates the captured step graph. */
 lb_status lb_set_kernel(lb_ctx *ctx, int variant);
+/* The kernel variant in use (1 or 2; automatic selection resolved). */
+lb_status lb_get_kernel(const lb_ctx *ctx, int *variant);
 
-/* Time each candidate tile on this lattice (the state is saved and restored)
- * and keep the fastest.  Returns the choice and its time per step in
+/* Time each candidate kernel variant and tile on this lattice (the state is
+ * saved and restored) and keep the fastest.  Returns the choice and its time per step in
  * microseconds.  Waits for the stream. */
 lb_status lb_autotune(lb_ctx *ctx, int *tile_x, int *tile_y, double *us_per_step);
 
 /* Description of the last error on ctx (or of the last failed lb_create when
  * ctx is NULL).  Never NULL. */
 const char *lb_last_error(const lb_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Batched sweeps: many binary capillaries of different sizes and parameters
+ * advanced together by one persistent kernel (every lattice of a batch takes
+ * the same number of steps).  The paper runs its capillaries one at a time; a
+ * batch exists to fill the GPU with the parameter sweeps behind Figs. 5 and 6
+ * and behind the l(t) surrogate.  Each lattice evolves exactly as it would in
+ * its own lb_ctx with the same parameters (bit for bit).
+ * ------------------------------------------------------------------------ */
+typedef struct lb_batch lb_batch;
+
+/* n lattices, each described as for lb_create (all binary, one common
+ * storage), each set to the default initial state.  *out set only on LB_OK. */
+lb_status lb_batch_create(int n, const lb_grid *grids, const lb_walls *walls, const lb_params *params,
+                          const lb_alloc *alloc, void *stream, lb_batch **out);
+void lb_batch_destroy(lb_batch *b);
+
+/* Advance every lattice by n steps: one cooperative persistent launch whose
+ * CTAs take the tiles of all lattices in turn and meet at a grid barrier after
+ * each step.  A barrier that does not complete within its time limit makes the
+ * next call that waits return LB_ERR_TIMEOUT.  Asynchronous. */
+lb_status lb_batch_step(lb_batch *b, long n);
+
+/* out[i*4 + k] = {l_centre, l_vol, mass, phi_sum} of lattice i (definitions as
+ * in lb_filled_length).  Waits for the stream. */
+lb_status lb_batch_lengths(lb_batch *b, double *out);
+
+/* Run to each of nsamples step counts at[k] (counted from now, non-decreasing)
+ * and record the four reductions of every lattice there: out[(i*nsamples + k)*4
+ * + j].  The whole sequence (persistent launches and reductions) is captured
+ * as one CUDA graph and launched once.  Waits for the stream. */
+lb_status lb_batch_run_sampled(lb_batch *b, int nsamples, const long *at, double *out);
+
+/* Populations of lattice i, as lb_get_populations. */
+lb_status lb_batch_populations(lb_batch *b, int i, double *f, double *g, int rested);
+
+/* Tile of the persistent kernel (tile_x = 64, 128, 256 threads along x, tile_y
+ * rows), and a tuner that times every candidate on the batch itself for
+ * 2*steps steps each (this advances the state). */
+lb_status lb_batch_set_tile(lb_batch *b, int tile_x, int tile_y);
+lb_status lb_batch_autotune(lb_batch *b, int steps, int *tile_x, int *tile_y, double *ms_per_step);
+
+/* Grid-barrier settings: the wait limit in seconds (default 2) and a number of
+ * arrivals that never come.  A nonzero absent_blocks makes every barrier wait
+ * run out (failure injection on the host, for tests): the kernel returns, the
+ * state is unreliable and the next waiting call returns LB_ERR_TIMEOUT. */
+lb_status lb_batch_set_barrier(lb_batch *b, unsigned int absent_blocks, double limit_seconds);
+
+long lb_batch_time(const lb_batch *b);
+/* Fluid nodes of lattice i, or of the whole batch for i < 0. */
+long lb_batch_fluid_nodes(const lb_batch *b, int i);
+const char *lb_batch_last_error(const lb_batch *b);
 
 /* ------------------------------------------------------------------------
  * Allocation-free reductions.  The paper has no counterpart: this entry point

@@ -1,0 +1,598 @@
+// Host side of the batched capillary sweep (lb_batch_* in include/lb.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "lb.h"
+#include "lb_batch.cuh"
+#include "lb_ops.h"
+
+using namespace lbk;
+
+namespace {
+
+thread_local char g_batch_create_err[512] = "";
+constexpr unsigned long long kDefaultLimitNs = 2000000000ull;
+
+}  // namespace
+
+struct lb_batch {
+  int n;
+  int storage;
+  std::vector<lb_grid> grids;
+  std::vector<lb_walls> walls;
+  std::vector<lb_params> params;
+  std::vector<size_t> off_f, off_g, off_g0;
+  std::vector<long> fluid;
+  cudaStream_t stream;
+  cudaStream_t cap;
+  lb_alloc alloc;
+  int have_alloc;
+  void* f[2];
+  void* g[2];
+  float* g0[2];
+  void* d_caps;
+  TileDesc* d_tiles;
+  int ntiles;
+  GridBarrier* d_bar;
+  int* d_err;
+  double* d_out;
+  size_t out_cap;  // doubles
+  int parity;
+  long t;
+  int tile_x, tile_y;
+  int grid_blocks;
+  unsigned int extra_arrivals;
+  unsigned long long limit_ns;
+  int poisoned;
+  int graph_fallbacks;
+  char err[512];
+  std::vector<void*> owned;
+};
+
+static void berr(lb_batch* b, const char* fmt, ...) {
+  char* dst = b ? b->err : g_batch_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 512, fmt, ap);
+  va_end(ap);
+}
+
+#define BCK(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      berr(b, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);     \
+      return LB_ERR_CUDA;                                                                      \
+    }                                                                                          \
+  } while (0)
+
+static void* balloc(lb_batch* b, size_t bytes) {
+  void* p = NULL;
+  if (b->have_alloc) {
+    p = b->alloc.malloc_fn(bytes, (void*)b->stream, b->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = NULL;
+  }
+  if (p) b->owned.push_back(p);
+  return p;
+}
+
+static void bfree_all(lb_batch* b) {
+  for (void* p : b->owned) {
+    if (b->have_alloc)
+      b->alloc.free_fn(p, (void*)b->stream, b->alloc.user);
+    else
+      cudaFree(p);
+  }
+  b->owned.clear();
+}
+
+static size_t elem_size(int storage) { return storage == LB_STORAGE_F64 ? 8 : (storage == LB_STORAGE_F32 ? 4 : 2); }
+
+static int solid_h(const lb_grid& g, const lb_walls& w, int x, int y) {
+  if (w.tube_len <= 0) return 0;
+  int dx = ((x - w.tube_x0) % g.nx + g.nx) % g.nx;
+  int dy = ((y - w.tube_y0) % g.ny + g.ny) % g.ny;
+  return dx < w.tube_len && dy >= w.tube_h;
+}
+
+// Op arguments addressing lattice i of buffer k (for the per-lattice kernels).
+static OpArgs lattice_args(const lb_batch* b, int i, int k) {
+  OpArgs a;
+  memset(&a, 0, sizeof a);
+  const lb_grid& g = b->grids[i];
+  const lb_walls& w = b->walls[i];
+  const lb_params& p = b->params[i];
+  a.nx = g.nx; a.ny = g.ny;
+  a.tube_x0 = w.tube_x0; a.tube_len = w.tube_len; a.tube_y0 = w.tube_y0; a.tube_h = w.tube_h;
+  a.kappa = p.kappa; a.a = p.a; a.b = p.b; a.T = p.T; a.Acoef = p.A; a.M = p.M;
+  a.nu_l = p.nu_l; a.nu_g = p.nu_g; a.nu = p.nu; a.lambda_scale = p.lambda_scale; a.h = w.wall_grad;
+  a.rho_l = p.rho_l; a.rho_g = p.rho_g;
+  const size_t el = elem_size(b->storage);
+  OpBufs ob;
+  ob.f = (char*)b->f[k] + b->off_f[i] * el;
+  ob.g = (char*)b->g[k] + b->off_g[i] * el;
+  ob.g0 = b->g0[k] ? b->g0[k] + b->off_g0[i] : NULL;
+  a.src = ob;
+  a.dst = ob;
+  return a;
+}
+
+static OpsFn batch_ops(int storage) {
+  return storage == LB_STORAGE_F64 ? ops_bin_f64 : (storage == LB_STORAGE_F32 ? ops_bin_f32 : ops_bin_f16);
+}
+
+static lb_status init_lattice(lb_batch* b, int i) {
+  const lb_grid& g = b->grids[i];
+  const lb_walls& w = b->walls[i];
+  const lb_params& p = b->params[i];
+  const size_t N = (size_t)g.nx * g.ny;
+  std::vector<double> host(4 * N, 0.0);
+  const double wdt = sqrt(2.0);
+  const double xa = w.gas_cols, xb = (double)w.tube_x0 + p.l0;
+  for (int y = 0; y < g.ny; ++y)
+    for (int x = 0; x < g.nx; ++x) {
+      const size_t n = (size_t)y * g.nx + x;
+      const double chi = 0.5 * (tanh((x - xa) / wdt) - tanh((x - xb) / wdt));
+      const int sol = solid_h(g, w, x, y);
+      host[n] = sol ? 0.0 : 1.0;
+      host[3 * N + n] = sol ? 0.0 : 2.0 * chi - 1.0;
+    }
+  double* d = NULL;
+  if (b->have_alloc)
+    d = (double*)b->alloc.malloc_fn(4 * N * sizeof(double), (void*)b->stream, b->alloc.user);
+  else if (cudaMalloc((void**)&d, 4 * N * sizeof(double)) != cudaSuccess)
+    d = NULL;
+  if (!d) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  cudaError_t e = cudaMemcpyAsync(d, host.data(), 4 * N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  OpArgs a = lattice_args(b, i, 0);
+  a.in0 = d; a.in1 = d + N; a.in2 = d + 2 * N; a.in3 = d + 3 * N;
+  if (e == cudaSuccess) e = batch_ops(b->storage)(OP_INIT, a, b->stream);
+  cudaError_t e2 = cudaStreamSynchronize(b->stream);
+  if (b->have_alloc)
+    b->alloc.free_fn(d, (void*)b->stream, b->alloc.user);
+  else
+    cudaFree(d);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return berr(b, "init of lattice %d failed: %s", i, cudaGetErrorString(e)), LB_ERR_CUDA;
+  return LB_OK;
+}
+
+static lb_status build_tiles(lb_batch* b) {
+  std::vector<TileDesc> tiles;
+  for (int i = 0; i < b->n; ++i) {
+    const lb_grid& g = b->grids[i];
+    const lb_walls& w = b->walls[i];
+    for (int y0 = 0; y0 < g.ny; y0 += b->tile_y)
+      for (int xb = 0; xb < g.nx; xb += b->tile_x) {
+        const int y1 = std::min(y0 + b->tile_y, g.ny);
+        const int x1 = std::min(xb + b->tile_x, g.nx);
+        bool any_fluid = false;
+        for (int y = y0; y < y1 && !any_fluid; ++y)
+          for (int x = xb; x < x1 && !any_fluid; ++x) any_fluid = !solid_h(g, w, x, y);
+        if (any_fluid) tiles.push_back(TileDesc{i, xb, y0, y1});
+      }
+  }
+  b->ntiles = (int)tiles.size();
+  if (b->d_tiles) {
+    if (b->have_alloc)
+      b->alloc.free_fn(b->d_tiles, (void*)b->stream, b->alloc.user);
+    else
+      cudaFree(b->d_tiles);
+    b->owned.erase(std::remove(b->owned.begin(), b->owned.end(), (void*)b->d_tiles), b->owned.end());
+  }
+  b->d_tiles = (TileDesc*)balloc(b, std::max<size_t>(1, tiles.size()) * sizeof(TileDesc));
+  if (!b->d_tiles) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  BCK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice,
+                      b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return LB_OK;
+}
+
+template <class S, int BX>
+static cudaError_t launch_batch_t(lb_batch* b, int nsteps, cudaStream_t s) {
+  BatchArgs<S> a;
+  a.caps = (const CapDesc<typename S::A>*)b->d_caps;
+  a.tiles = b->d_tiles;
+  a.ntiles = b->ntiles;
+  a.fa = (typename S::T*)b->f[0]; a.ga = (typename S::T*)b->g[0]; a.g0a = b->g0[0];
+  a.fb = (typename S::T*)b->f[1]; a.gb = (typename S::T*)b->g[1]; a.g0b = b->g0[1];
+  a.nsteps = nsteps;
+  a.parity = b->parity;
+  a.bar = b->d_bar;
+  a.limit_ns = b->limit_ns;
+  a.err = b->d_err;
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S, BX>, BX, 0);
+  if (e != cudaSuccess) return e;
+  int blocks = std::max(1, std::min(per * sms, b->ntiles));
+  b->grid_blocks = blocks;
+  a.expected = (unsigned)blocks + b->extra_arrivals;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(BX);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_step_kernel<S, BX>, a);
+}
+
+template <class S>
+static cudaError_t launch_batch_s(lb_batch* b, int nsteps, cudaStream_t s) {
+  if (b->tile_x == 64) return launch_batch_t<S, 64>(b, nsteps, s);
+  if (b->tile_x == 128) return launch_batch_t<S, 128>(b, nsteps, s);
+  return launch_batch_t<S, 256>(b, nsteps, s);
+}
+
+static cudaError_t launch_batch(lb_batch* b, int nsteps, cudaStream_t s) {
+  if (b->storage == LB_STORAGE_F64) return launch_batch_s<SF64>(b, nsteps, s);
+  if (b->storage == LB_STORAGE_F32) return launch_batch_s<SF32>(b, nsteps, s);
+  return launch_batch_s<SF16>(b, nsteps, s);
+}
+
+template <class S>
+static cudaError_t launch_reduce_s(lb_batch* b, int buf, int nsamples, int col, double* out, cudaStream_t s) {
+  batch_reduce_kernel<S><<<b->n, 1024, 0, s>>>((const CapDesc<typename S::A>*)b->d_caps, b->n,
+                                               (typename S::T*)b->f[buf], (typename S::T*)b->g[buf], b->g0[buf],
+                                               nsamples, col, out);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_reduce(lb_batch* b, int buf, int nsamples, int col, double* out, cudaStream_t s) {
+  if (b->storage == LB_STORAGE_F64) return launch_reduce_s<SF64>(b, buf, nsamples, col, out, s);
+  if (b->storage == LB_STORAGE_F32) return launch_reduce_s<SF32>(b, buf, nsamples, col, out, s);
+  return launch_reduce_s<SF16>(b, buf, nsamples, col, out, s);
+}
+
+template <typename A>
+static void fill_caps(lb_batch* b, std::vector<CapDesc<A>>& caps) {
+  caps.resize(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    const lb_grid& g = b->grids[i];
+    const lb_walls& w = b->walls[i];
+    const lb_params& p = b->params[i];
+    CapDesc<A>& c = caps[i];
+    c.G = Geom{g.nx, g.ny, w.tube_x0, w.tube_len, w.tube_y0, w.tube_h};
+    c.P.kappa = A(p.kappa); c.P.a = A(p.a); c.P.b = A(p.b); c.P.T = A(p.T);
+    c.P.Acoef = A(p.A); c.P.M = A(p.M); c.P.nu_l = A(p.nu_l); c.P.nu_g = A(p.nu_g);
+    c.P.nu = A(p.nu); c.P.lambda_scale = A(p.lambda_scale); c.P.h = A(w.wall_grad);
+    c.off_f = b->off_f[i];
+    c.off_g = b->off_g[i];
+    c.off_g0 = b->off_g0[i];
+    c.thr = 0.0;
+    c.rho_l = p.rho_l;
+    c.rho_g = p.rho_g;
+  }
+}
+
+static lb_status check_err(lb_batch* b) {
+  int h = 0;
+  BCK(cudaMemcpy(&h, b->d_err, sizeof h, cudaMemcpyDeviceToHost));
+  if (h) {
+    b->poisoned = 1;
+    berr(b, "the grid barrier of the persistent kernel timed out (state is unreliable)");
+    return LB_ERR_TIMEOUT;
+  }
+  return LB_OK;
+}
+
+static lb_status ensure_out(lb_batch* b, size_t ndoubles) {
+  if (b->out_cap >= ndoubles) return LB_OK;
+  double* p = (double*)balloc(b, ndoubles * sizeof(double));
+  if (!p) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  b->d_out = p;
+  b->out_cap = ndoubles;
+  return LB_OK;
+}
+
+extern "C" {
+
+lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, const lb_params* params,
+                          const lb_alloc* alloc, void* stream, lb_batch** out) {
+  if (!out || n < 1 || !grids || !walls || !params) return berr(NULL, "invalid arguments"), LB_ERR_ARG;
+  *out = NULL;
+  const int storage = params[0].storage;
+  for (int i = 0; i < n; ++i) {
+    if (params[i].model != LB_MODEL_BINARY) return berr(NULL, "batches hold binary lattices"), LB_ERR_ARG;
+    if (params[i].storage != storage) return berr(NULL, "all lattices of a batch share one storage"), LB_ERR_ARG;
+    const lb_grid& g = grids[i];
+    const lb_walls& w = walls[i];
+    if (g.nx < 3 || g.ny < 3 || (long)g.nx * g.ny > (1L << 31) - 1) return berr(NULL, "lattice %d: bad grid", i), LB_ERR_ARG;
+    if (w.tube_len < 0 || w.tube_len > g.nx) return berr(NULL, "lattice %d: tube_len outside [0, nx]", i), LB_ERR_ARG;
+    if (w.tube_len > 0 && (w.tube_x0 < 0 || w.tube_x0 >= g.nx || w.tube_y0 < 0 || w.tube_y0 >= g.ny ||
+                           w.tube_h < 2 || w.tube_h >= g.ny || (w.tube_len < g.nx && g.nx - w.tube_len < 2)))
+      return berr(NULL, "lattice %d: invalid tube geometry", i), LB_ERR_ARG;
+    if (!(params[i].nu_l > 0) || !(params[i].nu_g > 0) || !(params[i].A > 0) || !(params[i].kappa > 0))
+      return berr(NULL, "lattice %d: invalid binary parameters", i), LB_ERR_ARG;
+  }
+  if (alloc && (!alloc->malloc_fn || !alloc->free_fn)) return berr(NULL, "incomplete allocator"), LB_ERR_ARG;
+  lb_batch* b = new (std::nothrow) lb_batch();
+  if (!b) return berr(NULL, "out of host memory"), LB_ERR_NOMEM;
+  b->n = n;
+  b->storage = storage;
+  b->grids.assign(grids, grids + n);
+  b->walls.assign(walls, walls + n);
+  b->params.assign(params, params + n);
+  b->stream = (cudaStream_t)stream;
+  b->have_alloc = alloc != NULL;
+  if (alloc) b->alloc = *alloc;
+  b->tile_x = 128;
+  b->tile_y = 8;
+  b->limit_ns = kDefaultLimitNs;
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    berr(NULL, "cudaStreamCreate failed");
+    delete b;
+    return LB_ERR_CUDA;
+  }
+  const size_t el = elem_size(storage);
+  const int ng = storage == LB_STORAGE_F16DEV ? 8 : 9;
+  size_t of = 0, og = 0, o0 = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t N = (size_t)grids[i].nx * grids[i].ny;
+    b->off_f.push_back(of);
+    b->off_g.push_back(og);
+    b->off_g0.push_back(o0);
+    of += (9 * N + 63) / 64 * 64;
+    og += (ng * N + 63) / 64 * 64;
+    o0 += (N + 63) / 64 * 64;
+    long fl = 0;
+    for (int y = 0; y < grids[i].ny; ++y)
+      for (int x = 0; x < grids[i].nx; ++x) fl += !solid_h(grids[i], walls[i], x, y);
+    b->fluid.push_back(fl);
+  }
+  for (int k = 0; k < 2; ++k) {
+    b->f[k] = balloc(b, of * el);
+    b->g[k] = balloc(b, og * el);
+    b->g0[k] = storage == LB_STORAGE_F16DEV ? (float*)balloc(b, o0 * sizeof(float)) : NULL;
+    if (!b->f[k] || !b->g[k] || (storage == LB_STORAGE_F16DEV && !b->g0[k])) {
+      snprintf(g_batch_create_err, sizeof g_batch_create_err, "device allocation of the batch state failed");
+      lb_batch_destroy(b);
+      return LB_ERR_NOMEM;
+    }
+  }
+  const size_t capbytes = (size_t)n * std::max(sizeof(CapDesc<double>), sizeof(CapDesc<float>));
+  b->d_caps = balloc(b, capbytes);
+  b->d_bar = (GridBarrier*)balloc(b, 256);
+  b->d_err = (int*)balloc(b, 256);
+  if (!b->d_caps || !b->d_bar || !b->d_err) {
+    snprintf(g_batch_create_err, sizeof g_batch_create_err, "device allocation failed");
+    lb_batch_destroy(b);
+    return LB_ERR_NOMEM;
+  }
+  cudaError_t e = cudaSuccess;
+  if (storage == LB_STORAGE_F64) {
+    std::vector<CapDesc<double>> caps;
+    fill_caps(b, caps);
+    e = cudaMemcpy(b->d_caps, caps.data(), n * sizeof(CapDesc<double>), cudaMemcpyHostToDevice);
+  } else {
+    std::vector<CapDesc<float>> caps;
+    fill_caps(b, caps);
+    e = cudaMemcpy(b->d_caps, caps.data(), n * sizeof(CapDesc<float>), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 256);
+  if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 256);
+  lb_status st = e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+  if (st == LB_OK) st = build_tiles(b);
+  for (int i = 0; i < n && st == LB_OK; ++i) st = init_lattice(b, i);
+  if (st != LB_OK) {
+    snprintf(g_batch_create_err, sizeof g_batch_create_err, "%s", e != cudaSuccess ? cudaGetErrorString(e) : b->err);
+    lb_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return LB_OK;
+}
+
+void lb_batch_destroy(lb_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  bfree_all(b);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+lb_status lb_batch_step(lb_batch* b, long n) {
+  if (!b) return LB_ERR_ARG;
+  if (n < 0 || n > (1L << 30)) return berr(b, "step count out of range"), LB_ERR_ARG;
+  if (b->poisoned) return berr(b, "batch holds a timed-out state"), LB_ERR_STATE;
+  if (n == 0) return LB_OK;
+  BCK(launch_batch(b, (int)n, b->stream));
+  b->parity = (b->parity + (int)(n & 1)) & 1;
+  b->t += n;
+  return LB_OK;
+}
+
+lb_status lb_batch_lengths(lb_batch* b, double* out) {
+  if (!b || !out) return LB_ERR_ARG;
+  lb_status st = ensure_out(b, (size_t)b->n * 4);
+  if (st) return st;
+  BCK(launch_reduce(b, b->parity, 1, 0, b->d_out, b->stream));
+  BCK(cudaMemcpyAsync(out, b->d_out, (size_t)b->n * 4 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return check_err(b);
+}
+
+lb_status lb_batch_run_sampled(lb_batch* b, int nsamples, const long* at, double* out) {
+  if (!b || nsamples < 1 || !at || !out) return LB_ERR_ARG;
+  if (b->poisoned) return berr(b, "batch holds a timed-out state"), LB_ERR_STATE;
+  long prev = 0;
+  for (int k = 0; k < nsamples; ++k) {
+    if (at[k] < prev || at[k] - prev > (1L << 30)) return berr(b, "sample steps must be non-decreasing"), LB_ERR_ARG;
+    prev = at[k];
+  }
+  lb_status st = ensure_out(b, (size_t)b->n * nsamples * 4);
+  if (st) return st;
+  // one graph: for each sample, a persistent launch for the steps since the last
+  // sample and a reduction into that sample's column
+  BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  int parity = b->parity;
+  long t = 0;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < nsamples && e == cudaSuccess; ++k) {
+    const long d = at[k] - t;
+    if (d > 0) {
+      const int save = b->parity;
+      b->parity = parity;
+      e = launch_batch(b, (int)d, b->cap);
+      b->parity = save;
+      parity = (parity + (int)(d & 1)) & 1;
+      t = at[k];
+    }
+    if (e == cudaSuccess) e = launch_reduce(b, parity, nsamples, k, b->d_out, b->cap);
+  }
+  cudaGraph_t graph = NULL;
+  cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  cudaGraphExec_t exec = NULL;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e == cudaSuccess) {
+    e = cudaGraphLaunch(exec, b->stream);
+  } else {
+    // the driver refused the graph: issue the same sequence directly
+    cudaGetLastError();
+    parity = b->parity;
+    t = 0;
+    e = cudaSuccess;
+    for (int k = 0; k < nsamples && e == cudaSuccess; ++k) {
+      const long d = at[k] - t;
+      if (d > 0) {
+        const int save = b->parity;
+        b->parity = parity;
+        e = launch_batch(b, (int)d, b->stream);
+        b->parity = save;
+        parity = (parity + (int)(d & 1)) & 1;
+        t = at[k];
+      }
+      if (e == cudaSuccess) e = launch_reduce(b, parity, nsamples, k, b->d_out, b->stream);
+    }
+    b->graph_fallbacks++;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, b->d_out, (size_t)b->n * nsamples * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                        b->stream);
+  cudaError_t e3 = cudaStreamSynchronize(b->stream);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (e == cudaSuccess) e = e3;
+  if (e != cudaSuccess) return berr(b, "lb_batch_run_sampled: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  b->parity = parity;
+  b->t += t;
+  return check_err(b);
+}
+
+lb_status lb_batch_populations(lb_batch* b, int i, double* f, double* g, int rested) {
+  if (!b || i < 0 || i >= b->n || !f) return LB_ERR_ARG;
+  const size_t N = (size_t)b->grids[i].nx * b->grids[i].ny;
+  double* d = NULL;
+  if (b->have_alloc)
+    d = (double*)b->alloc.malloc_fn(18 * N * sizeof(double), (void*)b->stream, b->alloc.user);
+  else if (cudaMalloc((void**)&d, 18 * N * sizeof(double)) != cudaSuccess)
+    d = NULL;
+  if (!d) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  OpArgs a = lattice_args(b, i, b->parity);
+  a.flag = rested;
+  a.out0 = d;
+  a.out1 = d + 9 * N;
+  cudaError_t e = batch_ops(b->storage)(OP_POPS_OUT, a, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess && g) e = cudaMemcpyAsync(g, d + 9 * N, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  cudaError_t e2 = cudaStreamSynchronize(b->stream);
+  if (b->have_alloc)
+    b->alloc.free_fn(d, (void*)b->stream, b->alloc.user);
+  else
+    cudaFree(d);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return berr(b, "lb_batch_populations: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  return LB_OK;
+}
+
+lb_status lb_batch_set_tile(lb_batch* b, int tile_x, int tile_y) {
+  if (!b) return LB_ERR_ARG;
+  if (tile_x != 64 && tile_x != 128 && tile_x != 256) return berr(b, "tile_x must be 64, 128 or 256"), LB_ERR_ARG;
+  if (tile_y < 1 || tile_y > 4096) return berr(b, "tile_y out of range"), LB_ERR_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  b->tile_x = tile_x;
+  b->tile_y = tile_y;
+  return build_tiles(b);
+}
+
+lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, double* ms_per_step) {
+  if (!b || steps < 1) return LB_ERR_ARG;
+  if (b->poisoned) return LB_ERR_STATE;
+  // tuning runs advance the state: run an even number of steps per candidate and
+  // restore nothing else (callers tune before they start a measured run)
+  const int cx[3] = {64, 128, 256};
+  const int cy[5] = {4, 8, 16, 32, 64};
+  int bx = b->tile_x, by = b->tile_y;
+  float best = 1e30f;
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  lb_status st = LB_OK;
+  for (int i = 0; i < 3 && st == LB_OK; ++i)
+    for (int j = 0; j < 5 && st == LB_OK; ++j) {
+      st = lb_batch_set_tile(b, cx[i], cy[j]);
+      if (st) break;
+      st = lb_batch_step(b, 2);
+      if (st) break;
+      cudaEventRecord(e0, b->stream);
+      st = lb_batch_step(b, 2 * steps);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st == LB_OK && ms < best) {
+        best = ms;
+        bx = cx[i];
+        by = cy[j];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  st = check_err(b);
+  if (st) return st;
+  st = lb_batch_set_tile(b, bx, by);
+  if (st) return st;
+  if (tile_x) *tile_x = bx;
+  if (tile_y) *tile_y = by;
+  if (ms_per_step) *ms_per_step = best / (2.0 * steps);
+  return LB_OK;
+}
+
+lb_status lb_batch_set_barrier(lb_batch* b, unsigned int absent_blocks, double limit_seconds) {
+  if (!b || !(limit_seconds > 0) || limit_seconds > 60) return LB_ERR_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  b->extra_arrivals = absent_blocks;
+  b->limit_ns = (unsigned long long)(limit_seconds * 1e9);
+  BCK(cudaMemset(b->d_bar, 0, 256));
+  return LB_OK;
+}
+
+long lb_batch_time(const lb_batch* b) { return b ? b->t : -1; }
+
+long lb_batch_fluid_nodes(const lb_batch* b, int i) {
+  if (!b) return -1;
+  if (i >= 0) return i < b->n ? b->fluid[i] : -1;
+  long s = 0;
+  for (long v : b->fluid) s += v;
+  return s;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) { return b ? b->err : g_batch_create_err; }
+
+}  // extern "C"

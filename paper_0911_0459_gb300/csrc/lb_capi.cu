@@ -489,6 +489,12 @@ lb_status lb_sync(lb_ctx* c) {
   return check_device_error(c);
 }
 
+lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
+  if (!c || !variant) return LB_ERR_ARG;
+  *variant = c->kernel == 0 ? (c->grid.nx % 8 == 0 ? 2 : 1) : c->kernel;
+  return LB_OK;
+}
+
 lb_status lb_set_kernel(lb_ctx* c, int variant) {
   if (!c) return LB_ERR_ARG;
   if (variant < 0 || variant > 2) return set_err(c, "kernel variant must be 0, 1 or 2"), LB_ERR_ARG;
@@ -542,16 +548,21 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   if (e == cudaSuccess && gb) e = cudaMemcpyAsync(save + fb, cur.g, gb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess && g0b) e = cudaMemcpyAsync(save + fb + gb, cur.g0, g0b, cudaMemcpyDeviceToDevice, c->stream);
   const int cand_x[3] = {64, 128, 256};
-  const int cand_y[6] = {2, 4, 8, 16, 32, 64};
-  int best_x = c->tile_x, best_y = c->tile_y;
+  const int cand_y[7] = {1, 2, 4, 8, 16, 32, 64};
+  const int saved_kernel = c->kernel;
+  int best_x = c->tile_x, best_y = c->tile_y, best_k = saved_kernel;
   float best = 1e30f;
   cudaEvent_t e0 = NULL, e1 = NULL;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const int reps = 10;
+  // kernel variants: the staged kernel only where rows are 16-byte aligned
+  const int nk = c->grid.nx % 8 == 0 ? 2 : 1;
+  for (int ik = 0; ik < nk && e == cudaSuccess && st == LB_OK; ++ik)
   for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
-    for (int iy = 0; iy < 6 && e == cudaSuccess && st == LB_OK; ++iy) {
+    for (int iy = 0; iy < 7 && e == cudaSuccess && st == LB_OK; ++iy) {
       if (cand_y[iy] > c->grid.ny) continue;
+      c->kernel = ik == 0 ? 1 : 2;
       c->tile_x = cand_x[ix];
       c->tile_y = cand_y[iy];
       int from = c->cur;
@@ -566,8 +577,10 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
         best = ms;
         best_x = cand_x[ix];
         best_y = cand_y[iy];
+        best_k = c->kernel;
       }
     }
+  c->kernel = saved_kernel;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   // restore
@@ -578,6 +591,7 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   dev_free(c, save);
   c->tile_x = best_x;
   c->tile_y = best_y;
+  c->kernel = best_k;
   drop_graph(c);
   if (st != LB_OK) return st;
   if (e != cudaSuccess || er != cudaSuccess)

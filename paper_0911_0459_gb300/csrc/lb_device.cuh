@@ -60,6 +60,9 @@ struct SF64 {
     return __ldg(g + i * N + n);
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
+  // L2-coherent loads, for buffers written earlier in the same launch
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i) { return __ldcg(f + i * N + n); }
+  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
 };
 
 struct SF32 {
@@ -73,6 +76,8 @@ struct SF32 {
     return __ldg(g + i * N + n);
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i) { return __ldcg(f + i * N + n); }
+  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
 };
 
 struct SF16 {
@@ -88,6 +93,12 @@ struct SF16 {
   }
   __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) {
     f[i * N + n] = __float2half_rn(v - wstd(i));
+  }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i) {
+    return __half2float(__ldcg(f + i * N + n)) + wstd(i);
+  }
+  __device__ static A lgc(const T* g, const float* g0, size_t N, size_t n, int i) {
+    return i == 0 ? __ldcg(g0 + n) : __half2float(__ldcg(g + (i - 1) * N + n));
   }
   // g_1..g_8 in FP16 planes 0..7; g_0 (which carries phi) in an FP32 plane.
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__ g0, size_t N, size_t n, int i) {
@@ -362,19 +373,21 @@ struct StepSmem {
   typename S::A p[MODEL == MODEL_BINARY ? 4 : 1][BX + 2];
 };
 
-template <int MODEL, class S>
+template <int MODEL, class S, bool COHERENT = false>
 __device__ __forceinline__ void load_node(const Buf<S>& B, size_t N, size_t n, typename S::A f[9],
                                           typename S::A g[9]) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = S::lf(B.f, N, n, i);
+  for (int i = 0; i < 9; ++i) f[i] = COHERENT ? S::lfc(B.f, N, n, i) : S::lf(B.f, N, n, i);
   if (MODEL == MODEL_BINARY) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = S::lg(B.g, B.g0, N, n, i);
+    for (int i = 0; i < 9; ++i) g[i] = COHERENT ? S::lgc(B.g, B.g0, N, n, i) : S::lg(B.g, B.g0, N, n, i);
   }
 }
 
 // Process columns [xb, xb + BX) (clipped to nx) and rows [y0, y1) of one lattice.
-template <int MODEL, class S, int BX>
+// COHERENT loads bypass the non-coherent read path (buffers written earlier in
+// the same launch, as in the persistent batched kernel).
+template <int MODEL, class S, int BX, bool COHERENT = false>
 __device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::A>& P, const Buf<S>& src,
                                           const Buf<S>& dst, int xb, int y0, int y1,
                                           StepSmem<MODEL, S, BX>& sm) {
@@ -410,9 +423,9 @@ __device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::
   auto fetch = [&](int r, A* f, A* g, bool& fluid, bool& hfluid) {
     const int rr = wrapi(r, ny);
     fluid = act && !is_solid(G, x, rr);
-    if (fluid) load_node<MODEL, S>(src, N, (size_t)rr * nx + x, f, g);
+    if (fluid) load_node<MODEL, S, COHERENT>(src, N, (size_t)rr * nx + x, f, g);
     hfluid = hal && !is_solid(G, hx, rr);
-    if (hfluid) load_node<MODEL, S>(src, N, (size_t)rr * nx + hx, hf, hg);
+    if (hfluid) load_node<MODEL, S, COHERENT>(src, N, (size_t)rr * nx + hx, hf, hg);
   };
 
   bool fl_a, fl_b, fl_c, hfl;

@@ -84,9 +84,24 @@ def library():
         "lb_fluid_nodes": (C.c_long, [vp]),
         "lb_set_tile": (C.c_int, [vp, C.c_int, C.c_int]),
         "lb_set_kernel": (C.c_int, [vp, C.c_int]),
+        "lb_get_kernel": (C.c_int, [vp, C.POINTER(C.c_int)]),
         "lb_get_tile": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "lb_autotune": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "lb_last_error": (C.c_char_p, [vp]),
+        "lb_batch_create": (C.c_int, [C.c_int, C.POINTER(LbGrid), C.POINTER(LbWalls), C.POINTER(LbParams),
+                                      C.POINTER(LbAlloc), vp, C.POINTER(vp)]),
+        "lb_batch_destroy": (None, [vp]),
+        "lb_batch_step": (C.c_int, [vp, C.c_long]),
+        "lb_batch_lengths": (C.c_int, [vp, dp]),
+        "lb_batch_run_sampled": (C.c_int, [vp, C.c_int, dp, dp]),
+        "lb_batch_populations": (C.c_int, [vp, C.c_int, dp, dp, C.c_int]),
+        "lb_batch_set_tile": (C.c_int, [vp, C.c_int, C.c_int]),
+        "lb_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_double)]),
+        "lb_batch_set_barrier": (C.c_int, [vp, C.c_uint, C.c_double]),
+        "lb_batch_time": (C.c_long, [vp]),
+        "lb_batch_fluid_nodes": (C.c_long, [vp, C.c_int]),
+        "lb_batch_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -99,7 +114,10 @@ def library():
 def exported_symbols():
     return ["lb_create", "lb_destroy", "lb_init_fields", "lb_step", "lb_fields", "lb_filled_length",
             "lb_get_populations", "lb_set_populations", "lb_sync", "lb_time", "lb_fluid_nodes",
-            "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel"]
+            "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
+            "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
+            "lb_batch_populations", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
+            "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error"]
 
 
 class _TorchAllocator:
@@ -281,6 +299,11 @@ class Lattice:
         """0 automatic, 1 sliding-window kernel, 2 staged (bulk-copy) kernel."""
         _check(library().lb_set_kernel(self.h, int(variant)), self.h)
 
+    def kernel(self):
+        v = C.c_int()
+        _check(library().lb_get_kernel(self.h, C.byref(v)), self.h)
+        return v.value
+
     def tile(self):
         a, b = C.c_int(), C.c_int()
         _check(library().lb_get_tile(self.h, C.byref(a), C.byref(b)), self.h)
@@ -290,3 +313,106 @@ class Lattice:
         a, b, us = C.c_int(), C.c_int(), C.c_double()
         _check(library().lb_autotune(self.h, C.byref(a), C.byref(b), C.byref(us)), self.h)
         return a.value, b.value, us.value
+
+
+def _structs_for(cap, storage=None):
+    """lb_grid / lb_walls / lb_params for a workloads.Capillary description."""
+    p = cap.params
+    if cap.wall_grad is not None:
+        wg = cap.wall_grad
+    elif cap.theta_deg is not None:
+        if p.model != MODEL_BINARY:
+            raise ValueError("liquid-gas workloads must give wall_grad directly")
+        wg = binary_wall_gradient(cap.theta_deg, p.A, p.kappa)
+    else:
+        wg = 0.0
+    grid = LbGrid(cap.nx, cap.ny)
+    walls = LbWalls(cap.tube_x0, cap.tube_len, cap.tube_y0, cap.tube_h, cap.gas_cols, float(wg))
+    params = LbParams(p.model, p.storage if storage is None else storage, p.kappa, p.a, p.b, p.T, p.A, p.M,
+                      p.nu_l, p.nu_g, p.nu, p.lambda_scale, p.rho_l, p.rho_g, int(cap.l0))
+    return grid, walls, params
+
+
+def _bcheck(status, h):
+    if status != LB_OK:
+        raise LbError(status, library().lb_batch_last_error(h).decode(errors="replace"))
+
+
+class Batch:
+    """Many binary capillaries advanced together by one persistent kernel."""
+
+    def __init__(self, caps, storage=None, stream=None, use_torch_allocator=True):
+        import torch
+        L = library()
+        n = len(caps)
+        structs = [_structs_for(c, storage) for c in caps]
+        self.grids = (LbGrid * n)(*[s[0] for s in structs])
+        self.walls = (LbWalls * n)(*[s[1] for s in structs])
+        self.params = (LbParams * n)(*[s[2] for s in structs])
+        self.caps = list(caps)
+        self.n = n
+        dev = torch.cuda.current_device()
+        self._torch_stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._alloc = _TorchAllocator(dev) if use_torch_allocator else None
+        h = C.c_void_p()
+        st = L.lb_batch_create(n, self.grids, self.walls, self.params,
+                               C.byref(self._alloc.struct) if self._alloc else None,
+                               C.c_void_p(self._torch_stream.cuda_stream), C.byref(h))
+        if st != LB_OK:
+            raise LbError(st, L.lb_batch_last_error(None).decode(errors="replace"))
+        self.h = h
+
+    @property
+    def stream(self):
+        return self._torch_stream
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            library().lb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n):
+        _bcheck(library().lb_batch_step(self.h, int(n)), self.h)
+        return self
+
+    def lengths(self):
+        out = np.empty((self.n, 4))
+        _bcheck(library().lb_batch_lengths(self.h, _p(out)), self.h)
+        return out
+
+    def run_sampled(self, at):
+        at = np.ascontiguousarray(np.asarray(at, dtype=np.int64))
+        out = np.empty((self.n, len(at), 4))
+        _bcheck(library().lb_batch_run_sampled(self.h, len(at), at.ctypes.data_as(C.c_void_p), _p(out)), self.h)
+        return out
+
+    def populations(self, i, rested=True):
+        c = self.caps[i]
+        f = np.empty((9, c.ny, c.nx))
+        g = np.empty((9, c.ny, c.nx))
+        _bcheck(library().lb_batch_populations(self.h, int(i), _p(f), _p(g), int(bool(rested))), self.h)
+        return f, g
+
+    def set_tile(self, tx, ty):
+        _bcheck(library().lb_batch_set_tile(self.h, int(tx), int(ty)), self.h)
+
+    def autotune(self, steps=4):
+        a, b, ms = C.c_int(), C.c_int(), C.c_double()
+        _bcheck(library().lb_batch_autotune(self.h, int(steps), C.byref(a), C.byref(b), C.byref(ms)), self.h)
+        return a.value, b.value, ms.value
+
+    def set_barrier(self, absent_blocks=0, limit_seconds=2.0):
+        _bcheck(library().lb_batch_set_barrier(self.h, int(absent_blocks), float(limit_seconds)), self.h)
+
+    @property
+    def time(self):
+        return library().lb_batch_time(self.h)
+
+    def fluid_nodes(self, i=-1):
+        return library().lb_batch_fluid_nodes(self.h, int(i))

@@ -138,14 +138,15 @@ def viscosities_for_ratio(ratio: float):
 
 def sweep(seed: int = 0, n: int = 256, steps: int = 20000,
           lengths=(1024, 8192), fixed_len: Optional[int] = None,
-          vary_gamma: bool = False) -> List[Capillary]:
+          vary_gamma: bool = False, liquid_cols: int = 128) -> List[Capillary]:
     """Seeded sweep of uneven binary capillaries.
 
     H uniform in {16, 24, ..., 128}; tube length uniform in [1024, 8192]
     (or fixed_len); ny = H + 8; liquid reservoir 128 columns and a gas buffer of
     32 columns in front of it; viscosity ratio uniform in {1, 5, 10, 50, 100};
     theta uniform in [30, 80] degrees.  With vary_gamma the surface tension is
-    varied by drawing A = kappa uniformly in [0.03, 0.05].
+    varied by drawing A = kappa uniformly in [0.03, 0.05].  liquid_cols widens
+    the liquid reservoir (so that it does not run dry on long fills).
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -156,7 +157,7 @@ def sweep(seed: int = 0, n: int = 256, steps: int = 20000,
         theta = float(rng.uniform(30.0, 80.0))
         Ak = float(rng.uniform(0.03, 0.05)) if vary_gamma else 0.04
         nu_l, nu_g = viscosities_for_ratio(ratio)
-        gas, liquid = 32, 128
+        gas, liquid = 32, liquid_cols
         x0 = gas + liquid
         p = binary_params(nu_l=nu_l, nu_g=nu_g, A=Ak, kappa=Ak)
         out.append(Capillary(f"sweep{seed}_{k}", x0 + L, H + 8, x0, L, 4, H, gas, 10, p,
