@@ -213,6 +213,48 @@ def batched_vs_sequential(torch, Lattice, steps, n=256):
             "what": f"{steps} steps with 4 l(t) samples, wall clock, FP32"}
 
 
+def surrogate_metric(torch, threshold=0.02):
+    """Train the 5-member l(t) surrogate on the LB-generated training runs (4096 of the
+    seeded surrogate sweep), answer the 512 held-out queries, fall back to the LB where
+    the ensemble spread exceeds 2 %, and compare with the LB and with Washburn's law."""
+    from paper_0911_0459_gb300 import surrogate as S
+    path = os.path.join(ROOT, "paper_0911_0459_gb300", "data", "surrogate_data.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "no LB-generated training set (paper_0911_0459_gb300/data/surrogate_data.npz)"}
+    d = np.load(path)
+    test_caps = S.surrogate_sweep(2, int(d["l_test"].shape[0]))
+    x_train, l_train, x_test, l_test = d["x_train"], d["l_train"], d["x_test"], d["l_test"]
+    assert np.allclose(S.features(test_caps), x_test)
+    sur = S.Surrogate(members=5, seed=0)
+    t0 = time.perf_counter()
+    sur.fit(x_train, l_train, steps=6000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pred, spread = sur.predict(x_test)
+    t_pred = time.perf_counter() - t0
+    fall = np.where(spread.max(1) > threshold)[0]
+    t0 = time.perf_counter()
+    lb_fall = S.run_lb([test_caps[i] for i in fall])["l"] if len(fall) else np.zeros((0, l_test.shape[1]))
+    t_fall = time.perf_counter() - t0
+    combined = pred.copy()
+    combined[fall] = lb_fall
+    # LB cost per query on this GPU: a batched run of 64 held-out queries
+    probe = test_caps[:64]
+    t0 = time.perf_counter()
+    S.run_lb(probe)
+    t_lb64 = time.perf_counter() - t0
+    lb_per_query = t_lb64 / len(probe)
+    n = len(test_caps)
+    sur.close()
+    return {"rms_rel_vs_lb": S.rms_rel(pred, l_test), "rms_rel_with_fallback": S.rms_rel(combined, l_test),
+            "fallback_fraction": len(fall) / n, "rms_rel_washburn": S.rms_rel(S.washburn(test_caps), l_test),
+            "train_seconds": t_train, "inference_seconds": t_pred, "fallback_lb_seconds": t_fall,
+            "lb_seconds_per_query": lb_per_query,
+            "speedup_vs_lb": (lb_per_query * n) / (t_pred + t_fall), "queries": n,
+            "what": "MLP 4-256-256-64, BF16 tensor cores, 5 members; l(t) at 64 log-spaced times to 20k steps"}
+
+
 def timed_steps(lat, torch, K, red_every):
     """K steps with reductions every red_every steps; returns (total_ms, step_ms, launches)."""
     s = lat.stream
@@ -252,6 +294,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16dev"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep secondary metric")
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate secondary metric")
     ap.add_argument("--profile", action="store_true",
                     help="only the large capillary: warm-up then --steps steps (for ncu captures)")
     args = ap.parse_args()
@@ -383,6 +426,11 @@ def main():
             secondary["batched_sweep_256"] = batched_vs_sequential(torch, Lattice, args.batch_steps)
         except Exception as ex:
             secondary["batched_error"] = repr(ex)
+    if not args.no_surrogate:
+        try:
+            secondary["surrogate"] = surrogate_metric(torch)
+        except Exception as ex:
+            secondary["surrogate_error"] = repr(ex)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
