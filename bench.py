@@ -132,19 +132,37 @@ def ncu_traffic(kind):
         return None
 
 
-def cpu_baseline(sample_steps=1000):
-    """The FP64 oracle on the 1024 x 64 crop of the same capillary (single thread)."""
+def cpu_baseline(sample_steps=2000):
+    """The FP64 oracle on the 1024 x 64 crop of the same capillary (single thread).
+    Returns the timing and the oracle, whose state after the sample serves the
+    precision report."""
     import oracle
     cap = W.config_binary_crop_1024x64()
     o = oracle.Oracle(cap).init_default()
-    o.step(2)
     t0 = time.perf_counter()
     o.step(sample_steps)
     dt = time.perf_counter() - t0
     fluid = int((o.node_kinds() < 2).sum())
     return {"value": fluid * sample_steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"{sample_steps} steps of the 1024x64 crop (H=50, same parameters), FP64, 1 thread",
-            "seconds": dt}
+            "seconds": dt}, o
+
+
+def precision_report(Lattice, orc, steps):
+    """Error of each storage against the FP64 oracle on the crop after `steps` steps."""
+    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64
+    rho_o, _, _, phi_o = orc.fields()
+    l_o = orc.filled_length()["l"]
+    out = {"workload": "1024x64 crop of the large capillary, default initial state", "steps": steps}
+    for name, st in (("f64", STORAGE_F64), ("f32", STORAGE_F32), ("f16dev", STORAGE_F16DEV)):
+        lat = Lattice.from_workload(W.config_binary_crop_1024x64(st))
+        lat.step(steps)
+        rho, _, _, phi = lat.fields()
+        out[name] = {"max_abs_drho": float(np.abs(rho - rho_o).max()),
+                     "max_abs_dphi": float(np.abs(phi - phi_o).max()),
+                     "abs_dl": abs(lat.filled_length()["l"] - l_o)}
+        lat.close()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -175,8 +193,11 @@ def batched_vs_sequential(torch, Lattice, steps, n=256):
     ratios 1..100, 30..80 degrees), FP32: one persistent CUDA-graph launch per
     sampled run for all capillaries against one lattice per capillary run in
     turn, both with l(t) sampled 4 times over `steps` steps."""
-    from paper_0911_0459_gb300 import Batch
-    caps = W.sweep(seed=0, n=n)
+    from paper_0911_0459_gb300 import Batch, shard
+    rank, world, _ = dist_env()
+    caps_all = W.sweep(seed=0, n=n)
+    # ranks split the sweep by estimated cost; no exchange on the data path
+    caps = [caps_all[i] for i in shard.my_share(caps_all, rank, world)] if world > 1 else caps_all
     at = [steps // 4, steps // 2, 3 * steps // 4, steps]
     b = Batch(caps)
     tx, ty, _ = b.autotune(steps=2)
@@ -202,6 +223,14 @@ def batched_vs_sequential(torch, Lattice, steps, n=256):
             prev = s
         t_seq += time.perf_counter() - t0
         lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_batch, t_seq, float(fluid)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t_batch, t_seq, fluid = float(mx[0]), float(mx[1]), int(sm[2])
     cs_batch = n * steps / t_batch
     cs_seq = n * steps / t_seq
     return {"capillary_steps_per_s": cs_batch, "sequential_capillary_steps_per_s": cs_seq,
@@ -434,7 +463,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu, orc = cpu_baseline()
+        try:
+            secondary["precision_vs_oracle"] = precision_report(Lattice, orc, 2000)
+        except Exception as ex:
+            secondary["precision_error"] = repr(ex)
 
     if rank == 0:
         line = {

@@ -430,3 +430,46 @@ def test_filled_length_on_known_fields():
     tube = slice(16, 56)
     assert abs(d["l_vol"] - np.sum((phi[2:10, tube] + 1) / 2) / 8) < 1e-12
     assert abs(d["mass"] - np.sum(np.where(o.node_kinds() < 2, 1.0, 0.0))) < 1e-9
+
+
+# ------------------------------------------------------- capillary dynamics
+
+
+@pytest.mark.slow
+def test_binary_washburn_filling_and_poiseuille_profile():
+    """Sec. 3.2: with a high viscosity ratio the filled length follows Eq. (3):
+    l_eff^2 = (l + H/2)^2 grows linearly in t, with a dynamic angle above theta_eq
+    (the paper finds 63 for 60).  Eq. (1): the liquid flows as a parabola that
+    vanishes on the boundary-node rows (H_eff = H - 1 under the rest rule)."""
+    H, nul, nug, th = 10, 0.5, 0.0166, 45.0
+    cap = W.Capillary("w", 32 + 80 + 120, H + 4, 112, 120, 2, H, 32, 10,
+                      W.binary_params(nu_l=nul, nu_g=nug), theta_deg=th)
+    o = oracle.Oracle(cap).init_default()
+    ts, ls = [], []
+    for _ in range(40):
+        o.step(150)
+        ts.append(o.time)
+        ls.append(o.filled_length()["l"])
+    ts, ls = np.array(ts), np.array(ls)
+    assert ls[-1] > ls[0] + 8                       # it fills
+    half = len(ts) // 2
+    m, c, r2 = an.linear_fit(ts[half:], (ls[half:] + H / 2) ** 2)
+    assert r2 > 0.999
+    theta_dyn = math.degrees(math.acos(3 * nul * m / (GOLD["binary_gamma"]["value"] * (H - 1))))
+    assert th < theta_dyn < th + 30
+    rho, ux, _, phi = o.fields()
+    xc = 112 + int(ls[-1] / 2)
+    prof = ux[2:2 + H, xc]
+    y = np.arange(H)
+    coef = np.polyfit(y, prof, 2)
+    fit = np.polyval(coef, y)
+    assert 1 - np.sum((prof - fit) ** 2) / np.sum((prof - prof.mean()) ** 2) > 0.99
+    roots = np.sort(np.roots(coef).real)
+    assert abs(roots[0] - 0.0) < 0.2 and abs(roots[1] - (H - 1)) < 0.2
+    # Eq. (1) with dp/dx from p0 along the liquid centre line (approximate: developing flow)
+    p0 = rho / 3 + 0.04 * (-phi ** 2 / 2 + 0.75 * phi ** 4)
+    xs = np.arange(112 + 3, 112 + int(ls[-1]) - 4)
+    dpdx = np.polyfit(xs, p0[2 + H // 2, xs], 1)[0]
+    h_eff = roots[1] - roots[0]
+    vbar = np.sum(prof) / h_eff
+    assert abs(vbar / an.poiseuille_mean_velocity(h_eff, nul, dpdx) - 1) < 0.2
