@@ -230,9 +230,6 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) s
   const int x = c0 + lane;
   const bool act = x < xb + w;
   const int sc = x - xb + 8;          // stage column of this lane's node
-  // extra column summed by the edge lanes: left neighbour of lane 0, right of lane 31
-  const int sx = lane == 0 ? sc - 1 : sc + 1;
-  const bool edge = lane == 0 || lane == 31;
 
   auto load_pop = [&](int s, int c, A f[9], A g[9]) {
 #pragma unroll
@@ -242,17 +239,49 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) s
       for (int i = 0; i < 9; ++i) g[i] = S::pg(stage_g(s), stage_g0(s), W, c, i);
     }
   };
-  // rho/phi of this lane's column (and of the edge lane's extra column) in stage s
-  // (f, g receive this lane's populations, kept for the collision of that row)
-  auto sums = [&](int s, A f[9], A g[9], A& r, A& p, A& re, A& pe) {
+  // One row of the stencil window: this lane's rho/phi and its left/right
+  // neighbours (taken once per row, when the row is summed).
+  struct Row {
+    A rc, rl, rr, pc, pl, pr;
+  };
+  const int scw = sc - lane;  // stage column of this warp's first column
+  // Sum this lane's column (f, g keep its populations for the collision) and the
+  // warp's two halo columns cooperatively: in each half-warp, lanes 0..7 take
+  // planes 1..8 and lane 8 plane 0, so the xor butterfly adds them in the same
+  // order as sum9 (bit-identical to the sliding-window kernel).
+  auto sums = [&](int s, A f[9], A g[9], Row& R) {
     load_pop(s, sc, f, g);
-    r = sum9(f);
-    p = BIN ? sum9(g) : A(0);
-    if (edge) {
-      A fe[9], ge[9];
-      load_pop(s, sx, fe, ge);
-      re = sum9(fe);
-      pe = BIN ? sum9(ge) : A(0);
+    const A r = sum9(f);
+    const A p = BIN ? sum9(g) : A(0);
+    const int h = lane & 15;
+    const int plane = h < 8 ? h + 1 : 0;
+    A hl = A(0), hr = A(0);
+    if (h <= 8) {
+      if (lane < 16) {
+        hl = S::pf(stage_f(s), W, scw - 1, plane);
+        hr = S::pf(stage_f(s), W, scw + 32, plane);
+      } else if (BIN) {
+        hl = S::pg(stage_g(s), stage_g0(s), W, scw - 1, plane);
+        hr = S::pg(stage_g(s), stage_g0(s), W, scw + 32, plane);
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      hl += __shfl_xor_sync(0xffffffffu, hl, o);
+      hr += __shfl_xor_sync(0xffffffffu, hr, o);
+    }
+    // lanes 0..15 now hold the f sums (rho), lanes 16..31 the g sums (phi)
+    const A phl = __shfl_sync(0xffffffffu, hl, 16);
+    const A rhr = __shfl_sync(0xffffffffu, hr, 0);
+    const A rl = __shfl_up_sync(0xffffffffu, r, 1), rr = __shfl_down_sync(0xffffffffu, r, 1);
+    R.rc = r;
+    R.rl = lane == 0 ? hl : rl;
+    R.rr = lane == 31 ? rhr : rr;
+    if (BIN) {
+      const A pl = __shfl_up_sync(0xffffffffu, p, 1), pr = __shfl_down_sync(0xffffffffu, p, 1);
+      R.pc = p;
+      R.pl = lane == 0 ? phl : pl;
+      R.pr = lane == 31 ? hr : pr;
     }
   };
 
@@ -267,9 +296,8 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) s
   const int col[3] = {xm, x, xp};
   const bool warp_tube = __any_sync(0xffffffffu, tc[0] || tc[1] || tc[2]);
 
-  // rows k-1, k, k+1 of rho, phi and the edge lanes' extra column
-  A r[3] = {A(0), A(0), A(0)}, p[3] = {A(0), A(0), A(0)}, re[3] = {A(0), A(0), A(0)},
-    pe[3] = {A(0), A(0), A(0)};
+  // rows k-1, k, k+1 of the stencil window
+  Row R[3];
   bool failed = false;
   A fa[9], ga[9];  // populations of the row to collide next
   // prologue: rows y0 - 1 (k = 0, stencil halo only) and y0 (k = 1)
@@ -278,7 +306,7 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) s
       failed = true;
       break;
     }
-    sums(k, fa, ga, r[k + 1], p[k + 1], re[k + 1], pe[k + 1]);
+    sums(k, fa, ga, R[k + 1]);
     // the populations are in registers now: the stage can be refilled
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[k]);
@@ -288,31 +316,26 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) s
     const int kc = y - y0 + 1;  // staged index of row y
     const int sn = (kc + 1) % NS;
     // shift the row window and add row y + 1
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      r[j] = r[j + 1]; p[j] = p[j + 1]; re[j] = re[j + 1]; pe[j] = pe[j + 1];
-    }
+    R[0] = R[1];
+    R[1] = R[2];
     if (!mbar_wait(&full[sn], ((kc + 1) / NS) & 1)) {
       failed = true;
       break;
     }
     A fn[9], gn[9];
-    sums(sn, fn, gn, r[2], p[2], re[2], pe[2]);
+    sums(sn, fn, gn, R[2]);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[sn]);
-    // 3x3 neighbourhoods through shuffles (edge lanes use their extra column)
     A vr[3][3], vp[3][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const A rl = __shfl_up_sync(0xffffffffu, r[j], 1), rr = __shfl_down_sync(0xffffffffu, r[j], 1);
-      vr[j][0] = lane == 0 ? re[j] : rl;
-      vr[j][1] = r[j];
-      vr[j][2] = lane == 31 ? re[j] : rr;
+      vr[j][0] = R[j].rl;
+      vr[j][1] = R[j].rc;
+      vr[j][2] = R[j].rr;
       if (BIN) {
-        const A pl = __shfl_up_sync(0xffffffffu, p[j], 1), pr = __shfl_down_sync(0xffffffffu, p[j], 1);
-        vp[j][0] = lane == 0 ? pe[j] : pl;
-        vp[j][1] = p[j];
-        vp[j][2] = lane == 31 ? pe[j] : pr;
+        vp[j][0] = R[j].pl;
+        vp[j][1] = R[j].pc;
+        vp[j][2] = R[j].pr;
       }
     }
     const int yy = wrapi(y, ny);
