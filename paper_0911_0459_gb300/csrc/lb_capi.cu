@@ -41,6 +41,7 @@ struct lb_ctx {
   double* red_out;
   int tile_x, tile_y;
   int kernel;   // 0 auto, 1 sliding window, 2 staged
+  int deep;     // staged kernel ring depth choice
   int* errflag; // device error word written by the staged kernel
   cudaGraphExec_t gexec;
   int poisoned;
@@ -130,6 +131,7 @@ static OpArgs base_args(const lb_ctx* c) {
   a.bx = c->tile_x;
   a.yc = c->tile_y;
   a.staged = c->kernel == 2 || (c->kernel == 0 && c->grid.nx % 8 == 0);
+  a.deep = c->deep;
   a.err = c->errflag;
   return a;
 }
@@ -549,20 +551,22 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   if (e == cudaSuccess && g0b) e = cudaMemcpyAsync(save + fb + gb, cur.g0, g0b, cudaMemcpyDeviceToDevice, c->stream);
   const int cand_x[3] = {64, 128, 256};
   const int cand_y[7] = {1, 2, 4, 8, 16, 32, 64};
-  const int saved_kernel = c->kernel;
-  int best_x = c->tile_x, best_y = c->tile_y, best_k = saved_kernel;
+  const int saved_kernel = c->kernel, saved_deep = c->deep;
+  int best_x = c->tile_x, best_y = c->tile_y, best_k = saved_kernel, best_d = saved_deep;
   float best = 1e30f;
   cudaEvent_t e0 = NULL, e1 = NULL;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const int reps = 10;
   // kernel variants: the staged kernel only where rows are 16-byte aligned
-  const int nk = c->grid.nx % 8 == 0 ? 2 : 1;
+  // variants: sliding window, staged (shallow ring), staged (deep ring)
+  const int nk = c->grid.nx % 8 == 0 ? 3 : 1;
   for (int ik = 0; ik < nk && e == cudaSuccess && st == LB_OK; ++ik)
   for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
     for (int iy = 0; iy < 7 && e == cudaSuccess && st == LB_OK; ++iy) {
       if (cand_y[iy] > c->grid.ny) continue;
       c->kernel = ik == 0 ? 1 : 2;
+      c->deep = ik == 2;
       c->tile_x = cand_x[ix];
       c->tile_y = cand_y[iy];
       int from = c->cur;
@@ -578,9 +582,11 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
         best_x = cand_x[ix];
         best_y = cand_y[iy];
         best_k = c->kernel;
+        best_d = c->deep;
       }
     }
   c->kernel = saved_kernel;
+  c->deep = saved_deep;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   // restore
@@ -592,6 +598,7 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   c->tile_x = best_x;
   c->tile_y = best_y;
   c->kernel = best_k;
+  c->deep = best_d;
   drop_graph(c);
   if (st != LB_OK) return st;
   if (e != cudaSuccess || er != cudaSuccess)

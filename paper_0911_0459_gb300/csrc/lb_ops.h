@@ -26,6 +26,7 @@ struct OpArgs {
   // step tile and kernel variant (0: sliding window, 1: bulk-copy staged)
   int bx, yc;
   int staged;
+  int deep;      // staged kernel: 0 = shallow ring (more CTAs per SM), 1 = deeper ring
   int* err;      // device error word (a device-side wait gave up)
   // field / population / reduction arguments (device pointers)
   const double *in0, *in1, *in2, *in3;

@@ -75,9 +75,9 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
     case OP_STEP:
       if (a.staged) {
         if (a.nx % 8 != 0 || !a.err) return cudaErrorInvalidValue;
-        if (a.bx == 64) return launch_staged<MODEL, S, 64, 4>(a, s);
-        if (a.bx == 128) return launch_staged<MODEL, S, 128, 4>(a, s);
-        if (a.bx == 256) return launch_staged<MODEL, S, 256, 3>(a, s);
+        if (a.bx == 64) return a.deep ? launch_staged<MODEL, S, 64, 8>(a, s) : launch_staged<MODEL, S, 64, 4>(a, s);
+        if (a.bx == 128) return a.deep ? launch_staged<MODEL, S, 128, 6>(a, s) : launch_staged<MODEL, S, 128, 4>(a, s);
+        if (a.bx == 256) return a.deep ? launch_staged<MODEL, S, 256, 4>(a, s) : launch_staged<MODEL, S, 256, 3>(a, s);
         return cudaErrorInvalidValue;
       }
       if (a.bx == 64) return launch_step<MODEL, S, 64>(a, s);

@@ -128,7 +128,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 template <int MODEL, class S, int BX, int NS>
-__global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) step_tma_kernel(TmaArgs<MODEL, S> a) {
+__global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 128 ? (NS > 4 ? 3 : 5) : (NS > 3 ? 2 : 3))) step_tma_kernel(TmaArgs<MODEL, S> a) {
   using L = TmaLayout<MODEL, S, BX, NS>;
   using T = typename S::T;
   using A = typename S::A;
@@ -244,44 +244,31 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? 8 : (BX == 128 ? 5 : 3)) s
   struct Row {
     A rc, rl, rr, pc, pl, pr;
   };
-  const int scw = sc - lane;  // stage column of this warp's first column
-  // Sum this lane's column (f, g keep its populations for the collision) and the
-  // warp's two halo columns cooperatively: in each half-warp, lanes 0..7 take
-  // planes 1..8 and lane 8 plane 0, so the xor butterfly adds them in the same
-  // order as sum9 (bit-identical to the sliding-window kernel).
+  // extra column summed by the edge lanes: left neighbour of lane 0, right of lane 31
+  const int sx = lane == 0 ? sc - 1 : sc + 1;
+  const bool edge = lane == 0 || lane == 31;
+  // Sum this lane's column (f, g keep its populations for the collision); the edge
+  // lanes also sum the warp's halo column; then take the neighbours by shuffles.
   auto sums = [&](int s, A f[9], A g[9], Row& R) {
     load_pop(s, sc, f, g);
     const A r = sum9(f);
     const A p = BIN ? sum9(g) : A(0);
-    const int h = lane & 15;
-    const int plane = h < 8 ? h + 1 : 0;
-    A hl = A(0), hr = A(0);
-    if (h <= 8) {
-      if (lane < 16) {
-        hl = S::pf(stage_f(s), W, scw - 1, plane);
-        hr = S::pf(stage_f(s), W, scw + 32, plane);
-      } else if (BIN) {
-        hl = S::pg(stage_g(s), stage_g0(s), W, scw - 1, plane);
-        hr = S::pg(stage_g(s), stage_g0(s), W, scw + 32, plane);
-      }
+    A re = A(0), pe = A(0);
+    if (edge) {
+      A fe[9], ge[9];
+      load_pop(s, sx, fe, ge);
+      re = sum9(fe);
+      pe = BIN ? sum9(ge) : A(0);
     }
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-      hl += __shfl_xor_sync(0xffffffffu, hl, o);
-      hr += __shfl_xor_sync(0xffffffffu, hr, o);
-    }
-    // lanes 0..15 now hold the f sums (rho), lanes 16..31 the g sums (phi)
-    const A phl = __shfl_sync(0xffffffffu, hl, 16);
-    const A rhr = __shfl_sync(0xffffffffu, hr, 0);
     const A rl = __shfl_up_sync(0xffffffffu, r, 1), rr = __shfl_down_sync(0xffffffffu, r, 1);
     R.rc = r;
-    R.rl = lane == 0 ? hl : rl;
-    R.rr = lane == 31 ? rhr : rr;
+    R.rl = lane == 0 ? re : rl;
+    R.rr = lane == 31 ? re : rr;
     if (BIN) {
       const A pl = __shfl_up_sync(0xffffffffu, p, 1), pr = __shfl_down_sync(0xffffffffu, p, 1);
       R.pc = p;
-      R.pl = lane == 0 ? phl : pl;
-      R.pr = lane == 31 ? hr : pr;
+      R.pl = lane == 0 ? pe : pl;
+      R.pr = lane == 31 ? pe : pr;
     }
   };
 
