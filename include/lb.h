@@ -163,10 +163,11 @@ lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
 /* Choose the step kernel: 0 = automatic (the staged kernel whenever nx % 8 ==
  * 0, else the sliding-window kernel), 1 = sliding-window kernel (rows held in
  * registers), 2 = staged kernel (rows brought into shared memory by bulk
- * copies; needs nx % 8 == 0).  Both compute the same update bit for bit.
+ * copies; needs nx % 8 == 0) with its shallow ring of row stages, 3 = staged
+ * kernel with its deep ring.  All compute the same update bit for bit.
  * Invalidates the captured step graph. */
 lb_status lb_set_kernel(lb_ctx *ctx, int variant);
-/* The kernel variant in use (1 or 2; automatic selection resolved). */
+/* The kernel variant in use (1, 2 or 3; automatic selection resolved). */
 lb_status lb_get_kernel(const lb_ctx *ctx, int *variant);
 
 /* Time each candidate kernel variant and tile on this lattice (the state is
@@ -213,16 +214,26 @@ lb_status lb_batch_run_sampled(lb_batch *b, int nsamples, const long *at, double
 /* Populations of lattice i, as lb_get_populations. */
 lb_status lb_batch_populations(lb_batch *b, int i, double *f, double *g, int rested);
 
-/* Tile of the persistent kernel (tile_x = 64, 128, 256 threads along x, tile_y
- * rows), and a tuner that times every candidate on the batch itself for
- * 2*steps steps each (this advances the state). */
+/* Tile of the persistent kernel (tile_x = 64, 128, 256 consumer threads along
+ * x, tile_y rows), and a tuner that times every candidate (body, ring depth and
+ * tile) on the batch itself for 2*steps steps each (this advances the state). */
 lb_status lb_batch_set_tile(lb_batch *b, int tile_x, int tile_y);
 lb_status lb_batch_autotune(lb_batch *b, int steps, int *tile_x, int *tile_y, double *ms_per_step);
+
+/* Body of the persistent kernel, as lb_set_kernel: 0 = automatic (staged when
+ * every lattice has nx % 8 == 0, else sliding-window), 1 = sliding-window body,
+ * 2 / 3 = staged body with its shallow / deep ring (bulk copies into a
+ * shared-memory ring that runs on across tiles and steps; every nx % 8 == 0,
+ * else LB_ERR_ARG).  All give the same result bit for bit.  get returns the
+ * body in use (1, 2 or 3). */
+lb_status lb_batch_set_kernel(lb_batch *b, int variant);
+lb_status lb_batch_get_kernel(const lb_batch *b, int *variant);
 
 /* Grid-barrier settings: the wait limit in seconds (default 2) and a number of
  * arrivals that never come.  A nonzero absent_blocks makes every barrier wait
  * run out (failure injection on the host, for tests): the kernel returns, the
- * state is unreliable and the next waiting call returns LB_ERR_TIMEOUT. */
+ * state is unreliable and the next waiting call returns LB_ERR_TIMEOUT.  The
+ * staged body's shared-memory waits use a fixed 2 s limit. */
 lb_status lb_batch_set_barrier(lb_batch *b, unsigned int absent_blocks, double limit_seconds);
 
 long lb_batch_time(const lb_batch *b);

@@ -144,28 +144,53 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block partial sums in FP64 (the state may be FP32/FP16; every node value is
-// widened before it is added).  partials[b * RED_PARTS + k].
+// Per-node sums for the reductions: rho and phi of one node as the step
+// computes them (sum9 in the arithmetic type), then widened to FP64 for the
+// sums over nodes.  (FP64 arithmetic is scarce on this GPU: one widening per
+// node and field, not one per population.)  The tube's liquid volume is
+// accumulated as a sum of the node values and a node count and finished per
+// thread by finish_volume, which is exact up to rounding.
+struct RedAcc {
+  double mass = 0.0, phi = 0.0, tube = 0.0;
+  int ntube = 0;
+};
+
+template <int MODEL, class S>
+__device__ __forceinline__ void red_add_node(const Geom& G, const Buf<S>& B, size_t N, size_t n, int x, int y,
+                                             RedAcc& acc) {
+  using A = typename S::A;
+  A f[9], g[9];
+  load_node<MODEL, S, true>(B, N, n, f, g);
+  const double r = (double)sum9(f);
+  const double p = MODEL == MODEL_BINARY ? (double)sum9(g) : 0.0;
+  acc.mass += r;
+  acc.phi += p;
+  if (G.tube_len > 0 && col_in_tube(G, x) && row_in_band(G, y)) {
+    acc.tube += MODEL == MODEL_BINARY ? p : r;
+    ++acc.ntube;
+  }
+}
+
+// Liquid volume of the tube nodes a thread visited: sum of (phi + 1) / 2
+// (binary) or of (rho - rho_g) / (rho_l - rho_g) (liquid-gas).
+template <int MODEL>
+__device__ __forceinline__ double finish_volume(const RedAcc& acc, double rho_l, double rho_g) {
+  return MODEL == MODEL_BINARY ? 0.5 * (acc.tube + (double)acc.ntube)
+                               : (acc.tube - (double)acc.ntube * rho_g) / (rho_l - rho_g);
+}
+
+// Block partial sums in FP64 (see red_add_node).  partials[b * RED_PARTS + k].
 template <int MODEL, class S>
 __global__ void __launch_bounds__(RED_THREADS) reduce_partials_kernel(Geom G, Buf<S> B, double rho_l, double rho_g,
                                                                       double* __restrict__ partials) {
-  using A = typename S::A;
   const size_t N = (size_t)G.nx * G.ny;
-  double acc[RED_PARTS] = {0.0, 0.0, 0.0};
+  RedAcc ra;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
     if (is_solid(G, x, y)) continue;
-    A f[9], g[9];
-    load_node<MODEL, S>(B, N, n, f, g);
-    double r = 0.0, p = 0.0;
-    for (int i = 0; i < 9; ++i) r += (double)f[i];
-    if (MODEL == MODEL_BINARY)
-      for (int i = 0; i < 9; ++i) p += (double)g[i];
-    acc[0] += r;
-    acc[1] += p;
-    if (G.tube_len > 0 && col_in_tube(G, x) && row_in_band(G, y))
-      acc[2] += MODEL == MODEL_BINARY ? 0.5 * (p + 1.0) : (r - rho_g) / (rho_l - rho_g);
+    red_add_node<MODEL, S>(G, B, N, n, x, y, ra);
   }
+  const double acc[RED_PARTS] = {ra.mass, ra.phi, finish_volume<MODEL>(ra, rho_l, rho_g)};
   __shared__ double sh[RED_PARTS][RED_THREADS / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = 0; k < RED_PARTS; ++k) {

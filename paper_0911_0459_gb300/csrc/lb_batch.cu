@@ -40,6 +40,10 @@ struct lb_batch {
   void* d_caps;
   TileDesc* d_tiles;
   int ntiles;
+  RedChunk* d_chunks;  // reduction chunks of every lattice, lattice by lattice
+  int2* d_range;       // per lattice: first chunk, number of chunks
+  double* d_part;      // three partial sums per chunk
+  int nchunks;
   GridBarrier* d_bar;
   int* d_err;
   double* d_out;
@@ -47,6 +51,9 @@ struct lb_batch {
   int parity;
   long t;
   int tile_x, tile_y;
+  int kernel;      // 0 automatic, 1 sliding-window body, 2 staged body
+  int deep;        // staged body: the deeper of its two rings
+  int staged_ok;   // every lattice has nx % 8 == 0
   int grid_blocks;
   unsigned int extra_arrivals;
   unsigned long long limit_ns;
@@ -231,8 +238,65 @@ static cudaError_t launch_batch_t(lb_batch* b, int nsteps, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, batch_step_kernel<S, BX>, a);
 }
 
+template <class S, int BX, int NS>
+static cudaError_t launch_batch_tma(lb_batch* b, int nsteps, cudaStream_t s) {
+  using L = TmaLayout<MODEL_BINARY, S, BX, NS>;
+  static bool configured = false;  // dynamic shared memory opt-in, once per process
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(batch_tma_kernel<S, BX, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)L::BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  BatchArgs<S> a;
+  a.caps = (const CapDesc<typename S::A>*)b->d_caps;
+  a.tiles = b->d_tiles;
+  a.ntiles = b->ntiles;
+  a.fa = (typename S::T*)b->f[0]; a.ga = (typename S::T*)b->g[0]; a.g0a = b->g0[0];
+  a.fb = (typename S::T*)b->f[1]; a.gb = (typename S::T*)b->g[1]; a.g0b = b->g0[1];
+  a.nsteps = nsteps;
+  a.parity = b->parity;
+  a.bar = b->d_bar;
+  a.limit_ns = b->limit_ns;
+  a.err = b->d_err;
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_tma_kernel<S, BX, NS>, BX + 32, L::BYTES);
+  if (e != cudaSuccess) return e;
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  int blocks = std::max(1, std::min(per * sms, b->ntiles));
+  b->grid_blocks = blocks;
+  a.expected = (unsigned)blocks + b->extra_arrivals;
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(BX + 32);
+  cfg.dynamicSmemBytes = L::BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_tma_kernel<S, BX, NS>, a);
+}
+
+// 1 or 2: the body the next launch uses
+static int batch_variant(const lb_batch* b) {
+  if (b->kernel == 0) return b->staged_ok ? 2 : 1;
+  return b->kernel;
+}
+
 template <class S>
 static cudaError_t launch_batch_s(lb_batch* b, int nsteps, cudaStream_t s) {
+  if (batch_variant(b) == 2) {
+    // ring depths as for the single-lattice staged kernel
+    if (b->tile_x == 64) return b->deep ? launch_batch_tma<S, 64, 8>(b, nsteps, s) : launch_batch_tma<S, 64, 4>(b, nsteps, s);
+    if (b->tile_x == 128) return b->deep ? launch_batch_tma<S, 128, 6>(b, nsteps, s) : launch_batch_tma<S, 128, 4>(b, nsteps, s);
+    return b->deep ? launch_batch_tma<S, 256, 4>(b, nsteps, s) : launch_batch_tma<S, 256, 3>(b, nsteps, s);
+  }
   if (b->tile_x == 64) return launch_batch_t<S, 64>(b, nsteps, s);
   if (b->tile_x == 128) return launch_batch_t<S, 128>(b, nsteps, s);
   return launch_batch_t<S, 256>(b, nsteps, s);
@@ -246,10 +310,40 @@ static cudaError_t launch_batch(lb_batch* b, int nsteps, cudaStream_t s) {
 
 template <class S>
 static cudaError_t launch_reduce_s(lb_batch* b, int buf, int nsamples, int col, double* out, cudaStream_t s) {
-  batch_reduce_kernel<S><<<b->n, 1024, 0, s>>>((const CapDesc<typename S::A>*)b->d_caps, b->n,
-                                               (typename S::T*)b->f[buf], (typename S::T*)b->g[buf], b->g0[buf],
-                                               nsamples, col, out);
+  const CapDesc<typename S::A>* caps = (const CapDesc<typename S::A>*)b->d_caps;
+  typename S::T* f = (typename S::T*)b->f[buf];
+  typename S::T* g = (typename S::T*)b->g[buf];
+  batch_partials_kernel<S><<<b->nchunks, RED_THREADS, 0, s>>>(caps, b->d_chunks, f, g, b->g0[buf], b->d_part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  batch_final_kernel<S><<<b->n, 1024, 0, s>>>(caps, b->d_range, b->n, f, g, b->g0[buf], b->d_part, nsamples, col,
+                                              out);
   return cudaGetLastError();
+}
+
+// Reduction chunks: consecutive node ranges of kRedChunk nodes (the last one of
+// a lattice ragged), so that the first pass has enough blocks for any batch.
+static constexpr int kRedChunk = 1 << 13;
+
+static lb_status build_chunks(lb_batch* b) {
+  std::vector<RedChunk> chunks;
+  std::vector<int2> range(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    const int N = b->grids[i].nx * b->grids[i].ny;
+    range[i].x = (int)chunks.size();
+    for (int n0 = 0; n0 < N; n0 += kRedChunk) chunks.push_back(RedChunk{i, n0, std::min(N, n0 + kRedChunk)});
+    range[i].y = (int)chunks.size() - range[i].x;
+  }
+  b->nchunks = (int)chunks.size();
+  b->d_chunks = (RedChunk*)balloc(b, chunks.size() * sizeof(RedChunk));
+  b->d_range = (int2*)balloc(b, range.size() * sizeof(int2));
+  b->d_part = (double*)balloc(b, chunks.size() * 3 * sizeof(double));
+  if (!b->d_chunks || !b->d_range || !b->d_part) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  BCK(cudaMemcpyAsync(b->d_chunks, chunks.data(), chunks.size() * sizeof(RedChunk), cudaMemcpyHostToDevice,
+                      b->stream));
+  BCK(cudaMemcpyAsync(b->d_range, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return LB_OK;
 }
 
 static cudaError_t launch_reduce(lb_batch* b, int buf, int nsamples, int col, double* out, cudaStream_t s) {
@@ -284,7 +378,7 @@ static lb_status check_err(lb_batch* b) {
   BCK(cudaMemcpy(&h, b->d_err, sizeof h, cudaMemcpyDeviceToHost));
   if (h) {
     b->poisoned = 1;
-    berr(b, "the grid barrier of the persistent kernel timed out (state is unreliable)");
+    berr(b, "a wait of the persistent kernel timed out (state is unreliable)");
     return LB_ERR_TIMEOUT;
   }
   return LB_OK;
@@ -332,6 +426,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   if (alloc) b->alloc = *alloc;
   b->tile_x = 128;
   b->tile_y = 8;
+  b->staged_ok = 1;
+  for (int i = 0; i < n; ++i) b->staged_ok = b->staged_ok && grids[i].nx % 8 == 0;
   b->limit_ns = kDefaultLimitNs;
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     berr(NULL, "cudaStreamCreate failed");
@@ -387,6 +483,7 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 256);
   lb_status st = e == cudaSuccess ? LB_OK : LB_ERR_CUDA;
   if (st == LB_OK) st = build_tiles(b);
+  if (st == LB_OK) st = build_chunks(b);
   for (int i = 0; i < n && st == LB_OK; ++i) st = init_lattice(b, i);
   if (st != LB_OK) {
     snprintf(g_batch_create_err, sizeof g_batch_create_err, "%s", e != cudaSuccess ? cudaGetErrorString(e) : b->err);
@@ -534,40 +631,63 @@ lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, do
   if (!b || steps < 1) return LB_ERR_ARG;
   if (b->poisoned) return LB_ERR_STATE;
   // tuning runs advance the state: run an even number of steps per candidate and
-  // restore nothing else (callers tune before they start a measured run)
+  // restore nothing else (callers tune before they start a measured run).
+  // Candidates: the sliding-window body, and the staged body with its shallow
+  // and deep rings (when every nx % 8 == 0), each over the tiles below; an
+  // explicit lb_batch_set_kernel choice limits the bodies tried.
   const int cx[3] = {64, 128, 256};
   const int cy[5] = {4, 8, 16, 32, 64};
-  int bx = b->tile_x, by = b->tile_y;
+  struct Body {
+    int kernel, deep;
+  };
+  Body bodies[3];
+  int nb = 0;
+  if (b->kernel != 2) bodies[nb++] = Body{1, 0};
+  if (b->kernel != 1 && b->staged_ok) {
+    bodies[nb++] = Body{2, 0};
+    bodies[nb++] = Body{2, 1};
+  }
+  const int keep_kernel = b->kernel;
+  int bx = b->tile_x, by = b->tile_y, bk = batch_variant(b), bd = b->deep;
   float best = 1e30f;
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
   lb_status st = LB_OK;
-  for (int i = 0; i < 3 && st == LB_OK; ++i)
-    for (int j = 0; j < 5 && st == LB_OK; ++j) {
-      st = lb_batch_set_tile(b, cx[i], cy[j]);
-      if (st) break;
-      st = lb_batch_step(b, 2);
-      if (st) break;
-      cudaEventRecord(e0, b->stream);
-      st = lb_batch_step(b, 2 * steps);
-      cudaEventRecord(e1, b->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (st == LB_OK && ms < best) {
-        best = ms;
-        bx = cx[i];
-        by = cy[j];
+  for (int v = 0; v < nb && st == LB_OK; ++v)
+    for (int i = 0; i < 3 && st == LB_OK; ++i)
+      for (int j = 0; j < 5 && st == LB_OK; ++j) {
+        b->kernel = bodies[v].kernel;
+        b->deep = bodies[v].deep;
+        st = lb_batch_set_tile(b, cx[i], cy[j]);
+        if (st) break;
+        st = lb_batch_step(b, 2);
+        if (st) break;
+        cudaEventRecord(e0, b->stream);
+        st = lb_batch_step(b, 2 * steps);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (st == LB_OK && ms < best) {
+          best = ms;
+          bx = cx[i];
+          by = cy[j];
+          bk = bodies[v].kernel;
+          bd = bodies[v].deep;
+        }
       }
-    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->kernel = keep_kernel;
   if (st) return st;
   st = check_err(b);
   if (st) return st;
   st = lb_batch_set_tile(b, bx, by);
   if (st) return st;
+  // an automatic choice stays automatic unless tuning preferred the other body
+  if (keep_kernel != 0 || bk != batch_variant(b)) b->kernel = bk;
+  b->deep = bd;
   if (tile_x) *tile_x = bx;
   if (tile_y) *tile_y = by;
   if (ms_per_step) *ms_per_step = best / (2.0 * steps);
@@ -580,6 +700,23 @@ lb_status lb_batch_set_barrier(lb_batch* b, unsigned int absent_blocks, double l
   b->extra_arrivals = absent_blocks;
   b->limit_ns = (unsigned long long)(limit_seconds * 1e9);
   BCK(cudaMemset(b->d_bar, 0, 256));
+  return LB_OK;
+}
+
+lb_status lb_batch_set_kernel(lb_batch* b, int variant) {
+  if (!b) return LB_ERR_ARG;
+  if (variant < 0 || variant > 3) return berr(b, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
+  if (variant >= 2 && !b->staged_ok) return berr(b, "the staged body needs nx %% 8 == 0 in every lattice"), LB_ERR_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  b->kernel = variant == 3 ? 2 : variant;
+  if (variant >= 2) b->deep = variant == 3;
+  return LB_OK;
+}
+
+lb_status lb_batch_get_kernel(const lb_batch* b, int* variant) {
+  if (!b || !variant) return LB_ERR_ARG;
+  const int k = batch_variant(b);
+  *variant = k == 2 && b->deep ? 3 : k;
   return LB_OK;
 }
 

@@ -111,13 +111,142 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(BatchArgs<S> a) {
   }
 }
 
-// One block per lattice: mass, sum of phi, filled volume and l (as in
-// reduce_partials/reduce_final, for every lattice of the batch).  out[c * 4 + k]
-// or, with a sample column, out[(c * nsamples + col) * 4 + k].
+// Grid barrier of the staged batch kernel: every thread passes in whether its
+// own work failed; a failure anywhere sets the error word before the CTA
+// arrives, and every CTA reads the word after the barrier, so that all of them
+// leave at the same step.  Returns false when the CTA must stop.
+__device__ __forceinline__ bool grid_barrier_checked(GridBarrier* b, unsigned int expected,
+                                                     unsigned long long limit_ns, bool failed, int* err) {
+  __shared__ int ok_sh;
+  const int any = __syncthreads_or(failed ? 1 : 0);
+  if (threadIdx.x == 0) {
+    if (any) atomicExch(err, 1);
+    volatile unsigned int* vgen = &b->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&b->count, 1u);
+    int ok = 1;
+    if (arrived == expected - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*vgen == g) {
+        if (globaltimer_ns() - t0 > limit_ns) {
+          ok = 0;
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)err != 0) ok = 0;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// The staged update (bulk copies into a shared-memory ring by a producer warp,
+// BX/32 consumer warps) over the batch's tiles.  The ring's row counter runs on
+// across tiles and steps, so the producer keeps copying while the consumers
+// finish the previous tile.  Every lattice's nx is a multiple of 8 (the copies'
+// 16-byte alignment).  Per-node arithmetic is the single-lattice kernels', so
+// results are bitwise those of lb_step with the staged kernel.
+template <class S, int BX, int NS>
+__global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_kernel(BatchArgs<S> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Ring<MODEL_BINARY, S, BX, NS> R = ring_init<MODEL_BINARY, S, BX, NS>(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool producer = warp == BX / 32;
+  unsigned k = 0, issued = 0;
+  bool ok = true;
+  for (int s = 0; s < a.nsteps; ++s) {
+    const bool fromA = ((a.parity + s) & 1) == 0;
+    if (producer && lane == 0) {
+      // bulk copies read through the async proxy what other CTAs stored through
+      // the generic proxy before the grid barrier
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      const TileDesc td = a.tiles[t];
+      const CapDesc<typename S::A>& c = a.caps[td.cap];
+      if (ok) {
+        if (producer) {
+          if (lane == 0) {
+            const Buf<S> src = fromA ? cap_buf<S>(a.fa, a.ga, a.g0a, c) : cap_buf<S>(a.fb, a.gb, a.g0b, c);
+            ok = produce_tile<MODEL_BINARY, S, BX, NS>(R, c.G, src, td.xb, td.y0, td.y1, k, issued);
+          }
+        } else {
+          const Buf<S> dst = fromA ? cap_buf<S>(a.fb, a.gb, a.g0b, c) : cap_buf<S>(a.fa, a.ga, a.g0a, c);
+          ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, c.P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+        }
+      }
+      k += (unsigned)(td.y1 - td.y0 + 2);
+      // only k mod 2 NS (stage and phase) and whether k >= NS matter: keep the
+      // counter small so that long runs cannot wrap it
+      if (k >= 4 * NS) {
+        const unsigned shift = (k - 2 * NS) / (2 * NS) * (2 * NS);
+        k -= shift;
+        issued = issued >= shift ? issued - shift : 0;
+      }
+    }
+    if (!grid_barrier_checked(a.bar, a.expected, a.limit_ns, !ok, a.err)) break;
+  }
+  if (producer && lane == 0) drain_ring<MODEL_BINARY, S, BX, NS>(R, issued);
+}
+
+// Reductions of every lattice (mass, sum of phi, filled volume, l), in two
+// passes so that large lattices do not serialise on one block.  The nodes of
+// each lattice are cut into chunks of consecutive node indices; pass 1 gives
+// every chunk a block and writes its three partial sums, pass 2 gives every
+// lattice a block that adds its chunks' partials in chunk order (the result does
+// not depend on scheduling) and finds l from the centre line.
+struct RedChunk {
+  int cap;     // lattice
+  int n0, n1;  // node range [n0, n1) of the lattice
+};
+
 template <class S>
-__global__ void __launch_bounds__(1024) batch_reduce_kernel(const CapDesc<typename S::A>* caps, int ncaps,
-                                                            typename S::T* f, typename S::T* g, float* g0,
-                                                            int nsamples, int col, double* out) {
+__global__ void __launch_bounds__(RED_THREADS) batch_partials_kernel(const CapDesc<typename S::A>* caps,
+                                                                     const RedChunk* chunks, typename S::T* f,
+                                                                     typename S::T* g, float* g0, double* part) {
+  using A = typename S::A;
+  const RedChunk ch = chunks[blockIdx.x];
+  const CapDesc<A> c = caps[ch.cap];
+  const Geom& G = c.G;
+  const Buf<S> B = cap_buf<S>(f, g, g0, c);
+  const size_t N = (size_t)G.nx * G.ny;
+  RedAcc ra;
+  for (int n = ch.n0 + threadIdx.x; n < ch.n1; n += blockDim.x) {
+    const int x = n % G.nx, y = n / G.nx;
+    if (is_solid(G, x, y)) continue;
+    red_add_node<MODEL_BINARY, S>(G, B, N, (size_t)n, x, y, ra);
+  }
+  const double acc[3] = {ra.mass, ra.phi, finish_volume<MODEL_BINARY>(ra, 0.0, 0.0)};
+  __shared__ double sh[3][RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 3; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[threadIdx.x][w];
+    part[(size_t)blockIdx.x * 3 + threadIdx.x] = s;
+  }
+}
+
+// Pass 2: one block per lattice.  range[c] = {first chunk, number of chunks}.
+// out[c * 4 + k] or, with a sample column, out[(c * nsamples + col) * 4 + k].
+template <class S>
+__global__ void __launch_bounds__(1024) batch_final_kernel(const CapDesc<typename S::A>* caps, const int2* range,
+                                                           int ncaps, typename S::T* f, typename S::T* g,
+                                                           float* g0, const double* part, int nsamples, int col,
+                                                           double* out) {
   using A = typename S::A;
   const int ci = blockIdx.x;
   if (ci >= ncaps) return;
@@ -125,27 +254,8 @@ __global__ void __launch_bounds__(1024) batch_reduce_kernel(const CapDesc<typena
   const Geom& G = c.G;
   const Buf<S> B = cap_buf<S>(f, g, g0, c);
   const size_t N = (size_t)G.nx * G.ny;
-  double acc[3] = {0.0, 0.0, 0.0};
-  for (size_t n = threadIdx.x; n < N; n += blockDim.x) {
-    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
-    if (is_solid(G, x, y)) continue;
-    A fv[9], gv[9];
-    load_node<MODEL_BINARY, S, true>(B, N, n, fv, gv);
-    double r = 0.0, p = 0.0;
-    for (int i = 0; i < 9; ++i) r += (double)fv[i];
-    for (int i = 0; i < 9; ++i) p += (double)gv[i];
-    acc[0] += r;
-    acc[1] += p;
-    if (G.tube_len > 0 && col_in_tube(G, x) && row_in_band(G, y)) acc[2] += 0.5 * (p + 1.0);
-  }
-  __shared__ double sh[3][32];
   __shared__ int first;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (threadIdx.x == 0) first = INT_MAX;
-  for (int k = 0; k < 3; ++k) {
-    const double v = warp_sum(acc[k]);
-    if (lane == 0) sh[k][wid] = v;
-  }
   __syncthreads();
   const int L = G.tube_len;
   for (int k = threadIdx.x; k < L; k += blockDim.x) {
@@ -155,14 +265,21 @@ __global__ void __launch_bounds__(1024) batch_reduce_kernel(const CapDesc<typena
     if (!hit && k + 1 < L && c0 > 0.0) hit = !(centre_value<MODEL_BINARY, S>(G, B, N, k + 1, c.thr) > 0.0);
     if (hit) atomicMin(&first, k);
   }
+  // warp 0 adds the lattice's chunk partials: lane j takes chunks j, j + 32, ...
+  // in order, then a fixed shuffle tree (independent of scheduling)
+  __shared__ double tot[3];
+  if (threadIdx.x < 32) {
+    const int2 r = range[ci];
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int j = threadIdx.x; j < r.y; j += 32)
+      for (int k = 0; k < 3; ++k) t[k] += part[(size_t)(r.x + j) * 3 + k];
+    for (int k = 0; k < 3; ++k) {
+      const double v = warp_sum(t[k]);
+      if (threadIdx.x == 0) tot[k] = v;
+    }
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot[3];
-    for (int k = 0; k < 3; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += sh[k][w];
-      tot[k] = s;
-    }
     double l;
     if (L <= 0) {
       l = 0.0;

@@ -493,20 +493,24 @@ lb_status lb_sync(lb_ctx* c) {
 
 lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
   if (!c || !variant) return LB_ERR_ARG;
-  *variant = c->kernel == 0 ? (c->grid.nx % 8 == 0 ? 2 : 1) : c->kernel;
+  const int k = c->kernel == 0 ? (c->grid.nx % 8 == 0 ? 2 : 1) : c->kernel;
+  *variant = k == 2 && c->deep ? 3 : k;
   return LB_OK;
 }
 
 lb_status lb_set_kernel(lb_ctx* c, int variant) {
   if (!c) return LB_ERR_ARG;
-  if (variant < 0 || variant > 2) return set_err(c, "kernel variant must be 0, 1 or 2"), LB_ERR_ARG;
-  if (variant == 2 && c->grid.nx % 8 != 0)
+  if (variant < 0 || variant > 3) return set_err(c, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
+  if (variant >= 2 && c->grid.nx % 8 != 0)
     return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
-  if (variant != c->kernel) {
+  const int kernel = variant == 3 ? 2 : variant;
+  const int deep = variant == 3 ? 1 : (variant == 2 ? 0 : c->deep);
+  if (kernel != c->kernel || deep != c->deep) {
     CK(cudaStreamSynchronize(c->stream));
     drop_graph(c);
   }
-  c->kernel = variant;
+  c->kernel = kernel;
+  c->deep = deep;
   return LB_OK;
 }
 

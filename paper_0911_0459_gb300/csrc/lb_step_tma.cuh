@@ -127,105 +127,125 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// The shared-memory ring of one CTA.  Staged rows are numbered by a running
+// counter k across every tile (and every step) the CTA processes: row k uses
+// stage k % NS and completes phase k / NS of that stage's barriers.
 template <int MODEL, class S, int BX, int NS>
-__global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 128 ? (NS > 4 ? 3 : 5) : (NS > 3 ? 2 : 3))) step_tma_kernel(TmaArgs<MODEL, S> a) {
+struct Ring {
   using L = TmaLayout<MODEL, S, BX, NS>;
   using T = typename S::T;
-  using A = typename S::A;
-  constexpr bool BIN = L::BIN;
-  constexpr int W = L::W;
-  constexpr int NWARPS = BX / 32;
-  extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * L::STAGE);
-  uint64_t* empty = full + NS;
-  auto stage_f = [&](int s) { return reinterpret_cast<T*>(smem + s * L::STAGE); };
-  auto stage_g = [&](int s) { return reinterpret_cast<T*>(smem + s * L::STAGE) + 9 * W; };
-  auto stage_g0 = [&](int s) { return reinterpret_cast<float*>(smem + s * L::STAGE + L::STAGE_T); };
+  unsigned char* smem;
+  uint64_t* full;
+  uint64_t* empty;
+  __device__ T* f(int s) const { return reinterpret_cast<T*>(smem + s * L::STAGE); }
+  __device__ T* g(int s) const { return reinterpret_cast<T*>(smem + s * L::STAGE) + 9 * L::W; }
+  __device__ float* g0(int s) const { return reinterpret_cast<float*>(smem + s * L::STAGE + L::STAGE_T); }
+};
 
-  const Geom& G = a.G;
-  const int nx = G.nx, ny = G.ny;
-  const size_t N = (size_t)nx * ny;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int xb = blockIdx.x * BX;
-  const int w = min(BX, nx - xb);     // multiple of 8
-  const int y0 = blockIdx.y * a.yc;
-  const int y1 = min(y0 + a.yc, ny);
-  const int nrows = y1 - y0 + 2;      // rows y0-1 .. y1 are staged
-
-  if (tid == 0) {
+template <int MODEL, class S, int BX, int NS>
+__device__ __forceinline__ Ring<MODEL, S, BX, NS> ring_init(unsigned char* smem) {
+  using L = TmaLayout<MODEL, S, BX, NS>;
+  Ring<MODEL, S, BX, NS> R;
+  R.smem = smem;
+  R.full = reinterpret_cast<uint64_t*>(smem + NS * L::STAGE);
+  R.empty = R.full + NS;
+  if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], NWARPS);
+      mbar_init(&R.full[s], 1);
+      mbar_init(&R.empty[s], BX / 32);
     }
     mbar_fence_init();
   }
   __syncthreads();
+  return R;
+}
 
-  if (warp == NWARPS) {
-    // ------------------------------------------------------------ producer
-    if (lane != 0) return;
-    const int lo = xb >= 8 ? xb - 8 : 0;
-    const int hi = min(xb + BX + 8, nx);
-    const int ncols = hi - lo;
-    const bool wl = xb == 0;           // left halo wraps to the row end
-    const bool wr = xb + BX + 8 > nx;  // right halo wraps to the row start
-    const int so = lo - (xb - 8);      // stage column of global column lo
-    const int sr = nx - (xb - 8);      // stage column of the right wrap chunk
-    const uint32_t ecols = (uint32_t)(ncols + (wl ? 8 : 0) + (wr ? 8 : 0));
-    const uint32_t total = ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
-    auto planes = [&](const T* base, int nplanes, T* dst0, size_t rowoff, uint64_t* bar) {
-      for (int i = 0; i < nplanes; ++i) {
-        const T* src = base + (size_t)i * N + rowoff;
-        T* d = dst0 + i * W;
-        bulk_g2s(d + so, src + lo, (uint32_t)ncols * sizeof(T), bar);
-        if (wl) bulk_g2s(d, src + (nx - 8), 8 * sizeof(T), bar);
-        if (wr) bulk_g2s(d + sr, src, 8 * sizeof(T), bar);
-      }
-    };
-    // every staged column inside the tube: rows outside the band are all solid
-    // and their populations are never read (ghosts replace them), so they are
-    // not copied
-    int d0 = xb - 8 - G.tube_x0;
-    d0 = ((d0 % nx) + nx) % nx;
-    const bool all_tube = G.tube_len > 0 && d0 + w + 16 <= G.tube_len;
-    bool ok = true;
-    int issued = 0;
-    for (int k = 0; k < nrows && ok; ++k) {
-      const int s = k % NS;
-      if (k >= NS && !mbar_wait(&empty[s], ((k / NS) - 1) & 1)) {
-        ok = false;
-        break;
-      }
-      const int yy = wrapi(y0 - 1 + k, ny);
-      if (all_tube && !row_in_band(G, yy)) {
-        mbar_arrive(&full[s]);
-        issued = k + 1;
-        continue;
-      }
-      const size_t rowoff = (size_t)yy * nx;
-      mbar_arrive_expect_tx(&full[s], total);
-      planes(a.src.f, L::NF, stage_f(s), rowoff, &full[s]);
-      if (BIN) planes(a.src.g, L::NG, stage_g(s), rowoff, &full[s]);
-      if (L::NG0) {
-        const float* src = a.src.g0 + rowoff;
-        float* d = stage_g0(s);
-        bulk_g2s(d + so, src + lo, (uint32_t)ncols * 4u, &full[s]);
-        if (wl) bulk_g2s(d, src + (nx - 8), 32u, &full[s]);
-        if (wr) bulk_g2s(d + sr, src, 32u, &full[s]);
-      }
-      issued = k + 1;
+// Producer (one lane): stage rows y0 - 1 .. y1 of the tile starting at column xb
+// as ring rows kbase, kbase + 1, ...  Returns false if a wait ran out of time;
+// `issued` counts the ring rows handed to the copy engine.
+template <int MODEL, class S, int BX, int NS>
+__device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, const Buf<S>& src, int xb, int y0,
+                             int y1, unsigned kbase, unsigned& issued) {
+  using L = TmaLayout<MODEL, S, BX, NS>;
+  using T = typename S::T;
+  constexpr bool BIN = L::BIN;
+  constexpr int W = L::W;
+  const int nx = G.nx, ny = G.ny;
+  const size_t N = (size_t)nx * ny;
+  const int w = min(BX, nx - xb);
+  const int nrows = y1 - y0 + 2;
+  const int lo = xb >= 8 ? xb - 8 : 0;
+  const int hi = min(xb + BX + 8, nx);
+  const int ncols = hi - lo;
+  const bool wl = xb == 0;           // left halo wraps to the row end
+  const bool wr = xb + BX + 8 > nx;  // right halo wraps to the row start
+  const int so = lo - (xb - 8);      // stage column of global column lo
+  const int sr = nx - (xb - 8);      // stage column of the right wrap chunk
+  const uint32_t ecols = (uint32_t)(ncols + (wl ? 8 : 0) + (wr ? 8 : 0));
+  const uint32_t total = ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
+  auto planes = [&](const T* base, int nplanes, T* dst0, size_t rowoff, uint64_t* bar) {
+    for (int i = 0; i < nplanes; ++i) {
+      const T* sp = base + (size_t)i * N + rowoff;
+      T* d = dst0 + i * W;
+      bulk_g2s(d + so, sp + lo, (uint32_t)ncols * sizeof(T), bar);
+      if (wl) bulk_g2s(d, sp + (nx - 8), 8 * sizeof(T), bar);
+      if (wr) bulk_g2s(d + sr, sp, 8 * sizeof(T), bar);
     }
-    if (!ok) atomicExch(a.err, 1);
-    // stay until every copy issued by this CTA has landed (bounded)
-    const unsigned long long t0 = globaltimer_ns();
-    for (int k = max(0, issued - NS); k < issued; ++k)
-      while (!mbar_try_wait(&full[k % NS], (k / NS) & 1) && globaltimer_ns() - t0 < kWaitLimitNs) {
-      }
-    return;
+  };
+  // every staged column inside the tube: rows outside the band are all solid and
+  // their populations are never read (ghosts replace them), so they are not copied
+  int d0 = xb - 8 - G.tube_x0;
+  d0 = ((d0 % nx) + nx) % nx;
+  const bool all_tube = G.tube_len > 0 && d0 + w + 16 <= G.tube_len;
+  for (int j = 0; j < nrows; ++j) {
+    const unsigned k = kbase + j;
+    const int s = k % NS;
+    if (k >= NS && !mbar_wait(&R.empty[s], ((k / NS) - 1) & 1)) return false;
+    const int yy = wrapi(y0 - 1 + j, ny);
+    if (all_tube && !row_in_band(G, yy)) {
+      mbar_arrive(&R.full[s]);
+      issued = k + 1;
+      continue;
+    }
+    const size_t rowoff = (size_t)yy * nx;
+    mbar_arrive_expect_tx(&R.full[s], total);
+    planes(src.f, L::NF, R.f(s), rowoff, &R.full[s]);
+    if (BIN) planes(src.g, L::NG, R.g(s), rowoff, &R.full[s]);
+    if (L::NG0) {
+      const float* sp = src.g0 + rowoff;
+      float* d = R.g0(s);
+      bulk_g2s(d + so, sp + lo, (uint32_t)ncols * 4u, &R.full[s]);
+      if (wl) bulk_g2s(d, sp + (nx - 8), 32u, &R.full[s]);
+      if (wr) bulk_g2s(d + sr, sp, 32u, &R.full[s]);
+    }
+    issued = k + 1;
   }
+  return true;
+}
 
-  // -------------------------------------------------------------- consumers
+// Producer: wait (bounded) until the last copies issued have landed, so that none
+// lands in shared memory after the CTA has released it.
+template <int MODEL, class S, int BX, int NS>
+__device__ void drain_ring(const Ring<MODEL, S, BX, NS>& R, unsigned issued) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned k = issued > NS ? issued - NS : 0; k < issued; ++k)
+    while (!mbar_try_wait(&R.full[k % NS], (k / NS) & 1) && globaltimer_ns() - t0 < kWaitLimitNs) {
+    }
+}
+
+// Consumer warp `warp` (0 .. BX/32 - 1): collide rows y0 .. y1 - 1 of the tile
+// from ring rows kbase, kbase + 1, ... and push the results to dst.  Returns
+// false (in every lane of the warp) if a wait ran out of time.
+template <int MODEL, class S, int BX, int NS>
+__device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, const Phys<typename S::A>& P,
+                             const Buf<S>& dst, int xb, int y0, int y1, unsigned kbase, int warp, int lane) {
+  using L = TmaLayout<MODEL, S, BX, NS>;
+  using A = typename S::A;
+  constexpr bool BIN = L::BIN;
+  constexpr int W = L::W;
+  const int nx = G.nx, ny = G.ny;
+  const size_t N = (size_t)nx * ny;
+  const int w = min(BX, nx - xb);
   const int c0 = xb + warp * 32;      // first column of this warp
   const int x = c0 + lane;
   const bool act = x < xb + w;
@@ -233,10 +253,10 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 
 
   auto load_pop = [&](int s, int c, A f[9], A g[9]) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = S::pf(stage_f(s), W, c, i);
+    for (int i = 0; i < 9; ++i) f[i] = S::pf(R.f(s), W, c, i);
     if (BIN) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = S::pg(stage_g(s), stage_g0(s), W, c, i);
+      for (int i = 0; i < 9; ++i) g[i] = S::pg(R.g(s), R.g0(s), W, c, i);
     }
   };
   // One row of the stencil window: this lane's rho/phi and its left/right
@@ -249,7 +269,7 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 
   const bool edge = lane == 0 || lane == 31;
   // Sum this lane's column (f, g keep its populations for the collision); the edge
   // lanes also sum the warp's halo column; then take the neighbours by shuffles.
-  auto sums = [&](int s, A f[9], A g[9], Row& R) {
+  auto sums = [&](int s, A f[9], A g[9], Row& Rw) {
     load_pop(s, sc, f, g);
     const A r = sum9(f);
     const A p = BIN ? sum9(g) : A(0);
@@ -261,18 +281,18 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 
       pe = BIN ? sum9(ge) : A(0);
     }
     const A rl = __shfl_up_sync(0xffffffffu, r, 1), rr = __shfl_down_sync(0xffffffffu, r, 1);
-    R.rc = r;
-    R.rl = lane == 0 ? re : rl;
-    R.rr = lane == 31 ? re : rr;
+    Rw.rc = r;
+    Rw.rl = lane == 0 ? re : rl;
+    Rw.rr = lane == 31 ? re : rr;
     if (BIN) {
       const A pl = __shfl_up_sync(0xffffffffu, p, 1), pr = __shfl_down_sync(0xffffffffu, p, 1);
-      R.pc = p;
-      R.pl = lane == 0 ? pe : pl;
-      R.pr = lane == 31 ? pe : pr;
+      Rw.pc = p;
+      Rw.pl = lane == 0 ? pe : pl;
+      Rw.pr = lane == 31 ? pe : pr;
     }
   };
 
-  // loop-invariant column data
+  // column data of this lane
   const int xm = x == 0 ? nx - 1 : x - 1;
   const int xp = x + 1 >= nx ? 0 : x + 1;
   const bool tubed = G.tube_len > 0;
@@ -284,45 +304,39 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 
   const bool warp_tube = __any_sync(0xffffffffu, tc[0] || tc[1] || tc[2]);
 
   // rows k-1, k, k+1 of the stencil window
-  Row R[3];
-  bool failed = false;
+  Row Rw[3];
   A fa[9], ga[9];  // populations of the row to collide next
-  // prologue: rows y0 - 1 (k = 0, stencil halo only) and y0 (k = 1)
-  for (int k = 0; k < 2; ++k) {
-    if (!mbar_wait(&full[k], 0)) {
-      failed = true;
-      break;
-    }
-    sums(k, fa, ga, R[k + 1]);
+  // prologue: rows y0 - 1 (stencil halo only) and y0
+  for (int j = 0; j < 2; ++j) {
+    const unsigned k = kbase + j;
+    if (!__all_sync(0xffffffffu, mbar_wait(&R.full[k % NS], (k / NS) & 1))) return false;
+    sums(k % NS, fa, ga, Rw[j + 1]);
     // the populations are in registers now: the stage can be refilled
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[k]);
+    if (lane == 0) mbar_arrive(&R.empty[k % NS]);
   }
 
-  for (int y = y0; y < y1 && !failed; ++y) {
-    const int kc = y - y0 + 1;  // staged index of row y
-    const int sn = (kc + 1) % NS;
+  for (int y = y0; y < y1; ++y) {
+    const unsigned kn = kbase + (y - y0) + 2;  // ring row of y + 1
+    const int sn = kn % NS;
     // shift the row window and add row y + 1
-    R[0] = R[1];
-    R[1] = R[2];
-    if (!mbar_wait(&full[sn], ((kc + 1) / NS) & 1)) {
-      failed = true;
-      break;
-    }
+    Rw[0] = Rw[1];
+    Rw[1] = Rw[2];
+    if (!__all_sync(0xffffffffu, mbar_wait(&R.full[sn], (kn / NS) & 1))) return false;
     A fn[9], gn[9];
-    sums(sn, fn, gn, R[2]);
+    sums(sn, fn, gn, Rw[2]);
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[sn]);
+    if (lane == 0) mbar_arrive(&R.empty[sn]);
     A vr[3][3], vp[3][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      vr[j][0] = R[j].rl;
-      vr[j][1] = R[j].rc;
-      vr[j][2] = R[j].rr;
+      vr[j][0] = Rw[j].rl;
+      vr[j][1] = Rw[j].rc;
+      vr[j][2] = Rw[j].rr;
       if (BIN) {
-        vp[j][0] = R[j].pl;
-        vp[j][1] = R[j].pc;
-        vp[j][2] = R[j].pr;
+        vp[j][0] = Rw[j].pl;
+        vp[j][1] = Rw[j].pc;
+        vp[j][2] = Rw[j].pr;
       }
     }
     const int yy = wrapi(y, ny);
@@ -351,9 +365,9 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 
           for (int i = 0; i < 3; ++i) sol[j][i] = false;
       }
       A fs[9], ge[9];
-      collide_node<MODEL, A>(a.P, vr, vp, sol, bnd, fa, fs, ge);
+      collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
       const int rowb[3] = {ym * nx, yy * nx, yp * nx};
-      push_node<MODEL, S>(a.dst, N, rowb, col, sol, bnd, fs, ge);
+      push_node<MODEL, S>(dst, N, rowb, col, sol, bnd, fs, ge);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -361,7 +375,31 @@ __global__ void __launch_bounds__(BX + 32, BX == 64 ? (NS > 4 ? 4 : 8) : (BX == 
       if (BIN) ga[i] = gn[i];
     }
   }
-  if (failed && lane == 0) atomicExch(a.err, 1);
+  return true;
+}
+
+// Resident CTAs per SM the staged kernels are compiled for (caps their registers).
+constexpr int tma_min_blocks(int bx, int ns) {
+  return bx == 64 ? (ns > 4 ? 4 : 8) : (bx == 128 ? (ns > 4 ? 3 : 5) : (ns > 3 ? 2 : 3));
+}
+
+template <int MODEL, class S, int BX, int NS>
+__global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) step_tma_kernel(TmaArgs<MODEL, S> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const Ring<MODEL, S, BX, NS> R = ring_init<MODEL, S, BX, NS>(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int xb = blockIdx.x * BX;
+  const int y0 = blockIdx.y * a.yc;
+  const int y1 = min(y0 + a.yc, a.G.ny);
+  if (warp == BX / 32) {
+    if (lane != 0) return;
+    unsigned issued = 0;
+    if (!produce_tile<MODEL, S, BX, NS>(R, a.G, a.src, xb, y0, y1, 0u, issued)) atomicExch(a.err, 1);
+    drain_ring<MODEL, S, BX, NS>(R, issued);
+    return;
+  }
+  if (!consume_tile<MODEL, S, BX, NS>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane) && lane == 0)
+    atomicExch(a.err, 1);
 }
 
 }  // namespace lbk

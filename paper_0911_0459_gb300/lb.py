@@ -99,6 +99,8 @@ def library():
         "lb_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(C.c_double)]),
         "lb_batch_set_barrier": (C.c_int, [vp, C.c_uint, C.c_double]),
+        "lb_batch_set_kernel": (C.c_int, [vp, C.c_int]),
+        "lb_batch_get_kernel": (C.c_int, [vp, C.POINTER(C.c_int)]),
         "lb_batch_time": (C.c_long, [vp]),
         "lb_batch_fluid_nodes": (C.c_long, [vp, C.c_int]),
         "lb_batch_last_error": (C.c_char_p, [vp]),
@@ -117,7 +119,7 @@ def exported_symbols():
             "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
             "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
             "lb_batch_populations", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
-            "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error"]
+            "lb_batch_set_kernel", "lb_batch_get_kernel", "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error"]
 
 
 class _TorchAllocator:
@@ -296,7 +298,8 @@ class Lattice:
         _check(library().lb_set_tile(self.h, int(tx), int(ty)), self.h)
 
     def set_kernel(self, variant):
-        """0 automatic, 1 sliding-window kernel, 2 staged (bulk-copy) kernel."""
+        """0 automatic, 1 sliding-window kernel, 2 / 3 staged (bulk-copy) kernel with
+        its shallow / deep ring."""
         _check(library().lb_set_kernel(self.h, int(variant)), self.h)
 
     def kernel(self):
@@ -409,6 +412,16 @@ class Batch:
 
     def set_barrier(self, absent_blocks=0, limit_seconds=2.0):
         _bcheck(library().lb_batch_set_barrier(self.h, int(absent_blocks), float(limit_seconds)), self.h)
+
+    def set_kernel(self, variant):
+        """0 automatic, 1 sliding-window body, 2 / 3 staged body with its shallow /
+        deep ring (every nx % 8 == 0)."""
+        _bcheck(library().lb_batch_set_kernel(self.h, int(variant)), self.h)
+
+    def kernel(self):
+        v = C.c_int()
+        _bcheck(library().lb_batch_get_kernel(self.h, C.byref(v)), self.h)
+        return v.value
 
     @property
     def time(self):

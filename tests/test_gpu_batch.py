@@ -15,9 +15,9 @@ from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, Batc
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
 
 
-def small_sweep(seed=7, n=6):
+def small_sweep(seed=7, n=6, align=8):
     """Uneven capillaries shaped like the sweep, shortened so the oracle keeps up."""
-    caps = W.sweep(seed=seed, n=n, lengths=(96, 300))
+    caps = W.sweep(seed=seed, n=n, lengths=(96, 300), align=align)
     out = []
     for c in caps:
         c.nx = c.tube_x0 + c.tube_len   # keep the reservoirs, short tubes
@@ -25,21 +25,74 @@ def small_sweep(seed=7, n=6):
     return out
 
 
+@pytest.mark.parametrize("body", [1, 2, 3])
 @pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F64, STORAGE_F16DEV])
-def test_batch_is_bitwise_identical_to_independent_lattices(storage):
+def test_batch_is_bitwise_identical_to_independent_lattices(storage, body):
+    """Every body of the persistent kernel (sliding window; staged with the
+    shallow and the deep ring) against one lattice per capillary, over tiles
+    that change between launches and ragged last tiles and bands."""
     caps = small_sweep()
     b = Batch(caps, storage=storage)
-    for tx, ty in ((64, 4), (128, 16), (256, 64)):
+    assert b.kernel() == 2   # every nx is a multiple of 8: staged by default
+    b.set_kernel(body)
+    assert b.kernel() == body
+    for tx, ty in ((64, 4), (128, 16), (256, 64), (128, 5)):
         b.set_tile(tx, ty)
         b.step(13)
     total = b.time
+    red = b.lengths()
     for i, c in enumerate(caps):
         lat = Lattice.from_workload(c, storage=storage)
         lat.step(total)
         fb, gb = b.populations(i, rested=False)
         fl, gl = lat.populations(rested=False)
         assert np.array_equal(fb, fl) and np.array_equal(gb, gl), i
+        # the chunked batch reductions against the single-lattice ones: l from the
+        # same centre-line values, sums in another order
+        d = lat.filled_length()
+        assert red[i, 0] == d["l"], i
+        np.testing.assert_allclose(red[i, 1:], [d["l_vol"], d["mass"], d["phi_sum"]], rtol=1e-12,
+                                   atol=1e-12 * c.nodes)
         lat.close()
+    b.close()
+
+
+def test_batch_with_unaligned_rows_uses_the_sliding_window_body():
+    caps = small_sweep(seed=9, n=4, align=1)
+    assert any(c.nx % 8 for c in caps)
+    b = Batch(caps)
+    assert b.kernel() == 1
+    with pytest.raises(LbError):
+        b.set_kernel(2)
+    b.step(9)
+    for i, c in enumerate(caps):
+        lat = Lattice.from_workload(c)
+        lat.step(9)
+        fb, gb = b.populations(i, rested=False)
+        fl, gl = lat.populations(rested=False)
+        assert np.array_equal(fb, fl) and np.array_equal(gb, gl), i
+        lat.close()
+    b.close()
+
+
+def test_staged_body_long_run_matches_sliding_body():
+    """Many steps in one persistent launch: the ring counter runs across
+    hundreds of tiles and steps (and is renormalised) without drifting."""
+    caps = small_sweep(seed=4, n=5)
+    a = Batch(caps)
+    b = Batch(caps)
+    a.set_kernel(1)
+    b.set_kernel(3)
+    a.set_tile(64, 4)
+    b.set_tile(64, 4)
+    a.step(400)
+    b.step(400)
+    for i in range(len(caps)):
+        fa, ga = a.populations(i, rested=False)
+        fb, gb = b.populations(i, rested=False)
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb), i
+    np.testing.assert_array_equal(a.lengths(), b.lengths())
+    a.close()
     b.close()
 
 
@@ -75,11 +128,13 @@ def test_batch_autotune_and_fluid_count():
     b.close()
 
 
-def test_grid_barrier_timeout_is_reported_without_hanging():
+@pytest.mark.parametrize("body", [1, 2])
+def test_grid_barrier_timeout_is_reported_without_hanging(body):
     """Failure injection on the host: the barrier waits for an arrival that never
     comes, gives up after its short limit, and the host reads LB_ERR_TIMEOUT."""
     caps = small_sweep(seed=5, n=3)
     b = Batch(caps)
+    b.set_kernel(body)
     b.set_barrier(absent_blocks=1, limit_seconds=0.05)
     b.step(3)
     with pytest.raises(LbError) as e:

@@ -290,19 +290,23 @@ def test_staged_kernel_is_bitwise_identical_to_sliding_window(model, storage):
         fields = W.random_state_fields(cap.nx, cap.ny, seed=3, model=cap.params.model)
         for tx, ty in ((64, 1), (128, 5), (256, 16), (64, cap.ny)):
             a = Lattice.from_workload(cap, storage=storage).init_fields(*fields)
-            b = Lattice.from_workload(cap, storage=storage).init_fields(*fields)
             a.set_kernel(1)
-            b.set_kernel(2)
             a.set_tile(tx, ty)
-            b.set_tile(tx, ty)
             a.step(7)
-            b.step(7)
             fa, ga = a.populations(False)
-            fb, gb = b.populations(False)
-            assert np.array_equal(fa, fb), (cap.name, tx, ty)
-            if ga is not None:
-                assert np.array_equal(ga, gb), (cap.name, tx, ty)
-            b.sync()   # no device-side wait gave up
+            for variant in (2, 3):   # shallow and deep ring of row stages
+                b = Lattice.from_workload(cap, storage=storage).init_fields(*fields)
+                b.set_kernel(variant)
+                assert b.kernel() == variant
+                b.set_tile(tx, ty)
+                b.step(7)
+                fb, gb = b.populations(False)
+                assert np.array_equal(fa, fb), (cap.name, tx, ty, variant)
+                if ga is not None:
+                    assert np.array_equal(ga, gb), (cap.name, tx, ty, variant)
+                b.sync()   # no device-side wait gave up
+                b.close()
+            a.close()
 
 
 def test_staged_kernel_rejected_when_rows_are_not_16_byte_aligned():

@@ -138,11 +138,12 @@ def viscosities_for_ratio(ratio: float):
 
 def sweep(seed: int = 0, n: int = 256, steps: int = 20000,
           lengths=(1024, 8192), fixed_len: Optional[int] = None,
-          vary_gamma: bool = False, liquid_cols: int = 128) -> List[Capillary]:
+          vary_gamma: bool = False, liquid_cols: int = 128, align: int = 8) -> List[Capillary]:
     """Seeded sweep of uneven binary capillaries.
 
-    H uniform in {16, 24, ..., 128}; tube length uniform in [1024, 8192]
-    (or fixed_len); ny = H + 8; liquid reservoir 128 columns and a gas buffer of
+    H uniform in {16, 24, ..., 128}; tube length uniform over the multiples of
+    `align` in [1024, 8192] (or fixed_len), so that with the default align every
+    nx = 160 + L is a multiple of 8; ny = H + 8; liquid reservoir 128 columns and a gas buffer of
     32 columns in front of it; viscosity ratio uniform in {1, 5, 10, 50, 100};
     theta uniform in [30, 80] degrees.  With vary_gamma the surface tension is
     varied by drawing A = kappa uniformly in [0.03, 0.05].  liquid_cols widens
@@ -152,7 +153,11 @@ def sweep(seed: int = 0, n: int = 256, steps: int = 20000,
     out = []
     for k in range(n):
         H = int(rng.choice(np.arange(16, 129, 8)))
-        L = int(fixed_len) if fixed_len else int(rng.integers(lengths[0], lengths[1] + 1))
+        if fixed_len:
+            L = int(fixed_len)
+        else:
+            lo, hi = -(-lengths[0] // align), lengths[1] // align
+            L = align * int(rng.integers(lo, hi + 1))
         ratio = float(rng.choice(RATIOS))
         theta = float(rng.uniform(30.0, 80.0))
         Ak = float(rng.uniform(0.03, 0.05)) if vary_gamma else 0.04
