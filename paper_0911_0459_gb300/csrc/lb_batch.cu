@@ -38,7 +38,8 @@ struct lb_batch {
   void* g[2];
   float* g0[2];
   void* d_caps;
-  TileDesc* d_tiles;
+  TileDesc* d_tiles;   // tiles in schedule order: CTA k takes d_tiles[start[k] .. start[k+1])
+  int* d_start;
   int ntiles;
   RedChunk* d_chunks;  // reduction chunks of every lattice, lattice by lattice
   int2* d_range;       // per lattice: first chunk, number of chunks
@@ -173,61 +174,37 @@ static lb_status init_lattice(lb_batch* b, int i) {
   return LB_OK;
 }
 
-static lb_status build_tiles(lb_batch* b) {
-  std::vector<TileDesc> tiles;
-  for (int i = 0; i < b->n; ++i) {
-    const lb_grid& g = b->grids[i];
-    const lb_walls& w = b->walls[i];
-    for (int y0 = 0; y0 < g.ny; y0 += b->tile_y)
-      for (int xb = 0; xb < g.nx; xb += b->tile_x) {
-        const int y1 = std::min(y0 + b->tile_y, g.ny);
-        const int x1 = std::min(xb + b->tile_x, g.nx);
-        bool any_fluid = false;
-        for (int y = y0; y < y1 && !any_fluid; ++y)
-          for (int x = xb; x < x1 && !any_fluid; ++x) any_fluid = !solid_h(g, w, x, y);
-        if (any_fluid) tiles.push_back(TileDesc{i, xb, y0, y1});
-      }
-  }
-  b->ntiles = (int)tiles.size();
-  if (b->d_tiles) {
-    if (b->have_alloc)
-      b->alloc.free_fn(b->d_tiles, (void*)b->stream, b->alloc.user);
-    else
-      cudaFree(b->d_tiles);
-    b->owned.erase(std::remove(b->owned.begin(), b->owned.end(), (void*)b->d_tiles), b->owned.end());
-  }
-  b->d_tiles = (TileDesc*)balloc(b, std::max<size_t>(1, tiles.size()) * sizeof(TileDesc));
-  if (!b->d_tiles) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
-  BCK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice,
-                      b->stream));
-  BCK(cudaStreamSynchronize(b->stream));
-  return LB_OK;
+// 1 or 2: the body the next launch uses
+static int batch_variant(const lb_batch* b) {
+  if (b->kernel == 0) return b->staged_ok ? 2 : 1;
+  return b->kernel;
 }
 
-template <class S, int BX>
-static cudaError_t launch_batch_t(lb_batch* b, int nsteps, cudaStream_t s) {
-  BatchArgs<S> a;
+template <class S>
+static void fill_args(const lb_batch* b, int nsteps, BatchArgs<S>& a) {
   a.caps = (const CapDesc<typename S::A>*)b->d_caps;
   a.tiles = b->d_tiles;
-  a.ntiles = b->ntiles;
+  a.start = b->d_start;
   a.fa = (typename S::T*)b->f[0]; a.ga = (typename S::T*)b->g[0]; a.g0a = b->g0[0];
   a.fb = (typename S::T*)b->f[1]; a.gb = (typename S::T*)b->g[1]; a.g0b = b->g0[1];
   a.nsteps = nsteps;
   a.parity = b->parity;
   a.bar = b->d_bar;
+  a.expected = (unsigned)b->grid_blocks + b->extra_arrivals;
   a.limit_ns = b->limit_ns;
   a.err = b->d_err;
-  int dev = 0, sms = 0, per = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<S, BX>, BX, 0);
-  if (e != cudaSuccess) return e;
-  int blocks = std::max(1, std::min(per * sms, b->ntiles));
-  b->grid_blocks = blocks;
-  a.expected = (unsigned)blocks + b->extra_arrivals;
+}
+
+// Either launches the current body over nsteps steps (per == NULL) or returns
+// in *per how many of its CTAs are resident on one SM.
+template <class S, int BX>
+static cudaError_t run_sliding(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
+  if (per) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_step_kernel<S, BX>, BX, 0);
+  BatchArgs<S> a;
+  fill_args(b, nsteps, a);
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
-  cfg.gridDim = dim3(blocks);
+  cfg.gridDim = dim3(b->grid_blocks);
   cfg.blockDim = dim3(BX);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -239,7 +216,7 @@ static cudaError_t launch_batch_t(lb_batch* b, int nsteps, cudaStream_t s) {
 }
 
 template <class S, int BX, int NS>
-static cudaError_t launch_batch_tma(lb_batch* b, int nsteps, cudaStream_t s) {
+static cudaError_t run_staged(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
   using L = TmaLayout<MODEL_BINARY, S, BX, NS>;
   static bool configured = false;  // dynamic shared memory opt-in, once per process
   if (!configured) {
@@ -248,30 +225,12 @@ static cudaError_t launch_batch_tma(lb_batch* b, int nsteps, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  if (per) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_tma_kernel<S, BX, NS>, BX + 32, L::BYTES);
   BatchArgs<S> a;
-  a.caps = (const CapDesc<typename S::A>*)b->d_caps;
-  a.tiles = b->d_tiles;
-  a.ntiles = b->ntiles;
-  a.fa = (typename S::T*)b->f[0]; a.ga = (typename S::T*)b->g[0]; a.g0a = b->g0[0];
-  a.fb = (typename S::T*)b->f[1]; a.gb = (typename S::T*)b->g[1]; a.g0b = b->g0[1];
-  a.nsteps = nsteps;
-  a.parity = b->parity;
-  a.bar = b->d_bar;
-  a.limit_ns = b->limit_ns;
-  a.err = b->d_err;
-  int dev = 0, sms = 0, per = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_tma_kernel<S, BX, NS>, BX + 32, L::BYTES);
-  if (e != cudaSuccess) return e;
-  if (per < 1) return cudaErrorInvalidConfiguration;
-  int blocks = std::max(1, std::min(per * sms, b->ntiles));
-  b->grid_blocks = blocks;
-  a.expected = (unsigned)blocks + b->extra_arrivals;
+  fill_args(b, nsteps, a);
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
-  cfg.gridDim = dim3(blocks);
+  cfg.gridDim = dim3(b->grid_blocks);
   cfg.blockDim = dim3(BX + 32);
   cfg.dynamicSmemBytes = L::BYTES;
   cfg.stream = s;
@@ -283,29 +242,108 @@ static cudaError_t launch_batch_tma(lb_batch* b, int nsteps, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, batch_tma_kernel<S, BX, NS>, a);
 }
 
-// 1 or 2: the body the next launch uses
-static int batch_variant(const lb_batch* b) {
-  if (b->kernel == 0) return b->staged_ok ? 2 : 1;
-  return b->kernel;
-}
-
 template <class S>
-static cudaError_t launch_batch_s(lb_batch* b, int nsteps, cudaStream_t s) {
+static cudaError_t run_s(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
   if (batch_variant(b) == 2) {
     // ring depths as for the single-lattice staged kernel
-    if (b->tile_x == 64) return b->deep ? launch_batch_tma<S, 64, 8>(b, nsteps, s) : launch_batch_tma<S, 64, 4>(b, nsteps, s);
-    if (b->tile_x == 128) return b->deep ? launch_batch_tma<S, 128, 6>(b, nsteps, s) : launch_batch_tma<S, 128, 4>(b, nsteps, s);
-    return b->deep ? launch_batch_tma<S, 256, 4>(b, nsteps, s) : launch_batch_tma<S, 256, 3>(b, nsteps, s);
+    if (b->tile_x == 64) return b->deep ? run_staged<S, 64, 8>(b, nsteps, s, per) : run_staged<S, 64, 4>(b, nsteps, s, per);
+    if (b->tile_x == 128) return b->deep ? run_staged<S, 128, 6>(b, nsteps, s, per) : run_staged<S, 128, 4>(b, nsteps, s, per);
+    return b->deep ? run_staged<S, 256, 4>(b, nsteps, s, per) : run_staged<S, 256, 3>(b, nsteps, s, per);
   }
-  if (b->tile_x == 64) return launch_batch_t<S, 64>(b, nsteps, s);
-  if (b->tile_x == 128) return launch_batch_t<S, 128>(b, nsteps, s);
-  return launch_batch_t<S, 256>(b, nsteps, s);
+  if (b->tile_x == 64) return run_sliding<S, 64>(b, nsteps, s, per);
+  if (b->tile_x == 128) return run_sliding<S, 128>(b, nsteps, s, per);
+  return run_sliding<S, 256>(b, nsteps, s, per);
 }
 
-static cudaError_t launch_batch(lb_batch* b, int nsteps, cudaStream_t s) {
-  if (b->storage == LB_STORAGE_F64) return launch_batch_s<SF64>(b, nsteps, s);
-  if (b->storage == LB_STORAGE_F32) return launch_batch_s<SF32>(b, nsteps, s);
-  return launch_batch_s<SF16>(b, nsteps, s);
+static cudaError_t run_batch(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
+  if (b->storage == LB_STORAGE_F64) return run_s<SF64>(b, nsteps, s, per);
+  if (b->storage == LB_STORAGE_F32) return run_s<SF32>(b, nsteps, s, per);
+  return run_s<SF16>(b, nsteps, s, per);
+}
+
+static cudaError_t launch_batch(lb_batch* b, int nsteps, cudaStream_t s) { return run_batch(b, nsteps, s, NULL); }
+
+static void free_owned(lb_batch* b, void* p) {
+  if (!p) return;
+  if (b->have_alloc)
+    b->alloc.free_fn(p, (void*)b->stream, b->alloc.user);
+  else
+    cudaFree(p);
+  b->owned.erase(std::remove(b->owned.begin(), b->owned.end(), p), b->owned.end());
+}
+
+// Tiles of every lattice for the current body and tile shape, and their
+// schedule.  A CTA of the persistent kernel takes a fixed list of tiles every
+// step and all CTAs meet at a grid barrier after it, so a step lasts as long as
+// the longest list.  The lists are balanced by longest-processing-time-first on
+// an estimated cost (every staged row costs its row sums across the tile's
+// width, every fluid node its collision), then each list is put back in tile
+// order so that CTAs working at the same time touch neighbouring rows.
+static lb_status build_tiles(lb_batch* b) {
+  std::vector<TileDesc> tiles;
+  std::vector<double> cost;
+  for (int i = 0; i < b->n; ++i) {
+    const lb_grid& g = b->grids[i];
+    const lb_walls& w = b->walls[i];
+    // solid nodes are the tube's columns outside its band of rows: count them
+    // from prefix sums of tube columns and of rows outside the band
+    std::vector<long> tc(g.nx + 1, 0), ob(g.ny + 1, 0);
+    for (int x = 0; x < g.nx; ++x) tc[x + 1] = tc[x] + solid_h(g, w, x, (w.tube_y0 + w.tube_h) % g.ny);
+    for (int y = 0; y < g.ny; ++y) ob[y + 1] = ob[y] + solid_h(g, w, w.tube_x0, y);
+    for (int y0 = 0; y0 < g.ny; y0 += b->tile_y)
+      for (int xb = 0; xb < g.nx; xb += b->tile_x) {
+        const int y1 = std::min(y0 + b->tile_y, g.ny);
+        const int x1 = std::min(xb + b->tile_x, g.nx);
+        const long fluid = (long)(y1 - y0) * (x1 - xb) - (tc[x1] - tc[xb]) * (ob[y1] - ob[y0]);
+        if (fluid) {
+          tiles.push_back(TileDesc{i, xb, y0, y1});
+          cost.push_back(0.3 * (y1 - y0 + 2) * b->tile_x + (double)fluid);
+        }
+      }
+  }
+  b->ntiles = (int)tiles.size();
+  int dev = 0, sms = 0, per = 0;
+  BCK(cudaGetDevice(&dev));
+  BCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BCK(run_batch(b, 0, b->stream, &per));
+  if (per < 1) return berr(b, "the persistent kernel does not fit on an SM"), LB_ERR_CUDA;
+  const int blocks = std::max(1, std::min(per * sms, b->ntiles));
+  // longest processing time first onto the least loaded CTA
+  std::vector<int> order(tiles.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return cost[p] > cost[q]; });
+  std::vector<std::pair<double, int>> heap;
+  for (int k = 0; k < blocks; ++k) heap.push_back({0.0, k});
+  auto cmp = [](const std::pair<double, int>& p, const std::pair<double, int>& q) {
+    return p.first > q.first || (p.first == q.first && p.second > q.second);
+  };
+  std::make_heap(heap.begin(), heap.end(), cmp);
+  std::vector<std::vector<int>> lists(blocks);
+  for (int t : order) {
+    std::pop_heap(heap.begin(), heap.end(), cmp);
+    heap.back().first += cost[t];
+    lists[heap.back().second].push_back(t);
+    std::push_heap(heap.begin(), heap.end(), cmp);
+  }
+  std::vector<TileDesc> sched;
+  std::vector<int> start(blocks + 1, 0);
+  sched.reserve(tiles.size());
+  for (int k = 0; k < blocks; ++k) {
+    std::sort(lists[k].begin(), lists[k].end());
+    for (int t : lists[k]) sched.push_back(tiles[t]);
+    start[k + 1] = (int)sched.size();
+  }
+  free_owned(b, b->d_tiles);
+  free_owned(b, b->d_start);
+  b->d_tiles = (TileDesc*)balloc(b, std::max<size_t>(1, sched.size()) * sizeof(TileDesc));
+  b->d_start = (int*)balloc(b, start.size() * sizeof(int));
+  if (!b->d_tiles || !b->d_start) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  BCK(cudaMemcpyAsync(b->d_tiles, sched.data(), sched.size() * sizeof(TileDesc), cudaMemcpyHostToDevice,
+                      b->stream));
+  BCK(cudaMemcpyAsync(b->d_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  b->grid_blocks = blocks;
+  return LB_OK;
 }
 
 template <class S>
@@ -683,11 +721,11 @@ lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, do
   if (st) return st;
   st = check_err(b);
   if (st) return st;
-  st = lb_batch_set_tile(b, bx, by);
-  if (st) return st;
   // an automatic choice stays automatic unless tuning preferred the other body
   if (keep_kernel != 0 || bk != batch_variant(b)) b->kernel = bk;
   b->deep = bd;
+  st = lb_batch_set_tile(b, bx, by);  // rebuilds the schedule for this body
+  if (st) return st;
   if (tile_x) *tile_x = bx;
   if (tile_y) *tile_y = by;
   if (ms_per_step) *ms_per_step = best / (2.0 * steps);
@@ -710,7 +748,7 @@ lb_status lb_batch_set_kernel(lb_batch* b, int variant) {
   BCK(cudaStreamSynchronize(b->stream));
   b->kernel = variant == 3 ? 2 : variant;
   if (variant >= 2) b->deep = variant == 3;
-  return LB_OK;
+  return build_tiles(b);  // resident CTAs, hence the schedule, depend on the body
 }
 
 lb_status lb_batch_get_kernel(const lb_batch* b, int* variant) {

@@ -1,9 +1,8 @@
 // Batched capillaries: one persistent kernel advances every capillary of a
 // sweep.  The lattices live in one arena (two buffers); a flat list of tiles
 // (capillary, column block, row band) covers all of them.  Each CTA processes
-// tiles blockIdx.x, blockIdx.x + gridDim.x, ... of a time step with the
-// sliding-window band update, then waits at a grid barrier before the next
-// step.  The launch is cooperative, so all CTAs are resident; the barrier still
+// its own list of tiles (balanced on the host) every time step, then waits at
+// a grid barrier before the next step.  The launch is cooperative, so all CTAs are resident; the barrier still
 // gives up after a time limit, records LB_ERR_TIMEOUT in the error word and
 // every CTA returns.
 #pragma once
@@ -69,8 +68,8 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int expect
 template <class S>
 struct BatchArgs {
   const CapDesc<typename S::A>* caps;
-  const TileDesc* tiles;
-  int ntiles;
+  const TileDesc* tiles;  // CTA k takes tiles[start[k] .. start[k + 1]) every step
+  const int* start;
   typename S::T* fa;   // buffer A: f planes of every lattice
   typename S::T* ga;
   float* g0a;
@@ -96,7 +95,7 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(BatchArgs<S> a) {
   __shared__ StepSmem<MODEL_BINARY, S, BX> sm;
   for (int s = 0; s < a.nsteps; ++s) {
     const bool fromA = ((a.parity + s) & 1) == 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    for (int t = a.start[blockIdx.x]; t < a.start[blockIdx.x + 1]; ++t) {
       const TileDesc td = a.tiles[t];
       const CapDesc<typename S::A> c = a.caps[td.cap];
       const Buf<S> src = fromA ? cap_buf<S>(a.fa, a.ga, a.g0a, c) : cap_buf<S>(a.fb, a.gb, a.g0b, c);
@@ -170,7 +169,7 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_ker
       // the generic proxy before the grid barrier
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    for (int t = a.start[blockIdx.x]; t < a.start[blockIdx.x + 1]; ++t) {
       const TileDesc td = a.tiles[t];
       const CapDesc<typename S::A>& c = a.caps[td.cap];
       if (ok) {
