@@ -320,7 +320,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="BX,YC: fixed step-kernel tile instead of autotuning")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "moments"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep secondary metric")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate secondary metric")
@@ -335,7 +335,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, Lattice
+    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_MOMENTS, Lattice
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -345,7 +345,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    cap = W.config_binary_16384x256(STORAGE_F32 if args.storage == "f32" else STORAGE_F16DEV)
+    cap = W.config_binary_16384x256({"f32": STORAGE_F32, "f16dev": STORAGE_F16DEV,
+                                     "moments": STORAGE_MOMENTS}[args.storage])
     lat = Lattice.from_workload(cap)
     if args.tile:
         tx, ty = (int(v) for v in args.tile.split(","))

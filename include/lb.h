@@ -62,8 +62,25 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
 
 /* Storage of the distributions.  Arithmetic is FP64 for LB_STORAGE_F64 and FP32
  * otherwise.  LB_STORAGE_F16DEV keeps f_i - w_i rho0 (w = 4/9, 1/9, 1/36,
- * rho0 = 1) and g_1..g_8 in FP16 and g_0 in FP32. */
-typedef enum { LB_STORAGE_F64 = 0, LB_STORAGE_F32 = 1, LB_STORAGE_F16DEV = 2 } lb_storage;
+ * rho0 = 1) and g_1..g_8 in FP16 and g_0 in FP32.
+ *
+ * LB_STORAGE_MOMENTS (binary model only) keeps six FP32 numbers per node
+ * instead of the populations: rho, jx, jy, pxx - pyy, pxy of f and phi of g.
+ * With the relaxation matrix of App. A every other mode of f, and every mode
+ * of g, relaxes fully to equilibrium in one collision (Sec. 3.1), so the next
+ * state depends on nothing else: the update is the population scheme's in
+ * exact arithmetic, with 48 instead of 144 bytes moved per node update.  The
+ * populations themselves are not kept (lb_get_populations returns LB_ERR_ARG;
+ * lb_get_moments reads the state), and lb_set_populations stores their
+ * moments.  The density is held as rho - 1 (the binary model keeps rho near
+ * 1), which lb_get_moments, lb_fields and the reductions add back in FP64.  At
+ * most 715827882 nodes (6 nx ny < 2^32). */
+typedef enum {
+  LB_STORAGE_F64 = 0,
+  LB_STORAGE_F32 = 1,
+  LB_STORAGE_F16DEV = 2,
+  LB_STORAGE_MOMENTS = 3
+} lb_storage;
 
 typedef struct {
   int nx, ny;
@@ -145,6 +162,15 @@ lb_status lb_get_populations(lb_ctx *ctx, double *f, double *g, int rested);
  * type).  g is required for the binary model.  Solid nodes are ignored. */
 lb_status lb_set_populations(lb_ctx *ctx, const double *f, const double *g);
 
+/* The six moments of the stored state, host array (6, ny, nx) of doubles in
+ * the order rho, jx, jy, pxx - pyy, pxy (of f), phi (sum of g; 0 for the
+ * liquid-gas model): for the population storages they are summed in FP64
+ * from the stored populations, for LB_STORAGE_MOMENTS they are the state.  As
+ * lb_get_populations with rested = 0, boundary nodes are returned before the
+ * rest rule (which would set j = 0).  Solid nodes give zeros.  Waits for the
+ * stream. */
+lb_status lb_get_moments(lb_ctx *ctx, double *m);
+
 /* Wait for all work issued on the context's stream. */
 lb_status lb_sync(lb_ctx *ctx);
 
@@ -165,9 +191,10 @@ lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
  * registers), 2 = staged kernel (rows brought into shared memory by bulk
  * copies; needs nx % 8 == 0) with its shallow ring of row stages, 3 = staged
  * kernel with its deep ring.  All compute the same update bit for bit.
- * Invalidates the captured step graph. */
+ * LB_STORAGE_MOMENTS has one kernel of its own (variant 4; 0 and 4 are
+ * accepted).  Invalidates the captured step graph. */
 lb_status lb_set_kernel(lb_ctx *ctx, int variant);
-/* The kernel variant in use (1, 2 or 3; automatic selection resolved). */
+/* The kernel variant in use (1, 2, 3 or 4; automatic selection resolved). */
 lb_status lb_get_kernel(const lb_ctx *ctx, int *variant);
 
 /* Time each candidate kernel variant and tile on this lattice (the state is

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "lb_device.cuh"
+#include "lb_moment.cuh"
 
 namespace lbk {
 
@@ -30,9 +31,13 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
     if (is_solid(G, x, y)) {
-      for (int i = 0; i < 9; ++i) {
-        S::sf(B.f, N, n, i, A(0));
-        if (BIN) S::sg(B.g, B.g0, N, n, i, A(0));
+      if constexpr (is_moments<S>::value) {
+        for (int k = 0; k < M_PLANES; ++k) B.f[k * N + n] = 0.f;
+      } else {
+        for (int i = 0; i < 9; ++i) {
+          S::sf(B.f, N, n, i, A(0));
+          if (BIN) S::sg(B.g, B.g0, N, n, i, A(0));
+        }
       }
       continue;
     }
@@ -63,9 +68,16 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
       const A p0 = rho * P.T / (A(1) - P.b * rho) - P.a * rho * rho;
       feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * rho * rlap, P.kappa, rdx, rdy, rdx, rdy, P.lambda_scale * P.nu, fe);
     }
-    for (int i = 0; i < 9; ++i) {
-      S::sf(B.f, N, n, i, fe[i]);
-      if (BIN) S::sg(B.g, B.g0, N, n, i, ge[i]);
+    if constexpr (is_moments<S>::value) {
+      A m[M_PLANES];
+      pops_to_moments(fe, ge, m);
+      m[M_RHO] = (A)(rho_in[n] - 1.0);  // stored as rho - 1
+      for (int k = 0; k < M_PLANES; ++k) B.f[k * N + n] = m[k];
+    } else {
+      for (int i = 0; i < 9; ++i) {
+        S::sf(B.f, N, n, i, fe[i]);
+        if (BIN) S::sg(B.g, B.g0, N, n, i, ge[i]);
+      }
     }
   }
 }
@@ -91,16 +103,30 @@ __global__ void fields_kernel(Geom G, Buf<S> B, double* __restrict__ rho, double
   const size_t N = (size_t)G.nx * G.ny;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
-    A f[9], g[9];
-    if (!node_state<MODEL, S>(G, B, N, x, y, true, f, g)) {
-      rho[n] = ux[n] = uy[n] = phi[n] = 0.0;
-      continue;
+    if constexpr (is_moments<S>::value) {
+      if (is_solid(G, x, y)) {
+        rho[n] = ux[n] = uy[n] = phi[n] = 0.0;
+        continue;
+      }
+      bool sol[3][3], bnd;
+      neighbour_solids(G, x, y, sol, bnd);
+      const double r = 1.0 + (double)B.f[M_RHO * N + n];
+      rho[n] = r;
+      ux[n] = bnd ? 0.0 : (double)B.f[M_JX * N + n] / r;  // rest rule at boundary nodes
+      uy[n] = bnd ? 0.0 : (double)B.f[M_JY * N + n] / r;
+      phi[n] = (double)B.f[M_PHI * N + n];
+    } else {
+      A f[9], g[9];
+      if (!node_state<MODEL, S>(G, B, N, x, y, true, f, g)) {
+        rho[n] = ux[n] = uy[n] = phi[n] = 0.0;
+        continue;
+      }
+      const A r = sum9(f);
+      rho[n] = (double)r;
+      ux[n] = (double)(momx(f) / r);
+      uy[n] = (double)(momy(f) / r);
+      phi[n] = MODEL == MODEL_BINARY ? (double)sum9(g) : 0.0;
     }
-    const A r = sum9(f);
-    rho[n] = (double)r;
-    ux[n] = (double)(momx(f) / r);
-    uy[n] = (double)(momy(f) / r);
-    phi[n] = MODEL == MODEL_BINARY ? (double)sum9(g) : 0.0;
   }
 }
 
@@ -126,10 +152,50 @@ __global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, 
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
     const bool sol = is_solid(G, x, y);
-    for (int i = 0; i < 9; ++i) {
-      S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]));
-      if (MODEL == MODEL_BINARY) S::sg(B.g, B.g0, N, n, i, sol ? A(0) : A(gi[i * N + n]));
+    if constexpr (is_moments<S>::value) {
+      // moments of the given populations, summed in FP64 and rounded once
+      double f[9], g[9], m[M_PLANES];
+      for (int i = 0; i < 9; ++i) {
+        f[i] = fi[i * N + n];
+        g[i] = MODEL == MODEL_BINARY ? gi[i * N + n] : 0.0;
+      }
+      pops_to_moments(f, g, m);
+      m[M_RHO] -= 1.0;  // stored as rho - 1
+      for (int k = 0; k < M_PLANES; ++k) B.f[k * N + n] = sol ? 0.f : (float)m[k];
+    } else {
+      for (int i = 0; i < 9; ++i) {
+        S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]));
+        if (MODEL == MODEL_BINARY) S::sg(B.g, B.g0, N, n, i, sol ? A(0) : A(gi[i * N + n]));
+      }
     }
+  }
+}
+
+// The six moments of the stored state (plane-major [M_PLANES][ny][nx]); for the
+// population storages they are summed in FP64 from the stored populations.
+// Solid nodes give zeros.
+template <int MODEL, class S>
+__global__ void moments_out_kernel(Geom G, Buf<S> B, double* __restrict__ out) {
+  using A = typename S::A;
+  const size_t N = (size_t)G.nx * G.ny;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    const bool sol = is_solid(G, x, y);
+    double m[M_PLANES];
+    if constexpr (is_moments<S>::value) {
+      for (int k = 0; k < M_PLANES; ++k) m[k] = (double)B.f[k * N + n];
+      m[M_RHO] += 1.0;
+    } else {
+      A fa[9], ga[9];
+      load_node<MODEL, S>(B, N, n, fa, ga);
+      double f[9], g[9];
+      for (int i = 0; i < 9; ++i) {
+        f[i] = (double)fa[i];
+        g[i] = MODEL == MODEL_BINARY ? (double)ga[i] : 0.0;
+      }
+      pops_to_moments(f, g, m);
+    }
+    for (int k = 0; k < M_PLANES; ++k) out[k * N + n] = sol ? 0.0 : m[k];
   }
 }
 
@@ -159,10 +225,16 @@ template <int MODEL, class S>
 __device__ __forceinline__ void red_add_node(const Geom& G, const Buf<S>& B, size_t N, size_t n, int x, int y,
                                              RedAcc& acc) {
   using A = typename S::A;
-  A f[9], g[9];
-  load_node<MODEL, S, true>(B, N, n, f, g);
-  const double r = (double)sum9(f);
-  const double p = MODEL == MODEL_BINARY ? (double)sum9(g) : 0.0;
+  double r, p;
+  if constexpr (is_moments<S>::value) {
+    r = 1.0 + (double)__ldcg(B.f + M_RHO * N + n);
+    p = (double)__ldcg(B.f + M_PHI * N + n);
+  } else {
+    A f[9], g[9];
+    load_node<MODEL, S, true>(B, N, n, f, g);
+    r = (double)sum9(f);
+    p = MODEL == MODEL_BINARY ? (double)sum9(g) : 0.0;
+  }
   acc.mass += r;
   acc.phi += p;
   if (G.tube_len > 0 && col_in_tube(G, x) && row_in_band(G, y)) {
@@ -218,11 +290,18 @@ __device__ __forceinline__ double centre_value(const Geom& G, const Buf<S>& B, s
   }
   const int x = wrapi(G.tube_x0 + k, G.nx);
   double va = 0.0, vb = 0.0;
-  A f[9], g[9];
-  load_node<MODEL, S>(B, N, (size_t)ya * G.nx + x, f, g);
-  for (int i = 0; i < 9; ++i) va += MODEL == MODEL_BINARY ? (double)g[i] : (double)f[i];
-  load_node<MODEL, S>(B, N, (size_t)yb * G.nx + x, f, g);
-  for (int i = 0; i < 9; ++i) vb += MODEL == MODEL_BINARY ? (double)g[i] : (double)f[i];
+  if constexpr (is_moments<S>::value) {
+    const int plane = MODEL == MODEL_BINARY ? M_PHI : M_RHO;
+    const double off = MODEL == MODEL_BINARY ? 0.0 : 1.0;  // rho is stored as rho - 1
+    va = off + (double)__ldcg(B.f + plane * N + (size_t)ya * G.nx + x);
+    vb = off + (double)__ldcg(B.f + plane * N + (size_t)yb * G.nx + x);
+  } else {
+    A f[9], g[9];
+    load_node<MODEL, S>(B, N, (size_t)ya * G.nx + x, f, g);
+    for (int i = 0; i < 9; ++i) va += MODEL == MODEL_BINARY ? (double)g[i] : (double)f[i];
+    load_node<MODEL, S>(B, N, (size_t)yb * G.nx + x, f, g);
+    for (int i = 0; i < 9; ++i) vb += MODEL == MODEL_BINARY ? (double)g[i] : (double)f[i];
+  }
   return 0.5 * (va + vb) - thr;
 }
 

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "lb.h"
+#include "lb_moment.cuh"
 #include "lb_ops.h"
 
 using namespace lbk;
@@ -101,6 +102,7 @@ static OpsFn pick_ops(int model, int storage) {
     if (storage == LB_STORAGE_F64) return ops_bin_f64;
     if (storage == LB_STORAGE_F32) return ops_bin_f32;
     if (storage == LB_STORAGE_F16DEV) return ops_bin_f16;
+    if (storage == LB_STORAGE_MOMENTS) return ops_bin_m32;
   }
   return NULL;
 }
@@ -180,6 +182,12 @@ static lb_status build_graph(lb_ctx* c) {
 }
 
 static size_t state_bytes(int model, int storage, size_t N, size_t* fb, size_t* gb, size_t* g0b) {
+  if (storage == LB_STORAGE_MOMENTS) {  // six FP32 planes in the f buffer
+    *fb = (size_t)M_PLANES * N * sizeof(float);
+    *gb = 0;
+    *g0b = 0;
+    return *fb;
+  }
   size_t el = storage == LB_STORAGE_F64 ? 8 : (storage == LB_STORAGE_F32 ? 4 : 2);
   *fb = 9 * N * el;
   *gb = model == LB_MODEL_BINARY ? (storage == LB_STORAGE_F16DEV ? 8 : 9) * N * el : 0;
@@ -192,6 +200,8 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
   if (g->nx < 3 || g->ny < 3) return set_err(c, "grid must be at least 3x3"), LB_ERR_ARG;
   if ((long)g->nx * g->ny > (1L << 31) - 1) return set_err(c, "grid too large"), LB_ERR_ARG;
   if (!pick_ops(p->model, p->storage)) return set_err(c, "unsupported model/storage pair"), LB_ERR_ARG;
+  if (p->storage == LB_STORAGE_MOMENTS && (unsigned long long)M_PLANES * g->nx * g->ny >= (1ull << 32))
+    return set_err(c, "the moment storage holds at most 715827882 nodes"), LB_ERR_ARG;
   if (w->tube_len < 0 || w->tube_len > g->nx) return set_err(c, "tube_len outside [0, nx]"), LB_ERR_ARG;
   if (w->tube_len > 0) {
     if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny)
@@ -314,6 +324,15 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
       set_err(NULL, "device allocation of the state (%zu bytes) failed", 2 * (fb + gb + g0b));
       lb_destroy(c);
       return LB_ERR_NOMEM;
+    }
+    // solid nodes are never written by a step: start them (and everything) at 0
+    cudaError_t ez = cudaMemsetAsync(c->buf[k].f, 0, fb, c->stream);
+    if (ez == cudaSuccess && gb) ez = cudaMemsetAsync(c->buf[k].g, 0, gb, c->stream);
+    if (ez == cudaSuccess && g0b) ez = cudaMemsetAsync(c->buf[k].g0, 0, g0b, c->stream);
+    if (ez != cudaSuccess) {
+      set_err(NULL, "clearing the state failed: %s", cudaGetErrorString(ez));
+      lb_destroy(c);
+      return LB_ERR_CUDA;
     }
   }
   c->partials = (double*)dev_alloc_owned(c, kRedParts * 3 * sizeof(double));
@@ -442,6 +461,8 @@ lb_status lb_filled_length(lb_ctx* c, double* l_centre, double* l_vol, double* m
 
 lb_status lb_get_populations(lb_ctx* c, double* f, double* g, int rested) {
   if (!c || !f) return c ? (set_err(c, "f is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
+  if (c->prm.storage == LB_STORAGE_MOMENTS)
+    return set_err(c, "the moment storage keeps no populations (lb_get_moments)"), LB_ERR_ARG;
   const size_t N = (size_t)c->grid.nx * c->grid.ny;
   const int bin = c->prm.model == LB_MODEL_BINARY;
   double* d = (double*)dev_alloc(c, (bin ? 18 : 9) * N * sizeof(double));
@@ -485,6 +506,23 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
   return LB_OK;
 }
 
+lb_status lb_get_moments(lb_ctx* c, double* m) {
+  if (!c || !m) return c ? (set_err(c, "m is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
+  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+  double* d = (double*)dev_alloc(c, (size_t)M_PLANES * N * sizeof(double));
+  if (!d) return set_err(c, "device allocation failed"), LB_ERR_NOMEM;
+  OpArgs a = base_args(c);
+  a.src = c->buf[c->cur];
+  a.out0 = d;
+  cudaError_t e = c->ops(OP_MOMENTS_OUT, a, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m, d, (size_t)M_PLANES * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = e2;
+  dev_free(c, d);
+  if (e != cudaSuccess) return set_err(c, "lb_get_moments: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  return LB_OK;
+}
+
 lb_status lb_sync(lb_ctx* c) {
   if (!c) return LB_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));
@@ -493,6 +531,10 @@ lb_status lb_sync(lb_ctx* c) {
 
 lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
   if (!c || !variant) return LB_ERR_ARG;
+  if (c->prm.storage == LB_STORAGE_MOMENTS) {
+    *variant = 4;
+    return LB_OK;
+  }
   const int k = c->kernel == 0 ? (c->grid.nx % 8 == 0 ? 2 : 1) : c->kernel;
   *variant = k == 2 && c->deep ? 3 : k;
   return LB_OK;
@@ -500,6 +542,9 @@ lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
 
 lb_status lb_set_kernel(lb_ctx* c, int variant) {
   if (!c) return LB_ERR_ARG;
+  if (c->prm.storage == LB_STORAGE_MOMENTS && variant != 0 && variant != 4)
+    return set_err(c, "the moment storage has one step kernel (variant 4)"), LB_ERR_ARG;
+  if (c->prm.storage == LB_STORAGE_MOMENTS) return LB_OK;
   if (variant < 0 || variant > 3) return set_err(c, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
   if (variant >= 2 && c->grid.nx % 8 != 0)
     return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
@@ -564,13 +609,16 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   const int reps = 10;
   // kernel variants: the staged kernel only where rows are 16-byte aligned
   // variants: sliding window, staged (shallow ring), staged (deep ring)
-  const int nk = c->grid.nx % 8 == 0 ? 3 : 1;
+  const int moments = c->prm.storage == LB_STORAGE_MOMENTS;
+  const int nk = moments ? 1 : (c->grid.nx % 8 == 0 ? 3 : 1);
   for (int ik = 0; ik < nk && e == cudaSuccess && st == LB_OK; ++ik)
   for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
     for (int iy = 0; iy < 7 && e == cudaSuccess && st == LB_OK; ++iy) {
       if (cand_y[iy] > c->grid.ny) continue;
-      c->kernel = ik == 0 ? 1 : 2;
-      c->deep = ik == 2;
+      if (!moments) {
+        c->kernel = ik == 0 ? 1 : 2;
+        c->deep = ik == 2;
+      }
       c->tile_x = cand_x[ix];
       c->tile_y = cand_y[iy];
       int from = c->cur;

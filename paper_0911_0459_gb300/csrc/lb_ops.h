@@ -7,7 +7,7 @@
 
 namespace lbk {
 
-enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL };
+enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL, OP_MOMENTS_OUT };
 
 struct OpBufs {
   void* f;
@@ -30,7 +30,7 @@ struct OpArgs {
   int* err;      // device error word (a device-side wait gave up)
   // field / population / reduction arguments (device pointers)
   const double *in0, *in1, *in2, *in3;
-  double *out0, *out1, *out2, *out3;
+  double *out0, *out1, *out2, *out3;  // OP_MOMENTS_OUT: out0 holds 6 planes
   int flag;      // rested flag for OP_POPS_OUT
   int nparts;    // reduction partial blocks
   double* partials;
@@ -44,5 +44,6 @@ cudaError_t ops_lg_f32(OpKind, const OpArgs&, cudaStream_t);
 cudaError_t ops_bin_f64(OpKind, const OpArgs&, cudaStream_t);
 cudaError_t ops_bin_f32(OpKind, const OpArgs&, cudaStream_t);
 cudaError_t ops_bin_f16(OpKind, const OpArgs&, cudaStream_t);
+cudaError_t ops_bin_m32(OpKind, const OpArgs&, cudaStream_t);  // moment storage
 
 }  // namespace lbk

@@ -66,23 +66,48 @@ static cudaError_t launch_staged(const OpArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int NW>
+static cudaError_t launch_moment(const OpArgs& a, cudaStream_t s) {
+  MomArgs k;
+  k.G = to_geom(a);
+  k.P = to_phys<float>(a);
+  k.src = (const float*)a.src.f;
+  k.dst = (float*)a.dst.f;
+  k.yc = a.yc;
+  dim3 grid((a.nx + NW * kMomCols - 1) / (NW * kMomCols), (a.ny + a.yc - 1) / a.yc);
+  moment_step_kernel<NW><<<grid, NW * 32, 0, s>>>(k);
+  return cudaGetLastError();
+}
+
 template <int MODEL, class S>
 cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
   using A = typename S::A;
   const Geom G = to_geom(a);
   const size_t N = (size_t)a.nx * a.ny;
+  if constexpr (is_moments<S>::value) {
+    static_assert(MODEL == MODEL_BINARY, "the moment storage holds the binary model");
+    if (op == OP_STEP) {
+      if (a.bx == 64) return launch_moment<2>(a, s);
+      if (a.bx == 128) return launch_moment<4>(a, s);
+      if (a.bx == 256) return launch_moment<8>(a, s);
+      return cudaErrorInvalidValue;
+    }
+    if (op == OP_POPS_OUT) return cudaErrorNotSupported;  // populations are not kept
+  }
   switch (op) {
     case OP_STEP:
-      if (a.staged) {
-        if (a.nx % 8 != 0 || !a.err) return cudaErrorInvalidValue;
-        if (a.bx == 64) return a.deep ? launch_staged<MODEL, S, 64, 8>(a, s) : launch_staged<MODEL, S, 64, 4>(a, s);
-        if (a.bx == 128) return a.deep ? launch_staged<MODEL, S, 128, 6>(a, s) : launch_staged<MODEL, S, 128, 4>(a, s);
-        if (a.bx == 256) return a.deep ? launch_staged<MODEL, S, 256, 4>(a, s) : launch_staged<MODEL, S, 256, 3>(a, s);
-        return cudaErrorInvalidValue;
+      if constexpr (!is_moments<S>::value) {
+        if (a.staged) {
+          if (a.nx % 8 != 0 || !a.err) return cudaErrorInvalidValue;
+          if (a.bx == 64) return a.deep ? launch_staged<MODEL, S, 64, 8>(a, s) : launch_staged<MODEL, S, 64, 4>(a, s);
+          if (a.bx == 128) return a.deep ? launch_staged<MODEL, S, 128, 6>(a, s) : launch_staged<MODEL, S, 128, 4>(a, s);
+          if (a.bx == 256) return a.deep ? launch_staged<MODEL, S, 256, 4>(a, s) : launch_staged<MODEL, S, 256, 3>(a, s);
+          return cudaErrorInvalidValue;
+        }
+        if (a.bx == 64) return launch_step<MODEL, S, 64>(a, s);
+        if (a.bx == 128) return launch_step<MODEL, S, 128>(a, s);
+        if (a.bx == 256) return launch_step<MODEL, S, 256>(a, s);
       }
-      if (a.bx == 64) return launch_step<MODEL, S, 64>(a, s);
-      if (a.bx == 128) return launch_step<MODEL, S, 128>(a, s);
-      if (a.bx == 256) return launch_step<MODEL, S, 256>(a, s);
       return cudaErrorInvalidValue;
     case OP_INIT:
       init_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_phys<A>(a), to_buf<S>(a.dst), a.in0, a.in1,
@@ -92,7 +117,11 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
       fields_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.out0, a.out1, a.out2, a.out3);
       return cudaGetLastError();
     case OP_POPS_OUT:
-      pops_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.flag, a.out0, a.out1);
+      if constexpr (!is_moments<S>::value)
+        pops_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.flag, a.out0, a.out1);
+      return cudaGetLastError();
+    case OP_MOMENTS_OUT:
+      moments_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.out0);
       return cudaGetLastError();
     case OP_POPS_IN:
       pops_in_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.dst), a.in0, a.in1);

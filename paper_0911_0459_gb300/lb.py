@@ -22,7 +22,7 @@ LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, 
 STATUS_NAMES = ["LB_OK", "LB_ERR_ARG", "LB_ERR_CUDA", "LB_ERR_NONFINITE", "LB_ERR_TIMEOUT",
                 "LB_ERR_STATE", "LB_ERR_NOMEM"]
 MODEL_LIQUID_GAS, MODEL_BINARY = 0, 1
-STORAGE_F64, STORAGE_F32, STORAGE_F16DEV = 0, 1, 2
+STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS = 0, 1, 2, 3
 
 
 class LbError(RuntimeError):
@@ -78,6 +78,7 @@ def library():
         "lb_fields": (C.c_int, [vp, dp, dp, dp, dp]),
         "lb_filled_length": (C.c_int, [vp] + [C.POINTER(C.c_double)] * 4),
         "lb_get_populations": (C.c_int, [vp, dp, dp, C.c_int]),
+        "lb_get_moments": (C.c_int, [vp, dp]),
         "lb_set_populations": (C.c_int, [vp, dp, dp]),
         "lb_sync": (C.c_int, [vp]),
         "lb_time": (C.c_long, [vp]),
@@ -115,7 +116,7 @@ def library():
 
 def exported_symbols():
     return ["lb_create", "lb_destroy", "lb_init_fields", "lb_step", "lb_fields", "lb_filled_length",
-            "lb_get_populations", "lb_set_populations", "lb_sync", "lb_time", "lb_fluid_nodes",
+            "lb_get_populations", "lb_set_populations", "lb_get_moments", "lb_sync", "lb_time", "lb_fluid_nodes",
             "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
             "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
             "lb_batch_populations", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
@@ -286,6 +287,13 @@ class Lattice:
         g = np.empty((9,) + self.shape) if self.model == MODEL_BINARY else None
         _check(library().lb_get_populations(self.h, _p(f), _p(g), int(bool(rested))), self.h)
         return f, g
+
+    def moments(self):
+        """(6, ny, nx): rho, jx, jy, pxx - pyy, pxy, phi of the stored state (before
+        the boundary-node rest rule)."""
+        m = np.empty((6,) + self.shape)
+        _check(library().lb_get_moments(self.h, _p(m)), self.h)
+        return m
 
     def set_populations(self, f, g=None):
         s = (9,) + self.shape

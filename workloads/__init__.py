@@ -28,7 +28,7 @@ from typing import Dict, List, Optional
 import numpy as np
 
 LG, BINARY = 0, 1
-STORAGE_F64, STORAGE_F32, STORAGE_F16DEV = 0, 1, 2
+STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
