@@ -32,7 +32,8 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
     if (is_solid(G, x, y)) {
       if constexpr (is_moments<S>::value) {
-        for (int k = 0; k < M_PLANES; ++k) B.f[k * N + n] = 0.f;
+        const float z[M_PLANES] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        mom_store(B.f, N, n, z);
       } else {
         for (int i = 0; i < 9; ++i) {
           S::sf(B.f, N, n, i, A(0));
@@ -72,7 +73,7 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
       A m[M_PLANES];
       pops_to_moments(fe, ge, m);
       m[M_RHO] = (A)(rho_in[n] - 1.0);  // stored as rho - 1
-      for (int k = 0; k < M_PLANES; ++k) B.f[k * N + n] = m[k];
+      mom_store(B.f, N, n, m);
     } else {
       for (int i = 0; i < 9; ++i) {
         S::sf(B.f, N, n, i, fe[i]);
@@ -110,11 +111,13 @@ __global__ void fields_kernel(Geom G, Buf<S> B, double* __restrict__ rho, double
       }
       bool sol[3][3], bnd;
       neighbour_solids(G, x, y, sol, bnd);
-      const double r = 1.0 + (double)B.f[M_RHO * N + n];
+      float m[M_PLANES];
+      mom_load(B.f, N, n, m);
+      const double r = 1.0 + (double)m[M_RHO];
       rho[n] = r;
-      ux[n] = bnd ? 0.0 : (double)B.f[M_JX * N + n] / r;  // rest rule at boundary nodes
-      uy[n] = bnd ? 0.0 : (double)B.f[M_JY * N + n] / r;
-      phi[n] = (double)B.f[M_PHI * N + n];
+      ux[n] = bnd ? 0.0 : (double)m[M_JX] / r;  // rest rule at boundary nodes
+      uy[n] = bnd ? 0.0 : (double)m[M_JY] / r;
+      phi[n] = (double)m[M_PHI];
     } else {
       A f[9], g[9];
       if (!node_state<MODEL, S>(G, B, N, x, y, true, f, g)) {
@@ -161,7 +164,9 @@ __global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, 
       }
       pops_to_moments(f, g, m);
       m[M_RHO] -= 1.0;  // stored as rho - 1
-      for (int k = 0; k < M_PLANES; ++k) B.f[k * N + n] = sol ? 0.f : (float)m[k];
+      float mf[M_PLANES];
+      for (int k = 0; k < M_PLANES; ++k) mf[k] = sol ? 0.f : (float)m[k];
+      mom_store(B.f, N, n, mf);
     } else {
       for (int i = 0; i < 9; ++i) {
         S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]));
@@ -183,7 +188,9 @@ __global__ void moments_out_kernel(Geom G, Buf<S> B, double* __restrict__ out) {
     const bool sol = is_solid(G, x, y);
     double m[M_PLANES];
     if constexpr (is_moments<S>::value) {
-      for (int k = 0; k < M_PLANES; ++k) m[k] = (double)B.f[k * N + n];
+      float mf[M_PLANES];
+      mom_load(B.f, N, n, mf);
+      for (int k = 0; k < M_PLANES; ++k) m[k] = (double)mf[k];
       m[M_RHO] += 1.0;
     } else {
       A fa[9], ga[9];
@@ -227,8 +234,9 @@ __device__ __forceinline__ void red_add_node(const Geom& G, const Buf<S>& B, siz
   using A = typename S::A;
   double r, p;
   if constexpr (is_moments<S>::value) {
-    r = 1.0 + (double)__ldcg(B.f + M_RHO * N + n);
-    p = (double)__ldcg(B.f + M_PHI * N + n);
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(B.f) + MP_RP * N + n);
+    r = 1.0 + (double)v.x;
+    p = (double)v.y;
   } else {
     A f[9], g[9];
     load_node<MODEL, S, true>(B, N, n, f, g);
@@ -291,10 +299,11 @@ __device__ __forceinline__ double centre_value(const Geom& G, const Buf<S>& B, s
   const int x = wrapi(G.tube_x0 + k, G.nx);
   double va = 0.0, vb = 0.0;
   if constexpr (is_moments<S>::value) {
-    const int plane = MODEL == MODEL_BINARY ? M_PHI : M_RHO;
-    const double off = MODEL == MODEL_BINARY ? 0.0 : 1.0;  // rho is stored as rho - 1
-    va = off + (double)__ldcg(B.f + plane * N + (size_t)ya * G.nx + x);
-    vb = off + (double)__ldcg(B.f + plane * N + (size_t)yb * G.nx + x);
+    const float2* P = reinterpret_cast<const float2*>(B.f) + MP_RP * N;
+    const float2 a = __ldcg(P + (size_t)ya * G.nx + x), b = __ldcg(P + (size_t)yb * G.nx + x);
+    // binary: phi; liquid-gas: rho (stored as rho - 1)
+    va = MODEL == MODEL_BINARY ? (double)a.y : 1.0 + (double)a.x;
+    vb = MODEL == MODEL_BINARY ? (double)b.y : 1.0 + (double)b.x;
   } else {
     A f[9], g[9];
     load_node<MODEL, S>(B, N, (size_t)ya * G.nx + x, f, g);

@@ -39,13 +39,37 @@
 
 namespace lbk {
 
-// Storage trait of the moment representation: six FP32 planes per node, in the
-// order M_RHO .. M_PHI (plane k at base + k * N); plane M_RHO holds rho - 1.
+// Storage trait of the moment representation: six FP32 numbers per node, kept
+// as three planes of N float2, (rho - 1, phi), (jx, jy) and (pxx - pyy, pxy),
+// so that a node's moments take three 8-byte accesses.  M_RHO .. M_PHI name
+// the six moments in the order of the C interface.
 struct SM32 {
   using T = float;
   using A = float;
 };
 enum { M_RHO = 0, M_JX = 1, M_JY = 2, M_XX = 3, M_XY = 4, M_PHI = 5, M_PLANES = 6 };
+enum { MP_RP = 0, MP_J = 1, MP_S = 2 };  // float2 planes
+
+// The six moments of node n (rho - 1 in m[M_RHO]).
+template <bool COHERENT = false>
+__device__ __forceinline__ void mom_load(const float* base, size_t N, size_t n, float m[M_PLANES]) {
+  const float2* P = reinterpret_cast<const float2*>(base);
+  const float2 a = COHERENT ? __ldcg(P + MP_RP * N + n) : P[MP_RP * N + n];
+  const float2 b = COHERENT ? __ldcg(P + MP_J * N + n) : P[MP_J * N + n];
+  const float2 c = COHERENT ? __ldcg(P + MP_S * N + n) : P[MP_S * N + n];
+  m[M_RHO] = a.x;
+  m[M_PHI] = a.y;
+  m[M_JX] = b.x;
+  m[M_JY] = b.y;
+  m[M_XX] = c.x;
+  m[M_XY] = c.y;
+}
+__device__ __forceinline__ void mom_store(float* base, size_t N, size_t n, const float m[M_PLANES]) {
+  float2* P = reinterpret_cast<float2*>(base);
+  P[MP_RP * N + n] = make_float2(m[M_RHO], m[M_PHI]);
+  P[MP_J * N + n] = make_float2(m[M_JX], m[M_JY]);
+  P[MP_S * N + n] = make_float2(m[M_XX], m[M_XY]);
+}
 
 template <class S>
 struct is_moments {
@@ -164,7 +188,7 @@ __device__ __forceinline__ void collide_moment_node(const Phys<float>& P, float 
 struct MomArgs {
   Geom G;
   Phys<float> P;
-  const float* src;  // M_PLANES planes of N floats (M_PLANES * N < 2^32)
+  const float* src;  // three float2 planes of N nodes (6 N < 2^32)
   float* dst;
   int yc;            // rows per band
 };
@@ -200,8 +224,8 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 6 : 12)) mom
   const bool warp_tube = __any_sync(FULL, tc0 || tc1 || tc2);
   const int y0 = blockIdx.y * a.yc;
   const int y1 = min(y0 + a.yc, ny);
-  const float* __restrict__ src = a.src;
-  float* __restrict__ dst = a.dst;
+  const float2* __restrict__ src = reinterpret_cast<const float2*>(a.src);
+  float2* __restrict__ dst = reinterpret_cast<float2*>(a.dst);
 
   // one row of the stencil window: centre c, s = right - left and
   // d = (left - c) + (right - c) of rho and phi at this lane's column.  Solid
@@ -242,121 +266,153 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 6 : 12)) mom
     return w;
   };
   auto load_rp = [&](unsigned rowb, float& rv, float& pv, float& re, float& pe) {
-    rv = __ldg(src + (M_RHO * N + rowb + x));
-    pv = __ldg(src + (M_PHI * N + rowb + x));
+    const float2 v = __ldg(src + (MP_RP * N + rowb + x));
+    rv = v.x;
+    pv = v.y;
     re = 0.f;
     pe = 0.f;
     if (edge) {
-      re = __ldg(src + (M_RHO * N + rowb + xe));
-      pe = __ldg(src + (M_PHI * N + rowb + xe));
+      const float2 e = __ldg(src + (MP_RP * N + rowb + xe));
+      re = e.x;
+      pe = e.y;
     }
   };
   auto load_jm = [&](unsigned rowb, float& jx, float& jy, float& mx, float& my) {
     const unsigned o = rowb + x;
-    jx = __ldg(src + (M_JX * N + o));
-    jy = __ldg(src + (M_JY * N + o));
-    mx = __ldg(src + (M_XX * N + o));
-    my = __ldg(src + (M_XY * N + o));
+    const float2 j = __ldg(src + (MP_J * N + o));
+    const float2 m = __ldg(src + (MP_S * N + o));
+    jx = j.x;
+    jy = j.y;
+    mx = m.x;
+    my = m.y;
   };
   auto next_row = [&](int yy) { return yy + 1 == ny ? 0 : yy + 1; };
 
-  Row w0, w1, w2;                 // rho/phi rows k - 1, k, k + 1
-  float jx, jy, mx, my;           // moments of row k
-  int ym = wrapi(y0 - 2, ny);     // rows k - 1, k, k + 1 (wrapped), k = y0 - 1 first
-  int yy = next_row(ym);
-  int yp = next_row(yy);
-  bool rb0 = row_in_band(G, ym), rb1 = row_in_band(G, yy), rb2 = row_in_band(G, yp);
+  // A slot of the three-row window: a row's stencil summaries, its index and
+  // whether it lies in the tube's band.  The rows of collision row k are in
+  // slots (k - 1, k, k + 1); the loop body is called with the slots (and the
+  // accumulators) rotated, so that a new row lands in the slot the oldest row
+  // leaves and nothing is copied between iterations.
+  struct Slot {
+    Row w;
+    int y;
+    bool rb;
+  };
+  Slot S0, S1, S2;
+  S0.y = wrapi(y0 - 2, ny);
+  S1.y = next_row(S0.y);
+  S2.y = next_row(S1.y);
+  S0.rb = row_in_band(G, S0.y);
+  S1.rb = row_in_band(G, S1.y);
+  S2.rb = row_in_band(G, S2.y);
+  float jx, jy, mx, my;  // moments of the collision row
   {
     float r, p, re, pe;
-    load_rp((unsigned)ym * nx, r, p, re, pe);
-    w0 = make_row(r, p, re, pe, rb0);
-    load_rp((unsigned)yy * nx, r, p, re, pe);
-    w1 = make_row(r, p, re, pe, rb1);
-    load_rp((unsigned)yp * nx, r, p, re, pe);
-    w2 = make_row(r, p, re, pe, rb2);
-    load_jm((unsigned)yy * nx, jx, jy, mx, my);
+    load_rp((unsigned)S0.y * nx, r, p, re, pe);
+    S0.w = make_row(r, p, re, pe, S0.rb);
+    load_rp((unsigned)S1.y * nx, r, p, re, pe);
+    S1.w = make_row(r, p, re, pe, S1.rb);
+    load_rp((unsigned)S2.y * nx, r, p, re, pe);
+    S2.w = make_row(r, p, re, pe, S2.rb);
+    load_jm((unsigned)S1.y * nx, jx, jy, mx, my);
   }
-  MAcc a0 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // destination row k - 1
-  MAcc a1 = a0;                              // destination row k
+  MAcc A0 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, A1 = A0, A2 = A0;
 
-#pragma unroll 1
-  for (int k = y0 - 1; k <= y1; ++k) {
+  // collision row k: slots lo/mid/hi hold rows k - 1, k, k + 1; accumulators
+  // a0 (row k - 1, stored here), a1 (row k) and a2 (row k + 1, started here)
+  auto step = [&](Slot& lo, Slot& mid, Slot& hi, MAcc& a0, MAcc& a1, MAcc& a2, int k) {
     // next rows in flight while this one collides
-    const int yq = next_row(yp);  // row k + 2
+    const int yq = next_row(hi.y);  // row k + 2
     float nr = 0.f, np = 0.f, ner = 0.f, nep = 0.f, njx = 0.f, njy = 0.f, nmx = 0.f, nmy = 0.f;
     if (k < y1) {
       load_rp((unsigned)yq * nx, nr, np, ner, nep);
-      load_jm((unsigned)yp * nx, njx, njy, nmx, nmy);
+      load_jm((unsigned)hi.y * nx, njx, njy, nmx, nmy);
     }
-    const bool fluid = !(tc1 && !rb1);
-    // walls can touch this warp only if it has tube columns and a row leaves the band
-    const bool walls = warp_tube && !(rb0 && rb1 && rb2);
-    bool sol[3][3];
-    bool bnd = false;
-    if (walls) {
-      const bool tc[3] = {tc0, tc1, tc2};
-      const bool rb[3] = {rb0, rb1, rb2};
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          sol[j][i] = tc[i] && !rb[j];
-          bnd = bnd || sol[j][i];
-        }
-    }
+    // walls can touch this warp only if it has tube columns and a row leaves the
+    // band (warp-uniform); otherwise every node is fluid with fluid neighbours
+    const bool walls = warp_tube && !(lo.rb && mid.rb && hi.rb);
     float fs[9], ge[9];
-    if (fluid) {
+    if (!walls) {
       float rdx, rdy, rlap, pdx, pdy, plap;
-      float cjx = jx, cjy = jy;
-      if (!bnd) {
-        const float rc[3] = {w0.rc, w1.rc, w2.rc}, rs[3] = {w0.rs, w1.rs, w2.rs}, rh[3] = {w0.rh, w1.rh, w2.rh};
-        const float pc[3] = {w0.pc, w1.pc, w2.pc}, ps[3] = {w0.ps, w1.ps, w2.ps}, ph[3] = {w0.ph, w1.ph, w2.ph};
-        stencil_rows(rc, rs, rh, rdx, rdy, rlap);
-        stencil_rows(pc, ps, ph, pdx, pdy, plap);
-      } else {
-        // boundary node: wall ghosts on the full neighbourhood, and the rest rule
-        const Row* wr[3] = {&w0, &w1, &w2};
-        float vr[3][3], vp[3][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          vr[j][0] = fmaf(0.5f, wr[j]->rh - wr[j]->rs, wr[j]->rc);
-          vr[j][1] = wr[j]->rc;
-          vr[j][2] = fmaf(0.5f, wr[j]->rh + wr[j]->rs, wr[j]->rc);
-          vp[j][0] = fmaf(0.5f, wr[j]->ph - wr[j]->ps, wr[j]->pc);
-          vp[j][1] = wr[j]->pc;
-          vp[j][2] = fmaf(0.5f, wr[j]->ph + wr[j]->ps, wr[j]->pc);
-        }
-        apply_ghosts(vr, sol, 0.f);
-        apply_ghosts(vp, sol, a.P.h);
-        stencil3(vr, rdx, rdy, rlap);
-        stencil3(vp, pdx, pdy, plap);
-        cjx = 0.f;
-        cjy = 0.f;
-      }
-      collide_moment_node(a.P, w1.rc, cjx, cjy, mx, my, w1.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+      const float rc[3] = {lo.w.rc, mid.w.rc, hi.w.rc}, rs[3] = {lo.w.rs, mid.w.rs, hi.w.rs};
+      const float rh[3] = {lo.w.rh, mid.w.rh, hi.w.rh};
+      const float pc[3] = {lo.w.pc, mid.w.pc, hi.w.pc}, ps[3] = {lo.w.ps, mid.w.ps, hi.w.ps};
+      const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
+      stencil_rows(rc, rs, rh, rdx, rdy, rlap);
+      stencil_rows(pc, ps, ph, pdx, pdy, plap);
+      collide_moment_node(a.P, mid.w.rc, jx, jy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+      a1.r += fs[0];
+      a1.p += ge[0];
     } else {
+      const bool fluid = !(tc1 && !mid.rb);
+      bool sol[3][3];
+      bool bnd = false;
+      {
+        const bool tc[3] = {tc0, tc1, tc2};
+        const bool rb[3] = {lo.rb, mid.rb, hi.rb};
 #pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        fs[i] = 0.f;  // a solid node sends nothing
-        ge[i] = 0.f;
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            sol[j][i] = tc[i] && !rb[j];
+            bnd = bnd || sol[j][i];
+          }
       }
-    }
-    // own node: the rest population, and bounce-back of what was sent into a wall
-    // (all populations as deviations from w_i, which add up to 1, 0, 0, 0, 0)
-    a1.r += fs[0];
-    a1.p += ge[0];
-    if (bnd && fluid) {
+      if (fluid) {
+        float rdx, rdy, rlap, pdx, pdy, plap;
+        float cjx = jx, cjy = jy;
+        if (!bnd) {
+          const float rc[3] = {lo.w.rc, mid.w.rc, hi.w.rc}, rs[3] = {lo.w.rs, mid.w.rs, hi.w.rs};
+          const float rh[3] = {lo.w.rh, mid.w.rh, hi.w.rh};
+          const float pc[3] = {lo.w.pc, mid.w.pc, hi.w.pc}, ps[3] = {lo.w.ps, mid.w.ps, hi.w.ps};
+          const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
+          stencil_rows(rc, rs, rh, rdx, rdy, rlap);
+          stencil_rows(pc, ps, ph, pdx, pdy, plap);
+        } else {
+          // boundary node: wall ghosts on the full neighbourhood, and the rest rule
+          const Row* wr[3] = {&lo.w, &mid.w, &hi.w};
+          float vr[3][3], vp[3][3];
 #pragma unroll
-      for (int i = 1; i < 9; ++i)
-        if (sol[1 + EYd(i)][1 + EXd(i)]) {
-          const float v = fs[i];
-          a1.r += v;
-          a1.jx -= float(EXd(i)) * v;
-          a1.jy -= float(EYd(i)) * v;
-          a1.xx += float(SXXd(i)) * v;
-          a1.xy += float(SXYd(i)) * v;
-          a1.p += ge[i];
+          for (int j = 0; j < 3; ++j) {
+            vr[j][0] = fmaf(0.5f, wr[j]->rh - wr[j]->rs, wr[j]->rc);
+            vr[j][1] = wr[j]->rc;
+            vr[j][2] = fmaf(0.5f, wr[j]->rh + wr[j]->rs, wr[j]->rc);
+            vp[j][0] = fmaf(0.5f, wr[j]->ph - wr[j]->ps, wr[j]->pc);
+            vp[j][1] = wr[j]->pc;
+            vp[j][2] = fmaf(0.5f, wr[j]->ph + wr[j]->ps, wr[j]->pc);
+          }
+          apply_ghosts(vr, sol, 0.f);
+          apply_ghosts(vp, sol, a.P.h);
+          stencil3(vr, rdx, rdy, rlap);
+          stencil3(vp, pdx, pdy, plap);
+          cjx = 0.f;
+          cjy = 0.f;
         }
+        collide_moment_node(a.P, mid.w.rc, cjx, cjy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+        // own node: the rest population, and bounce-back of what was sent into a
+        // wall (all populations as deviations from w_i, which add up to 1, 0, 0, 0, 0)
+        a1.r += fs[0];
+        a1.p += ge[0];
+        if (bnd) {
+#pragma unroll
+          for (int i = 1; i < 9; ++i)
+            if (sol[1 + EYd(i)][1 + EXd(i)]) {
+              const float v = fs[i];
+              a1.r += v;
+              a1.jx -= float(EXd(i)) * v;
+              a1.jy -= float(EYd(i)) * v;
+              a1.xx += float(SXXd(i)) * v;
+              a1.xy += float(SXYd(i)) * v;
+              a1.p += ge[i];
+            }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          fs[i] = 0.f;  // a solid node sends nothing
+          ge[i] = 0.f;
+        }
+      }
     }
     // populations moving in +x come from lane - 1, in -x from lane + 1
     const float f1 = __shfl_up_sync(FULL, fs[1], 1), f5 = __shfl_up_sync(FULL, fs[5], 1);
@@ -373,7 +429,6 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 6 : 12)) mom
     a1.xx += f1 + f2;
     a1.p += g1 + g2;
     // row k + 1: e_y = +1 (3 from here, 5 from x - 1, 7 from x + 1)
-    MAcc a2;
     a2.r = fs[3] + (f5 + f7);
     a2.jx = f5 - f7;
     a2.jy = a2.r;
@@ -389,33 +444,33 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 6 : 12)) mom
     a0.xy += f6 - f8;
     a0.p += ge[4] + (g6 + g8);
     // row k - 1 has received everything
-    if (k > y0 && store_lane && !(tc1 && !rb0)) {
-      const unsigned o = (unsigned)ym * nx + x;
-      dst[M_RHO * N + o] = a0.r;
-      dst[M_JX * N + o] = a0.jx;
-      dst[M_JY * N + o] = a0.jy;
-      dst[M_XX * N + o] = a0.xx;
-      dst[M_XY * N + o] = a0.xy;
-      dst[M_PHI * N + o] = a0.p;
+    if (k > y0 && store_lane && !(tc1 && !lo.rb)) {
+      const unsigned o = (unsigned)lo.y * nx + x;
+      dst[MP_RP * N + o] = make_float2(a0.r, a0.p);
+      dst[MP_J * N + o] = make_float2(a0.jx, a0.jy);
+      dst[MP_S * N + o] = make_float2(a0.xx, a0.xy);
     }
-    a0 = a1;
-    a1 = a2;
     if (k < y1) {
-      const bool rbq = row_in_band(G, yq);
-      w0 = w1;
-      w1 = w2;
-      w2 = make_row(nr, np, ner, nep, rbq);
+      // row k + 2 takes the slot of row k - 1
+      lo.y = yq;
+      lo.rb = row_in_band(G, yq);
+      lo.w = make_row(nr, np, ner, nep, lo.rb);
       jx = njx;
       jy = njy;
       mx = nmx;
       my = nmy;
-      ym = yy;
-      yy = yp;
-      yp = yq;
-      rb0 = rb1;
-      rb1 = rb2;
-      rb2 = rbq;
     }
+  };
+
+  int k = y0 - 1;
+#pragma unroll 1
+  while (true) {
+    step(S0, S1, S2, A0, A1, A2, k);
+    if (++k > y1) break;
+    step(S1, S2, S0, A1, A2, A0, k);
+    if (++k > y1) break;
+    step(S2, S0, S1, A2, A0, A1, k);
+    if (++k > y1) break;
   }
 }
 
