@@ -150,11 +150,12 @@ def cpu_baseline(sample_steps=2000):
 
 def precision_report(Lattice, orc, steps):
     """Error of each storage against the FP64 oracle on the crop after `steps` steps."""
-    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64
+    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STORAGE_MOMENTS
     rho_o, _, _, phi_o = orc.fields()
     l_o = orc.filled_length()["l"]
     out = {"workload": "1024x64 crop of the large capillary, default initial state", "steps": steps}
-    for name, st in (("f64", STORAGE_F64), ("f32", STORAGE_F32), ("f16dev", STORAGE_F16DEV)):
+    for name, st in (("f64", STORAGE_F64), ("f32", STORAGE_F32), ("f16dev", STORAGE_F16DEV),
+                     ("moments_f32", STORAGE_MOMENTS)):
         lat = Lattice.from_workload(W.config_binary_crop_1024x64(st))
         lat.step(steps)
         rho, _, _, phi = lat.fields()
@@ -449,6 +450,24 @@ def main():
         torch.cuda.synchronize()
         secondary["lg_256x32_fp64_us_per_step"] = 1e3 * a.elapsed_time(b) / 1984
         l1.close()
+        # the same large capillary with the state held as six FP32 moments per node
+        cm = W.config_binary_16384x256(STORAGE_MOMENTS)
+        lm = Lattice.from_workload(cm)
+        mtx, mty, _ = lm.autotune()
+        lm.step(8)
+        torch.cuda.synchronize()
+        a.record(lm.stream)
+        lm.step(512)
+        b.record(lm.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 512
+        gbs = lm.fluid_nodes * 48 / (ms * 1e-3) / 1e9
+        secondary["moments_16384x256"] = {
+            "MLUPS": lm.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "tile": [mtx, mty],
+            "bytes_per_lu": 48, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
+            "what": "moment storage (rho-1, j, pxx-pyy, pxy, phi in FP32), moment_step_kernel, 512 steps, "
+                    "CUDA events; the same update as the FP32 population kernel in exact arithmetic"}
+        lm.close()
     except Exception as ex:  # secondary numbers never block the headline line
         secondary["error"] = repr(ex)
     if not args.no_batch:

@@ -599,21 +599,24 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   if (e == cudaSuccess && gb) e = cudaMemcpyAsync(save + fb, cur.g, gb, cudaMemcpyDeviceToDevice, c->stream);
   if (e == cudaSuccess && g0b) e = cudaMemcpyAsync(save + fb + gb, cur.g0, g0b, cudaMemcpyDeviceToDevice, c->stream);
   const int cand_x[3] = {64, 128, 256};
-  const int cand_y[7] = {1, 2, 4, 8, 16, 32, 64};
+  // band heights: the moment kernel's time depends on how its warps fill the
+  // GPU in waves, so it gets a finer set
+  const int moments = c->prm.storage == LB_STORAGE_MOMENTS;
+  const std::vector<int> cand_y = moments ? std::vector<int>{4, 8, 12, 14, 16, 18, 20, 22, 24, 32, 48, 64}
+                                          : std::vector<int>{1, 2, 4, 8, 16, 32, 64};
   const int saved_kernel = c->kernel, saved_deep = c->deep;
   int best_x = c->tile_x, best_y = c->tile_y, best_k = saved_kernel, best_d = saved_deep;
   float best = 1e30f;
   cudaEvent_t e0 = NULL, e1 = NULL;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int reps = 10;
+  const int reps = 10, trials = 3;  // each candidate: best of 3 timings of 10 steps
   // kernel variants: the staged kernel only where rows are 16-byte aligned
   // variants: sliding window, staged (shallow ring), staged (deep ring)
-  const int moments = c->prm.storage == LB_STORAGE_MOMENTS;
   const int nk = moments ? 1 : (c->grid.nx % 8 == 0 ? 3 : 1);
   for (int ik = 0; ik < nk && e == cudaSuccess && st == LB_OK; ++ik)
   for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
-    for (int iy = 0; iy < 7 && e == cudaSuccess && st == LB_OK; ++iy) {
+    for (size_t iy = 0; iy < cand_y.size() && e == cudaSuccess && st == LB_OK; ++iy) {
       if (cand_y[iy] > c->grid.ny) continue;
       if (!moments) {
         c->kernel = ik == 0 ? 1 : 2;
@@ -623,12 +626,16 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
       c->tile_y = cand_y[iy];
       int from = c->cur;
       for (int k = 0; k < 2 && st == LB_OK; ++k, from ^= 1) st = launch_one(c, c->stream, from);
-      e = cudaEventRecord(e0, c->stream);
-      for (int k = 0; k < reps && st == LB_OK; ++k, from ^= 1) st = launch_one(c, c->stream, from);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      float ms = 1e30f;
+      for (int tr = 0; tr < trials && e == cudaSuccess && st == LB_OK; ++tr) {
+        e = cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < reps && st == LB_OK; ++k, from ^= 1) st = launch_one(c, c->stream, from);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess && t < ms) ms = t;
+      }
       if (e == cudaSuccess && ms < best) {
         best = ms;
         best_x = cand_x[ix];

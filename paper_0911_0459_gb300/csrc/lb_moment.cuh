@@ -202,7 +202,7 @@ struct MAcc {
 constexpr int kMomCols = 30;
 
 template <int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 6 : 12)) moment_step_kernel(MomArgs a) {
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) moment_step_kernel(MomArgs a) {
   constexpr unsigned FULL = 0xffffffffu;
   const Geom& G = a.G;
   const int nx = G.nx, ny = G.ny;
