@@ -189,18 +189,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def batched_vs_sequential(torch, Lattice, steps, n=256):
+def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
     """The seeded sweep of 256 uneven binary capillaries (H 16..128, tube 1024..8192,
     ratios 1..100, 30..80 degrees), FP32: one persistent CUDA-graph launch per
     sampled run for all capillaries against one lattice per capillary run in
-    turn, both with l(t) sampled 4 times over `steps` steps."""
+    turn (same storage), both with l(t) sampled 4 times over `steps` steps."""
     from paper_0911_0459_gb300 import Batch, shard
     rank, world, _ = dist_env()
     caps_all = W.sweep(seed=0, n=n)
     # ranks split the sweep by estimated cost; no exchange on the data path
     caps = [caps_all[i] for i in shard.my_share(caps_all, rank, world)] if world > 1 else caps_all
     at = [steps // 4, steps // 2, 3 * steps // 4, steps]
-    b = Batch(caps)
+    b = Batch(caps, storage=storage)
     tx, ty, _ = b.autotune(steps=2)
     b.run_sampled([2])
     torch.cuda.synchronize()
@@ -213,7 +213,7 @@ def batched_vs_sequential(torch, Lattice, steps, n=256):
     torch.cuda.empty_cache()
     t_seq = 0.0
     for c in caps:
-        lat = Lattice.from_workload(c)
+        lat = Lattice.from_workload(c, storage=storage)
         lat.step(2)
         lat.filled_length()
         t0 = time.perf_counter()
@@ -240,7 +240,8 @@ def batched_vs_sequential(torch, Lattice, steps, n=256):
             "sequential_capillaries_per_s_at_20k_steps": cs_seq / 20000.0,
             "GLUPS_batched": fluid * steps / t_batch / 1e9, "fluid_nodes": fluid, "steps": steps,
             "tile": [tx, ty], "l_finite": bool(np.isfinite(out).all()),
-            "what": f"{steps} steps with 4 l(t) samples, wall clock, FP32"}
+            "storage": "moments (FP32)" if storage == 3 else "FP32 populations",
+            "what": f"{steps} steps with 4 l(t) samples, wall clock"}
 
 
 def surrogate_metric(torch, threshold=0.02):
@@ -473,6 +474,8 @@ def main():
     if not args.no_batch:
         try:
             secondary["batched_sweep_256"] = batched_vs_sequential(torch, Lattice, args.batch_steps)
+            secondary["batched_sweep_256_moments"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
+                                                                           storage=STORAGE_MOMENTS)
         except Exception as ex:
             secondary["batched_error"] = repr(ex)
     if not args.no_surrogate:

@@ -238,8 +238,10 @@ lb_status lb_batch_lengths(lb_batch *b, double *out);
  * as one CUDA graph and launched once.  Waits for the stream. */
 lb_status lb_batch_run_sampled(lb_batch *b, int nsamples, const long *at, double *out);
 
-/* Populations of lattice i, as lb_get_populations. */
+/* Populations of lattice i, as lb_get_populations (LB_ERR_ARG for
+ * LB_STORAGE_MOMENTS), and its six moments, as lb_get_moments. */
 lb_status lb_batch_populations(lb_batch *b, int i, double *f, double *g, int rested);
+lb_status lb_batch_moments(lb_batch *b, int i, double *m);
 
 /* Tile of the persistent kernel (tile_x = 64, 128, 256 consumer threads along
  * x, tile_y rows), and a tuner that times every candidate (body, ring depth and
@@ -251,8 +253,9 @@ lb_status lb_batch_autotune(lb_batch *b, int steps, int *tile_x, int *tile_y, do
  * every lattice has nx % 8 == 0, else sliding-window), 1 = sliding-window body,
  * 2 / 3 = staged body with its shallow / deep ring (bulk copies into a
  * shared-memory ring that runs on across tiles and steps; every nx % 8 == 0,
- * else LB_ERR_ARG).  All give the same result bit for bit.  get returns the
- * body in use (1, 2 or 3). */
+ * else LB_ERR_ARG).  All give the same result bit for bit.  A batch in
+ * LB_STORAGE_MOMENTS has one body (4), the single-lattice moment kernel's
+ * strips.  get returns the body in use (1, 2, 3 or 4). */
 lb_status lb_batch_set_kernel(lb_batch *b, int variant);
 lb_status lb_batch_get_kernel(const lb_batch *b, int *variant);
 

@@ -103,7 +103,14 @@ static void bfree_all(lb_batch* b) {
   b->owned.clear();
 }
 
-static size_t elem_size(int storage) { return storage == LB_STORAGE_F64 ? 8 : (storage == LB_STORAGE_F32 ? 4 : 2); }
+static size_t elem_size(int storage) {
+  return storage == LB_STORAGE_F64 ? 8 : ((storage == LB_STORAGE_F32 || storage == LB_STORAGE_MOMENTS) ? 4 : 2);
+}
+
+// Columns of a tile of tile_x threads (the moment kernel's warps produce 30).
+static int tile_cols(const lb_batch* b) {
+  return b->storage == LB_STORAGE_MOMENTS ? (b->tile_x / 32) * kMomCols : b->tile_x;
+}
 
 static int solid_h(const lb_grid& g, const lb_walls& w, int x, int y) {
   if (w.tube_len <= 0) return 0;
@@ -127,7 +134,7 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
   const size_t el = elem_size(b->storage);
   OpBufs ob;
   ob.f = (char*)b->f[k] + b->off_f[i] * el;
-  ob.g = (char*)b->g[k] + b->off_g[i] * el;
+  ob.g = b->g[k] ? (char*)b->g[k] + b->off_g[i] * el : NULL;
   ob.g0 = b->g0[k] ? b->g0[k] + b->off_g0[i] : NULL;
   a.src = ob;
   a.dst = ob;
@@ -135,6 +142,7 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
 }
 
 static OpsFn batch_ops(int storage) {
+  if (storage == LB_STORAGE_MOMENTS) return ops_bin_m32;
   return storage == LB_STORAGE_F64 ? ops_bin_f64 : (storage == LB_STORAGE_F32 ? ops_bin_f32 : ops_bin_f16);
 }
 
@@ -176,6 +184,7 @@ static lb_status init_lattice(lb_batch* b, int i) {
 
 // 1 or 2: the body the next launch uses
 static int batch_variant(const lb_batch* b) {
+  if (b->storage == LB_STORAGE_MOMENTS) return 4;
   if (b->kernel == 0) return b->staged_ok ? 2 : 1;
   return b->kernel;
 }
@@ -242,6 +251,24 @@ static cudaError_t run_staged(lb_batch* b, int nsteps, cudaStream_t s, int* per)
   return cudaLaunchKernelEx(&cfg, batch_tma_kernel<S, BX, NS>, a);
 }
 
+template <int NW>
+static cudaError_t run_moment(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
+  if (per) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_moment_kernel<NW>, NW * 32, 0);
+  BatchArgs<SM32> a;
+  fill_args(b, nsteps, a);
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(b->grid_blocks);
+  cfg.blockDim = dim3(NW * 32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_moment_kernel<NW>, a);
+}
+
 template <class S>
 static cudaError_t run_s(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
   if (batch_variant(b) == 2) {
@@ -256,6 +283,11 @@ static cudaError_t run_s(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
 }
 
 static cudaError_t run_batch(lb_batch* b, int nsteps, cudaStream_t s, int* per) {
+  if (b->storage == LB_STORAGE_MOMENTS) {
+    if (b->tile_x == 64) return run_moment<2>(b, nsteps, s, per);
+    if (b->tile_x == 128) return run_moment<4>(b, nsteps, s, per);
+    return run_moment<8>(b, nsteps, s, per);
+  }
   if (b->storage == LB_STORAGE_F64) return run_s<SF64>(b, nsteps, s, per);
   if (b->storage == LB_STORAGE_F32) return run_s<SF32>(b, nsteps, s, per);
   return run_s<SF16>(b, nsteps, s, per);
@@ -290,14 +322,15 @@ static lb_status build_tiles(lb_batch* b) {
     std::vector<long> tc(g.nx + 1, 0), ob(g.ny + 1, 0);
     for (int x = 0; x < g.nx; ++x) tc[x + 1] = tc[x] + solid_h(g, w, x, (w.tube_y0 + w.tube_h) % g.ny);
     for (int y = 0; y < g.ny; ++y) ob[y + 1] = ob[y] + solid_h(g, w, w.tube_x0, y);
+    const int tw = tile_cols(b);
     for (int y0 = 0; y0 < g.ny; y0 += b->tile_y)
-      for (int xb = 0; xb < g.nx; xb += b->tile_x) {
+      for (int xb = 0; xb < g.nx; xb += tw) {
         const int y1 = std::min(y0 + b->tile_y, g.ny);
-        const int x1 = std::min(xb + b->tile_x, g.nx);
+        const int x1 = std::min(xb + tw, g.nx);
         const long fluid = (long)(y1 - y0) * (x1 - xb) - (tc[x1] - tc[xb]) * (ob[y1] - ob[y0]);
         if (fluid) {
           tiles.push_back(TileDesc{i, xb, y0, y1});
-          cost.push_back(0.3 * (y1 - y0 + 2) * b->tile_x + (double)fluid);
+          cost.push_back(0.3 * (y1 - y0 + 2) * tw + (double)fluid);
         }
       }
   }
@@ -385,6 +418,7 @@ static lb_status build_chunks(lb_batch* b) {
 }
 
 static cudaError_t launch_reduce(lb_batch* b, int buf, int nsamples, int col, double* out, cudaStream_t s) {
+  if (b->storage == LB_STORAGE_MOMENTS) return launch_reduce_s<SM32>(b, buf, nsamples, col, out, s);
   if (b->storage == LB_STORAGE_F64) return launch_reduce_s<SF64>(b, buf, nsamples, col, out, s);
   if (b->storage == LB_STORAGE_F32) return launch_reduce_s<SF32>(b, buf, nsamples, col, out, s);
   return launch_reduce_s<SF16>(b, buf, nsamples, col, out, s);
@@ -473,14 +507,16 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
     return LB_ERR_CUDA;
   }
   const size_t el = elem_size(storage);
-  const int ng = storage == LB_STORAGE_F16DEV ? 8 : 9;
+  const int moments = storage == LB_STORAGE_MOMENTS;
+  const int nf = moments ? M_PLANES : 9;
+  const int ng = moments ? 0 : (storage == LB_STORAGE_F16DEV ? 8 : 9);
   size_t of = 0, og = 0, o0 = 0;
   for (int i = 0; i < n; ++i) {
     const size_t N = (size_t)grids[i].nx * grids[i].ny;
     b->off_f.push_back(of);
     b->off_g.push_back(og);
     b->off_g0.push_back(o0);
-    of += (9 * N + 63) / 64 * 64;
+    of += (nf * N + 63) / 64 * 64;
     og += (ng * N + 63) / 64 * 64;
     o0 += (N + 63) / 64 * 64;
     long fl = 0;
@@ -490,12 +526,21 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   }
   for (int k = 0; k < 2; ++k) {
     b->f[k] = balloc(b, of * el);
-    b->g[k] = balloc(b, og * el);
+    b->g[k] = og ? balloc(b, og * el) : NULL;
     b->g0[k] = storage == LB_STORAGE_F16DEV ? (float*)balloc(b, o0 * sizeof(float)) : NULL;
-    if (!b->f[k] || !b->g[k] || (storage == LB_STORAGE_F16DEV && !b->g0[k])) {
+    if (!b->f[k] || (og && !b->g[k]) || (storage == LB_STORAGE_F16DEV && !b->g0[k])) {
       snprintf(g_batch_create_err, sizeof g_batch_create_err, "device allocation of the batch state failed");
       lb_batch_destroy(b);
       return LB_ERR_NOMEM;
+    }
+    // solid nodes are never written by a step: start them (and everything) at 0
+    cudaError_t ez = cudaMemsetAsync(b->f[k], 0, of * el, b->stream);
+    if (ez == cudaSuccess && og) ez = cudaMemsetAsync(b->g[k], 0, og * el, b->stream);
+    if (ez == cudaSuccess && b->g0[k]) ez = cudaMemsetAsync(b->g0[k], 0, o0 * sizeof(float), b->stream);
+    if (ez != cudaSuccess) {
+      snprintf(g_batch_create_err, sizeof g_batch_create_err, "clearing the batch state failed");
+      lb_batch_destroy(b);
+      return LB_ERR_CUDA;
     }
   }
   const size_t capbytes = (size_t)n * std::max(sizeof(CapDesc<double>), sizeof(CapDesc<float>));
@@ -629,8 +674,33 @@ lb_status lb_batch_run_sampled(lb_batch* b, int nsamples, const long* at, double
   return check_err(b);
 }
 
+lb_status lb_batch_moments(lb_batch* b, int i, double* m) {
+  if (!b || i < 0 || i >= b->n || !m) return LB_ERR_ARG;
+  const size_t N = (size_t)b->grids[i].nx * b->grids[i].ny;
+  double* d = NULL;
+  if (b->have_alloc)
+    d = (double*)b->alloc.malloc_fn(M_PLANES * N * sizeof(double), (void*)b->stream, b->alloc.user);
+  else if (cudaMalloc((void**)&d, M_PLANES * N * sizeof(double)) != cudaSuccess)
+    d = NULL;
+  if (!d) return berr(b, "device allocation failed"), LB_ERR_NOMEM;
+  OpArgs a = lattice_args(b, i, b->parity);
+  a.out0 = d;
+  cudaError_t e = batch_ops(b->storage)(OP_MOMENTS_OUT, a, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m, d, M_PLANES * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  cudaError_t e2 = cudaStreamSynchronize(b->stream);
+  if (b->have_alloc)
+    b->alloc.free_fn(d, (void*)b->stream, b->alloc.user);
+  else
+    cudaFree(d);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return berr(b, "lb_batch_moments: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  return LB_OK;
+}
+
 lb_status lb_batch_populations(lb_batch* b, int i, double* f, double* g, int rested) {
   if (!b || i < 0 || i >= b->n || !f) return LB_ERR_ARG;
+  if (b->storage == LB_STORAGE_MOMENTS)
+    return berr(b, "the moment storage keeps no populations (lb_batch_moments)"), LB_ERR_ARG;
   const size_t N = (size_t)b->grids[i].nx * b->grids[i].ny;
   double* d = NULL;
   if (b->have_alloc)
@@ -673,17 +743,24 @@ lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, do
   // Candidates: the sliding-window body, and the staged body with its shallow
   // and deep rings (when every nx % 8 == 0), each over the tiles below; an
   // explicit lb_batch_set_kernel choice limits the bodies tried.
+  // The moment storage has one body (band heights as in lb_autotune).
+  const int moments = b->storage == LB_STORAGE_MOMENTS;
   const int cx[3] = {64, 128, 256};
-  const int cy[5] = {4, 8, 16, 32, 64};
+  const std::vector<int> cy = moments ? std::vector<int>{8, 12, 16, 20, 24, 32, 48}
+                                      : std::vector<int>{4, 8, 16, 32, 64};
   struct Body {
     int kernel, deep;
   };
   Body bodies[3];
   int nb = 0;
-  if (b->kernel != 2) bodies[nb++] = Body{1, 0};
-  if (b->kernel != 1 && b->staged_ok) {
-    bodies[nb++] = Body{2, 0};
-    bodies[nb++] = Body{2, 1};
+  if (moments) {
+    bodies[nb++] = Body{0, 0};
+  } else {
+    if (b->kernel != 2) bodies[nb++] = Body{1, 0};
+    if (b->kernel != 1 && b->staged_ok) {
+      bodies[nb++] = Body{2, 0};
+      bodies[nb++] = Body{2, 1};
+    }
   }
   const int keep_kernel = b->kernel;
   int bx = b->tile_x, by = b->tile_y, bk = batch_variant(b), bd = b->deep;
@@ -694,7 +771,7 @@ lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, do
   lb_status st = LB_OK;
   for (int v = 0; v < nb && st == LB_OK; ++v)
     for (int i = 0; i < 3 && st == LB_OK; ++i)
-      for (int j = 0; j < 5 && st == LB_OK; ++j) {
+      for (size_t j = 0; j < cy.size() && st == LB_OK; ++j) {
         b->kernel = bodies[v].kernel;
         b->deep = bodies[v].deep;
         st = lb_batch_set_tile(b, cx[i], cy[j]);
@@ -722,7 +799,7 @@ lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, do
   st = check_err(b);
   if (st) return st;
   // an automatic choice stays automatic unless tuning preferred the other body
-  if (keep_kernel != 0 || bk != batch_variant(b)) b->kernel = bk;
+  if (!moments && (keep_kernel != 0 || bk != batch_variant(b))) b->kernel = bk;
   b->deep = bd;
   st = lb_batch_set_tile(b, bx, by);  // rebuilds the schedule for this body
   if (st) return st;
@@ -743,6 +820,8 @@ lb_status lb_batch_set_barrier(lb_batch* b, unsigned int absent_blocks, double l
 
 lb_status lb_batch_set_kernel(lb_batch* b, int variant) {
   if (!b) return LB_ERR_ARG;
+  if (b->storage == LB_STORAGE_MOMENTS)
+    return variant == 0 || variant == 4 ? LB_OK : (berr(b, "the moment storage has one body (variant 4)"), LB_ERR_ARG);
   if (variant < 0 || variant > 3) return berr(b, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
   if (variant >= 2 && !b->staged_ok) return berr(b, "the staged body needs nx %% 8 == 0 in every lattice"), LB_ERR_ARG;
   BCK(cudaStreamSynchronize(b->stream));

@@ -9,6 +9,7 @@
 
 #include "lb_aux.cuh"
 #include "lb_device.cuh"
+#include "lb_moment.cuh"
 #include "lb_step_tma.cuh"
 
 namespace lbk {
@@ -87,7 +88,7 @@ struct BatchArgs {
 template <class S>
 __device__ __forceinline__ Buf<S> cap_buf(typename S::T* f, typename S::T* g, float* g0,
                                           const CapDesc<typename S::A>& c) {
-  return Buf<S>{f + c.off_f, g + c.off_g, g0 ? g0 + c.off_g0 : nullptr};
+  return Buf<S>{f + c.off_f, g ? g + c.off_g : nullptr, g0 ? g0 + c.off_g0 : nullptr};
 }
 
 template <class S, int BX>
@@ -195,6 +196,28 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_ker
     if (!grid_barrier_checked(a.bar, a.expected, a.limit_ns, !ok, a.err)) break;
   }
   if (producer && lane == 0) drain_ring<MODEL_BINARY, S, BX, NS>(R, issued);
+}
+
+// The moment storage over the batch's tiles: each warp of a CTA advances its
+// 30-column strip of the tile (the single-lattice moment kernel's strip), read
+// through L2 since other CTAs wrote the state earlier in the same launch.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : (NW == 4 ? 5 : 10)) batch_moment_kernel(BatchArgs<SM32> a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int s = 0; s < a.nsteps; ++s) {
+    const bool fromA = ((a.parity + s) & 1) == 0;
+    for (int t = a.start[blockIdx.x]; t < a.start[blockIdx.x + 1]; ++t) {
+      const TileDesc td = a.tiles[t];
+      const CapDesc<float>& c = a.caps[td.cap];
+      const float* src = (fromA ? a.fa : a.fb) + c.off_f;
+      float* dst = (fromA ? a.fb : a.fa) + c.off_f;
+      moment_strip<true>(c.G, c.P, src, dst, td.xb + warp * kMomCols, td.y0, td.y1, lane);
+    }
+    if (!grid_barrier(a.bar, a.expected, a.limit_ns)) {
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      return;
+    }
+  }
 }
 
 // Reductions of every lattice (mass, sum of phi, filled volume, l), in two

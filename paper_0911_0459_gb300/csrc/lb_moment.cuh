@@ -201,14 +201,16 @@ struct MAcc {
 // Columns produced per warp.
 constexpr int kMomCols = 30;
 
-template <int NW>
-__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) moment_step_kernel(MomArgs a) {
+// One warp advances columns [xo, xo + 30) of rows [y0, y1) of one lattice by
+// one step (every lane of the warp calls it, with the same arguments).
+// COHERENT: read src through L2 (a persistent launch whose other CTAs wrote
+// src earlier in the same launch).
+template <bool COHERENT>
+__device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P, const float* src_f, float* dst_f,
+                                             int xo, int y0, int y1, int lane) {
   constexpr unsigned FULL = 0xffffffffu;
-  const Geom& G = a.G;
   const int nx = G.nx, ny = G.ny;
   const unsigned N = (unsigned)nx * (unsigned)ny;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int xo = (blockIdx.x * NW + warp) * kMomCols;  // first column this warp produces
   if (xo >= nx) return;                                // whole warp
   const int xl = xo - 1 + lane;                        // this lane's column before wrapping
   const int x = ((xl % nx) + nx) % nx;
@@ -222,16 +224,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) mom
   const bool tc1 = tubed && col_in_tube(G, x);
   const bool tc2 = tubed && col_in_tube(G, xp);
   const bool warp_tube = __any_sync(FULL, tc0 || tc1 || tc2);
-  const int y0 = blockIdx.y * a.yc;
-  const int y1 = min(y0 + a.yc, ny);
-  const float2* __restrict__ src = reinterpret_cast<const float2*>(a.src);
-  float2* __restrict__ dst = reinterpret_cast<float2*>(a.dst);
+  const float2* __restrict__ src = reinterpret_cast<const float2*>(src_f);
+  float2* __restrict__ dst = reinterpret_cast<float2*>(dst_f);
+  auto ld2 = [&](unsigned i) { return COHERENT ? __ldcg(src + i) : __ldg(src + i); };
 
   // one row of the stencil window: centre c, s = right - left and
-  // d = (left - c) + (right - c) of rho and phi at this lane's column.  Solid
-  // neighbours enter as the centre value (the stored values of solid nodes are
-  // never used, and may be anything): a boundary node recovers its neighbours
-  // from c, s and d, then replaces the solid ones by the wall ghosts.
+  // d = (left - c) + (right - c) of rho and phi at this lane's column.  The
+  // stored values of solid nodes are never used and may be anything: a solid
+  // centre enters as 0 and solid neighbours as the centre value, so that a
+  // boundary node recovers its fluid neighbours from c, s and d, then replaces
+  // the solid ones by the wall ghosts.
   struct Row {
     float rc, rs, rh, pc, ps, ph;  // rh, ph hold d
   };
@@ -248,6 +250,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) mom
       pr = pe;
     }
     if (warp_tube && !in_band) {
+      if (tc1) {
+        r = 0.f;
+        p = 0.f;
+      }
       if (tc0) {
         rl = r;
         pl = p;
@@ -266,21 +272,21 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) mom
     return w;
   };
   auto load_rp = [&](unsigned rowb, float& rv, float& pv, float& re, float& pe) {
-    const float2 v = __ldg(src + (MP_RP * N + rowb + x));
+    const float2 v = ld2(MP_RP * N + rowb + x);
     rv = v.x;
     pv = v.y;
     re = 0.f;
     pe = 0.f;
     if (edge) {
-      const float2 e = __ldg(src + (MP_RP * N + rowb + xe));
+      const float2 e = ld2(MP_RP * N + rowb + xe);
       re = e.x;
       pe = e.y;
     }
   };
   auto load_jm = [&](unsigned rowb, float& jx, float& jy, float& mx, float& my) {
     const unsigned o = rowb + x;
-    const float2 j = __ldg(src + (MP_J * N + o));
-    const float2 m = __ldg(src + (MP_S * N + o));
+    const float2 j = ld2(MP_J * N + o);
+    const float2 m = ld2(MP_S * N + o);
     jx = j.x;
     jy = j.y;
     mx = m.x;
@@ -340,7 +346,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) mom
       const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
       stencil_rows(rc, rs, rh, rdx, rdy, rlap);
       stencil_rows(pc, ps, ph, pdx, pdy, plap);
-      collide_moment_node(a.P, mid.w.rc, jx, jy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+      collide_moment_node(P, mid.w.rc, jx, jy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
       a1.r += fs[0];
       a1.p += ge[0];
     } else {
@@ -382,13 +388,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) mom
             vp[j][2] = fmaf(0.5f, wr[j]->ph + wr[j]->ps, wr[j]->pc);
           }
           apply_ghosts(vr, sol, 0.f);
-          apply_ghosts(vp, sol, a.P.h);
+          apply_ghosts(vp, sol, P.h);
           stencil3(vr, rdx, rdy, rlap);
           stencil3(vp, pdx, pdy, plap);
           cjx = 0.f;
           cjy = 0.f;
         }
-        collide_moment_node(a.P, mid.w.rc, cjx, cjy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+        collide_moment_node(P, mid.w.rc, cjx, cjy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
         // own node: the rest population, and bounce-back of what was sent into a
         // wall (all populations as deviations from w_i, which add up to 1, 0, 0, 0, 0)
         a1.r += fs[0];
@@ -472,6 +478,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) mom
     step(S2, S0, S1, A2, A0, A1, k);
     if (++k > y1) break;
   }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) moment_step_kernel(MomArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int y0 = blockIdx.y * a.yc;
+  moment_strip<false>(a.G, a.P, a.src, a.dst, (blockIdx.x * NW + warp) * kMomCols, y0, min(y0 + a.yc, a.G.ny), lane);
 }
 
 }  // namespace lbk

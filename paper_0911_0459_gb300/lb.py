@@ -96,6 +96,7 @@ def library():
         "lb_batch_lengths": (C.c_int, [vp, dp]),
         "lb_batch_run_sampled": (C.c_int, [vp, C.c_int, dp, dp]),
         "lb_batch_populations": (C.c_int, [vp, C.c_int, dp, dp, C.c_int]),
+        "lb_batch_moments": (C.c_int, [vp, C.c_int, dp]),
         "lb_batch_set_tile": (C.c_int, [vp, C.c_int, C.c_int]),
         "lb_batch_autotune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(C.c_double)]),
@@ -119,7 +120,7 @@ def exported_symbols():
             "lb_get_populations", "lb_set_populations", "lb_get_moments", "lb_sync", "lb_time", "lb_fluid_nodes",
             "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
             "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
-            "lb_batch_populations", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
+            "lb_batch_populations", "lb_batch_moments", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
             "lb_batch_set_kernel", "lb_batch_get_kernel", "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error"]
 
 
@@ -409,6 +410,13 @@ class Batch:
         g = np.empty((9, c.ny, c.nx))
         _bcheck(library().lb_batch_populations(self.h, int(i), _p(f), _p(g), int(bool(rested))), self.h)
         return f, g
+
+    def moments(self, i):
+        """(6, ny, nx) moments of lattice i, as Lattice.moments."""
+        c = self.caps[i]
+        m = np.empty((6, c.ny, c.nx))
+        _bcheck(library().lb_batch_moments(self.h, int(i), _p(m)), self.h)
+        return m
 
     def set_tile(self, tx, ty):
         _bcheck(library().lb_batch_set_tile(self.h, int(tx), int(ty)), self.h)

@@ -11,7 +11,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, Batch, Lattice, LbError  # noqa: E402
+from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STORAGE_MOMENTS, Batch,  # noqa: E402
+                                   Lattice, LbError)
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
 
 
@@ -54,6 +55,35 @@ def test_batch_is_bitwise_identical_to_independent_lattices(storage, body):
         np.testing.assert_allclose(red[i, 1:], [d["l_vol"], d["mass"], d["phi_sum"]], rtol=1e-12,
                                    atol=1e-12 * c.nodes)
         lat.close()
+    b.close()
+
+
+@pytest.mark.parametrize("align", [8, 1])
+def test_moment_storage_batch_is_bitwise_identical_to_independent_lattices(align):
+    """The persistent moment body runs the single-lattice moment kernel's strips:
+    every lattice evolves bit for bit as it does alone, over changing tiles,
+    ragged strips and bands, and nx of any residue."""
+    caps = small_sweep(seed=6, n=5, align=align)
+    b = Batch(caps, storage=STORAGE_MOMENTS)
+    assert b.kernel() == 4
+    with pytest.raises(LbError):
+        b.populations(0)
+    for tx, ty in ((64, 4), (128, 20), (256, 7), (128, 64)):
+        b.set_tile(tx, ty)
+        b.step(11)
+    total = b.time
+    red = b.lengths()
+    for i, c in enumerate(caps):
+        lat = Lattice.from_workload(c, storage=STORAGE_MOMENTS)
+        lat.step(total)
+        assert np.array_equal(b.moments(i), lat.moments()), i
+        d = lat.filled_length()
+        assert red[i, 0] == d["l"], i
+        np.testing.assert_allclose(red[i, 1:], [d["l_vol"], d["mass"], d["phi_sum"]], rtol=1e-12,
+                                   atol=1e-12 * c.nodes)
+        lat.close()
+    tx, ty, ms = b.autotune(steps=2)
+    assert tx in (64, 128, 256) and ms > 0
     b.close()
 
 
