@@ -154,9 +154,12 @@ def precision_report(Lattice, orc, steps):
     rho_o, _, _, phi_o = orc.fields()
     l_o = orc.filled_length()["l"]
     out = {"workload": "1024x64 crop of the large capillary, default initial state", "steps": steps}
-    for name, st in (("f64", STORAGE_F64), ("f32", STORAGE_F32), ("f16dev", STORAGE_F16DEV),
-                     ("moments_f32", STORAGE_MOMENTS)):
-        lat = Lattice.from_workload(W.config_binary_crop_1024x64(st))
+    import dataclasses
+    for name, st, table in (("f64", STORAGE_F64, 0), ("f32", STORAGE_F32, 0), ("f16dev", STORAGE_F16DEV, 0),
+                            ("moments_f32", STORAGE_MOMENTS, 0), ("f32_nu_table_1e4", STORAGE_F32, 10000)):
+        cap = W.config_binary_crop_1024x64(st)
+        cap.params = dataclasses.replace(cap.params, nu_table=table)
+        lat = Lattice.from_workload(cap)
         lat.step(steps)
         rho, _, _, phi = lat.fields()
         out[name] = {"max_abs_drho": float(np.abs(rho - rho_o).max()),

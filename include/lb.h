@@ -104,6 +104,9 @@ typedef struct {
   double rho_l, rho_g;     /* liquid-gas: densities of the default initial state and of the
                               l(t) threshold (rho_l + rho_g)/2 */
   int l0;                  /* default initial state: liquid in [gas_cols, tube_x0 + l0) */
+  int nu_table;            /* binary: 0 = omega from the exact local nu; K >= 2 = from the
+                              nearest of K viscosities evenly spaced over [nu_g, nu_l], the
+                              look-up table of App. A (the paper uses ~10^4) */
 } lb_params;
 
 /* Optional device allocator.  malloc_fn returns device memory of at least bytes

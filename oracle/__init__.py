@@ -24,7 +24,7 @@ class OrcParams(C.Structure):
                 ("kappa", C.c_double), ("a", C.c_double), ("b", C.c_double), ("T", C.c_double),
                 ("A", C.c_double), ("M", C.c_double), ("nu_l", C.c_double), ("nu_g", C.c_double),
                 ("nu", C.c_double), ("lambda_scale", C.c_double),
-                ("rho_l", C.c_double), ("rho_g", C.c_double)]
+                ("rho_l", C.c_double), ("rho_g", C.c_double), ("nu_table", C.c_int)]
 
 
 def lib():
@@ -96,7 +96,7 @@ class Oracle:
         self.wall_grad = wg
         self.params = OrcParams(cap.nx, cap.ny, p.model, cap.tube_x0, cap.tube_len, cap.tube_y0,
                                 cap.tube_h, wg, p.kappa, p.a, p.b, p.T, p.A, p.M, p.nu_l, p.nu_g,
-                                p.nu, p.lambda_scale, p.rho_l, p.rho_g)
+                                p.nu, p.lambda_scale, p.rho_l, p.rho_g, int(getattr(p, "nu_table", 0)))
         h = C.c_void_p()
         rc = lib().orc_create(C.byref(self.params), C.byref(h))
         if rc != 0:

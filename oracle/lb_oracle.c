@@ -46,6 +46,9 @@
  *             from x0, of phi (binary) or rho - (rho_l + rho_g)/2 (liquid-gas)
  *             along the tube's middle row (mean of the two middle rows when H is
  *             even), linearly interpolated.
+ *   table   : App. A keeps collision matrices for ~10^4 viscosities and uses the
+ *             closest one; with nu_table = K >= 2 the K viscosities are spaced
+ *             evenly over [nu_g, nu_l] and the nearest is used (0: exact nu).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -104,6 +107,7 @@ typedef struct {
   double A, M, nu_l, nu_g;
   double nu, lambda_scale;
   double rho_l, rho_g;
+  int nu_table; /* 0: exact nu; K >= 2: nearest of K viscosities evenly spaced over [nu_g, nu_l] */
 } orc_params;
 
 typedef struct {
@@ -336,6 +340,7 @@ int orc_create(const orc_params *p, void **out) {
   if (p->tube_len < 0 || p->tube_len > p->nx) return ORC_ERR_ARG;
   if (p->tube_len > 0 && (p->tube_h < 2 || p->tube_h >= p->ny)) return ORC_ERR_ARG;
   if (p->tube_len > 0 && p->tube_len < p->nx && p->nx - p->tube_len < 2) return ORC_ERR_ARG;
+  if (p->nu_table < 0 || p->nu_table == 1) return ORC_ERR_ARG;
   orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
   if (!s) return ORC_ERR_MEM;
   s->p = *p;
@@ -385,6 +390,8 @@ static double local_nu(const orc_params *p, double phi) {
   double c = 0.5 * (phi + 1.0);
   if (c < 0.0) c = 0.0;
   if (c > 1.0) c = 1.0;
+  /* App. A: a table of viscosities, the closest entry is used */
+  if (p->nu_table >= 2) c = nearbyint(c * (p->nu_table - 1)) / (p->nu_table - 1);
   return p->nu_g + c * (p->nu_l - p->nu_g);
 }
 

@@ -325,10 +325,16 @@ __global__ void __launch_bounds__(1024) reduce_final_kernel(Geom G, Buf<S> B, do
   __shared__ int first;
   __shared__ double tot[RED_PARTS];
   if (threadIdx.x == 0) first = INT_MAX;
-  if (threadIdx.x < RED_PARTS) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += partials[b * RED_PARTS + threadIdx.x];
-    tot[threadIdx.x] = s;
+  // warp 0 adds the partials: lane j takes blocks j, j + 32, ... in order, then a
+  // fixed shuffle tree (the result does not depend on scheduling)
+  if (threadIdx.x < 32) {
+    double t[RED_PARTS] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nparts; b += 32)
+      for (int k = 0; k < RED_PARTS; ++k) t[k] += partials[b * RED_PARTS + k];
+    for (int k = 0; k < RED_PARTS; ++k) {
+      const double v = warp_sum(t[k]);
+      if (threadIdx.x == 0) tot[k] = v;
+    }
   }
   __syncthreads();
   const int L = G.tube_len;

@@ -130,6 +130,7 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
   a.tube_x0 = w.tube_x0; a.tube_len = w.tube_len; a.tube_y0 = w.tube_y0; a.tube_h = w.tube_h;
   a.kappa = p.kappa; a.a = p.a; a.b = p.b; a.T = p.T; a.Acoef = p.A; a.M = p.M;
   a.nu_l = p.nu_l; a.nu_g = p.nu_g; a.nu = p.nu; a.lambda_scale = p.lambda_scale; a.h = w.wall_grad;
+  a.lut = p.nu_table >= 2 ? p.nu_table - 1 : 0;
   a.rho_l = p.rho_l; a.rho_g = p.rho_g;
   const size_t el = elem_size(b->storage);
   OpBufs ob;
@@ -436,6 +437,8 @@ static void fill_caps(lb_batch* b, std::vector<CapDesc<A>>& caps) {
     c.P.kappa = A(p.kappa); c.P.a = A(p.a); c.P.b = A(p.b); c.P.T = A(p.T);
     c.P.Acoef = A(p.A); c.P.M = A(p.M); c.P.nu_l = A(p.nu_l); c.P.nu_g = A(p.nu_g);
     c.P.nu = A(p.nu); c.P.lambda_scale = A(p.lambda_scale); c.P.h = A(w.wall_grad);
+    c.P.lut = A(p.nu_table >= 2 ? p.nu_table - 1 : 0);
+    c.P.lut_inv = p.nu_table >= 2 ? A(1.0 / (p.nu_table - 1)) : A(0);
     c.off_f = b->off_f[i];
     c.off_g = b->off_g[i];
     c.off_g0 = b->off_g0[i];
@@ -482,6 +485,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
     if (w.tube_len > 0 && (w.tube_x0 < 0 || w.tube_x0 >= g.nx || w.tube_y0 < 0 || w.tube_y0 >= g.ny ||
                            w.tube_h < 2 || w.tube_h >= g.ny || (w.tube_len < g.nx && g.nx - w.tube_len < 2)))
       return berr(NULL, "lattice %d: invalid tube geometry", i), LB_ERR_ARG;
+    if (params[i].nu_table < 0 || params[i].nu_table == 1)
+      return berr(NULL, "lattice %d: nu_table must be 0 or >= 2", i), LB_ERR_ARG;
     if (!(params[i].nu_l > 0) || !(params[i].nu_g > 0) || !(params[i].A > 0) || !(params[i].kappa > 0))
       return berr(NULL, "lattice %d: invalid binary parameters", i), LB_ERR_ARG;
   }

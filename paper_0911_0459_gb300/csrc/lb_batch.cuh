@@ -181,7 +181,11 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_ker
           }
         } else {
           const Buf<S> dst = fromA ? cap_buf<S>(a.fb, a.gb, a.g0b, c) : cap_buf<S>(a.fa, a.ga, a.g0a, c);
-          ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, c.P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+          // a value copy: the per-node arithmetic then compiles as in the single-lattice
+          // kernel (parameters that live behind a pointer the pushes might alias led the
+          // compiler to fuse multiply-adds differently, a last-bit difference)
+          const Phys<typename S::A> P = c.P;
+          ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane);
         }
       }
       k += (unsigned)(td.y1 - td.y0 + 2);

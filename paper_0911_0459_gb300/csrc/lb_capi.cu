@@ -128,6 +128,7 @@ static OpArgs base_args(const lb_ctx* c) {
   a.kappa = p.kappa; a.a = p.a; a.b = p.b; a.T = p.T;
   a.Acoef = p.A; a.M = p.M; a.nu_l = p.nu_l; a.nu_g = p.nu_g;
   a.nu = p.nu; a.lambda_scale = p.lambda_scale; a.h = c->walls.wall_grad;
+  a.lut = p.model == LB_MODEL_BINARY && p.nu_table >= 2 ? p.nu_table - 1 : 0;
   a.rho_l = p.rho_l; a.rho_g = p.rho_g;
   a.thr = p.model == LB_MODEL_LIQUID_GAS ? 0.5 * (p.rho_l + p.rho_g) : 0.0;
   a.bx = c->tile_x;
@@ -219,6 +220,7 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
   } else {
     if (!(p->nu_l > 0) || !(p->nu_g > 0)) return set_err(c, "nu_l, nu_g must be > 0"), LB_ERR_ARG;
     if (!(p->A > 0) || !(p->kappa > 0) || !(p->M >= 0)) return set_err(c, "invalid binary parameters"), LB_ERR_ARG;
+    if (p->nu_table < 0 || p->nu_table == 1) return set_err(c, "nu_table must be 0 or >= 2"), LB_ERR_ARG;
   }
   return LB_OK;
 }

@@ -39,6 +39,7 @@ struct Phys {
   A nu;                // liquid-gas viscosity
   A lambda_scale;      // lambda = lambda_scale * nu_local
   A h;                 // wall gradient of the wetted field
+  A lut, lut_inv;      // viscosity table of App. A: K - 1 steps (0: exact nu) and 1 / (K - 1)
 };
 
 // ------------------------------------------------------------------ storage
@@ -263,12 +264,15 @@ __device__ __forceinline__ void rest(A f[9]) {
   f[5] -= c; f[6] += c; f[7] -= d; f[8] += d;
 }
 
-// Local viscosity, Eq. (nu), with (phi + 1)/2 clamped to [0, 1].
+// Local viscosity, Eq. (nu), with (phi + 1)/2 clamped to [0, 1]; with the table of
+// App. A, the nearest of its evenly spaced viscosities.
 template <typename A>
 __device__ __forceinline__ A local_nu_binary(const Phys<A>& P, A phi) {
   A c = (phi + A(1)) * A(0.5);
   c = c < A(0) ? A(0) : (c > A(1) ? A(1) : c);
-  return P.nu_g + c * (P.nu_l - P.nu_g);
+  if (P.lut > A(0)) c = rint(c * P.lut) * P.lut_inv;
+  // explicit fused multiply-add: the same rounding in every kernel that inlines this
+  return fma(c, P.nu_l - P.nu_g, P.nu_g);
 }
 
 // Lattice velocities (Sec. 2.1, c = 1) as compile-time functions of i.
@@ -310,7 +314,7 @@ __device__ __forceinline__ void collide_node(const Phys<A>& P, A vr[3][3], A vp[
     const A p0 = rho * A(1.0 / 3.0) + P.Acoef * (A(-0.5) * phi2 + A(0.75) * phi2 * phi2);
     const A mu = P.Acoef * (phi2 * phi - phi) - P.kappa * plap;
     const A nu = local_nu_binary(P, phi);
-    omega = A(2) * rcp_rn(A(6) * nu + A(1));
+    omega = A(2) * rcp_rn(fma(A(6), nu, A(1)));
     feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * phi * plap, P.kappa, pdx, pdy, rdx, rdy, P.lambda_scale * nu, fe);
     geq9<A>(phi, ux, uy, A(2) * P.M * mu, ge);
   } else {

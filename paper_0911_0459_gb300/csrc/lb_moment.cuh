@@ -133,7 +133,9 @@ __device__ __forceinline__ void collide_moment_node(const Phys<float>& P, float 
   const float ux = jx * inv, uy = jy * inv;
   const float phi2 = phi * phi;
   const float mu = fmaf(-P.kappa, plap, P.Acoef * fmaf(phi2, phi, -phi));
-  const float nu = fmaf(__saturatef(fmaf(phi, 0.5f, 0.5f)), P.nu_l - P.nu_g, P.nu_g);
+  float cl = __saturatef(fmaf(phi, 0.5f, 0.5f));  // liquid fraction (Eq. nu, clamped)
+  if (P.lut > 0.f) cl = rintf(cl * P.lut) * P.lut_inv;  // viscosity table of App. A
+  const float nu = fmaf(cl, P.nu_l - P.nu_g, P.nu_g);
   const float omega = 2.f * rcp_fast(fmaf(6.f, nu, 1.f));
   const float lam = P.lambda_scale * nu;
   // P0 - 1/3: the pressure p0 = rho/3 + A(-phi^2/2 + 3 phi^4/4) less kappa phi lap phi

@@ -20,6 +20,7 @@ struct OpArgs {
   int nx, ny, tube_x0, tube_len, tube_y0, tube_h;
   // physics (converted to the arithmetic type by the instantiation)
   double kappa, a, b, T, Acoef, M, nu_l, nu_g, nu, lambda_scale, h;
+  double lut;  // viscosity table steps K - 1 (0: exact)
   double rho_l, rho_g, thr;
   // buffers
   OpBufs src, dst;

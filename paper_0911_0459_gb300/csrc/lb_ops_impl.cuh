@@ -23,6 +23,8 @@ static Phys<A> to_phys(const OpArgs& a) {
   p.kappa = A(a.kappa); p.a = A(a.a); p.b = A(a.b); p.T = A(a.T);
   p.Acoef = A(a.Acoef); p.M = A(a.M); p.nu_l = A(a.nu_l); p.nu_g = A(a.nu_g);
   p.nu = A(a.nu); p.lambda_scale = A(a.lambda_scale); p.h = A(a.h);
+  p.lut = A(a.lut);
+  p.lut_inv = a.lut > 0 ? A(1.0 / a.lut) : A(0);
   return p;
 }
 

@@ -45,7 +45,7 @@ class LbParams(C.Structure):
                 ("kappa", C.c_double), ("a", C.c_double), ("b", C.c_double), ("T", C.c_double),
                 ("A", C.c_double), ("M", C.c_double), ("nu_l", C.c_double), ("nu_g", C.c_double),
                 ("nu", C.c_double), ("lambda_scale", C.c_double),
-                ("rho_l", C.c_double), ("rho_g", C.c_double), ("l0", C.c_int)]
+                ("rho_l", C.c_double), ("rho_g", C.c_double), ("l0", C.c_int), ("nu_table", C.c_int)]
 
 
 MALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -192,7 +192,7 @@ class Lattice:
     def __init__(self, nx, ny, *, model, storage, tube_x0=0, tube_len=0, tube_y0=0, tube_h=None,
                  gas_cols=0, wall_grad=0.0, kappa=0.04, a=9 / 49, b=2 / 21, T=0.56, A=0.04, M=0.1,
                  nu_l=1 / 6, nu_g=1 / 6, nu=1 / 6, lambda_scale=1.0, rho_l=4.54, rho_g=2.59, l0=10,
-                 stream=None, use_torch_allocator=True):
+                 nu_table=0, stream=None, use_torch_allocator=True):
         import torch
         L = library()
         if tube_h is None:
@@ -202,7 +202,7 @@ class Lattice:
         self.walls = LbWalls(int(tube_x0), int(tube_len), int(tube_y0), int(tube_h), int(gas_cols),
                              float(wall_grad))
         self.params = LbParams(int(model), int(storage), kappa, a, b, T, A, M, nu_l, nu_g, nu,
-                               lambda_scale, rho_l, rho_g, int(l0))
+                               lambda_scale, rho_l, rho_g, int(l0), int(nu_table))
         dev = torch.cuda.current_device()
         self._torch_stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self._alloc = _TorchAllocator(dev) if use_torch_allocator else None
@@ -230,7 +230,7 @@ class Lattice:
                    tube_x0=cap.tube_x0, tube_len=cap.tube_len, tube_y0=cap.tube_y0, tube_h=cap.tube_h,
                    gas_cols=cap.gas_cols, wall_grad=wg, kappa=p.kappa, a=p.a, b=p.b, T=p.T, A=p.A,
                    M=p.M, nu_l=p.nu_l, nu_g=p.nu_g, nu=p.nu, lambda_scale=p.lambda_scale,
-                   rho_l=p.rho_l, rho_g=p.rho_g, l0=cap.l0, **kw)
+                   rho_l=p.rho_l, rho_g=p.rho_g, l0=cap.l0, nu_table=p.nu_table, **kw)
 
     def close(self):
         if getattr(self, "h", None) is not None:
@@ -341,7 +341,8 @@ def _structs_for(cap, storage=None):
     grid = LbGrid(cap.nx, cap.ny)
     walls = LbWalls(cap.tube_x0, cap.tube_len, cap.tube_y0, cap.tube_h, cap.gas_cols, float(wg))
     params = LbParams(p.model, p.storage if storage is None else storage, p.kappa, p.a, p.b, p.T, p.A, p.M,
-                      p.nu_l, p.nu_g, p.nu, p.lambda_scale, p.rho_l, p.rho_g, int(cap.l0))
+                      p.nu_l, p.nu_g, p.nu, p.lambda_scale, p.rho_l, p.rho_g, int(cap.l0),
+                      int(p.nu_table))
     return grid, walls, params
 
 

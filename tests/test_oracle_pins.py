@@ -515,3 +515,32 @@ def test_binary_washburn_filling_and_poiseuille_profile():
     h_eff = roots[1] - roots[0]
     vbar = np.sum(prof) / h_eff
     assert abs(vbar / an.poiseuille_mean_velocity(h_eff, nul, dpdx) - 1) < 0.2
+
+
+# ------------------------------------------------------ viscosity table (App. A)
+
+
+def test_viscosity_table_picks_the_nearest_entry():
+    """App. A: collision matrices for a table of viscosities, the closest one used.
+    With two entries every node relaxes at the bulk rate of its phase (the sign of
+    phi); with 10^4 entries omega differs from the exact one by at most half a step
+    of the table times d omega / d nu."""
+    base = dict(nu_l=0.83, nu_g=0.0166)
+    cap0 = W.Capillary("t", 64, 20, 16, 40, 3, 12, 4, 20, W.binary_params(**base), wall_grad=-0.1)
+    fields = W.random_state_fields(cap0.nx, cap0.ny, seed=8, model=W.BINARY, amp_u=0.01)
+    _, _, om_exact = oracle.Oracle(cap0).init_fields(*fields).equilibria()
+    phi = fields[3]
+    fluid = oracle.Oracle(cap0).node_kinds() != 2
+    om = lambda nu: 2.0 / (6.0 * nu + 1.0)
+    for K in (2, 10000):
+        cap = W.Capillary("t", 64, 20, 16, 40, 3, 12, 4, 20, W.binary_params(**base, nu_table=K),
+                          wall_grad=-0.1)
+        _, _, om_t = oracle.Oracle(cap).init_fields(*fields).equilibria()
+        if K == 2:
+            want = np.where(phi > 0, om(0.83), om(0.0166))
+            np.testing.assert_allclose(om_t[fluid], want[fluid], rtol=1e-14)
+        else:
+            step = (0.83 - 0.0166) / (K - 1)
+            bound = 0.5 * step * 12.0 / (6.0 * 0.0166 + 1.0) ** 2   # |d omega / d nu| <= 12 / (6 nu_g + 1)^2
+            d = np.abs(om_t - om_exact)[fluid]
+            assert d.max() <= bound * (1 + 1e-9) and d.max() > 0

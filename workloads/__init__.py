@@ -52,6 +52,9 @@ class Params:
     # densities used for the initial profile and for the liquid-gas l(t) threshold
     rho_l: float = 4.54
     rho_g: float = 2.59
+    # binary: 0 = exact local viscosity; K >= 2 = the nearest of K viscosities evenly
+    # spaced over [nu_g, nu_l] (the look-up table of App. A)
+    nu_table: int = 0
 
 
 def lg_params(**kw) -> Params:
