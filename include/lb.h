@@ -296,8 +296,8 @@ const char *lb_batch_last_error(const lb_batch *b);
  * lb_filled_length).  nblocks is the number of blocks of the first reduction
  * pass, each of which leaves one partial sum in the scratch.
  *
- * Scratch: a file-scope device array of LB_NOALLOC_MAX_BLOCKS x 3 doubles
- * (48 KiB) that every GPU which loads the library holds until the process
+ * Scratch: a file-scope device array of LB_NOALLOC_MAX_BLOCKS x 4 doubles
+ * (64 KiB) that every GPU which loads the library holds until the process
  * exits.  nblocks outside [1, LB_NOALLOC_MAX_BLOCKS] is rejected with
  * LB_ERR_ARG.  Every call shares that array and it keeps the last call's
  * contents; each call writes every slot it later reads, so nothing has to be

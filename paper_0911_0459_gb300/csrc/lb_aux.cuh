@@ -209,7 +209,7 @@ __global__ void moments_out_kernel(Geom G, Buf<S> B, double* __restrict__ out) {
 // ------------------------------------------------------------- reductions
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_PARTS = 3;  // mass, phi sum, tube liquid volume
+constexpr int RED_PARTS = 4;  // mass, phi sum, tube liquid volume, first meniscus column
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -259,32 +259,6 @@ __device__ __forceinline__ double finish_volume(const RedAcc& acc, double rho_l,
                                : (acc.tube - (double)acc.ntube * rho_g) / (rho_l - rho_g);
 }
 
-// Block partial sums in FP64 (see red_add_node).  partials[b * RED_PARTS + k].
-template <int MODEL, class S>
-__global__ void __launch_bounds__(RED_THREADS) reduce_partials_kernel(Geom G, Buf<S> B, double rho_l, double rho_g,
-                                                                      double* __restrict__ partials) {
-  const size_t N = (size_t)G.nx * G.ny;
-  RedAcc ra;
-  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
-    if (is_solid(G, x, y)) continue;
-    red_add_node<MODEL, S>(G, B, N, n, x, y, ra);
-  }
-  const double acc[RED_PARTS] = {ra.mass, ra.phi, finish_volume<MODEL>(ra, rho_l, rho_g)};
-  __shared__ double sh[RED_PARTS][RED_THREADS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = 0; k < RED_PARTS; ++k) {
-    const double v = warp_sum(acc[k]);
-    if (lane == 0) sh[k][wid] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < RED_PARTS) {
-    double s = 0.0;
-    for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[threadIdx.x][w];
-    partials[blockIdx.x * RED_PARTS + threadIdx.x] = s;
-  }
-}
-
 // Centre-line value of the tube at tube column k: phi (binary) or rho - threshold.
 template <int MODEL, class S>
 __device__ __forceinline__ double centre_value(const Geom& G, const Buf<S>& B, size_t N, int k, double thr) {
@@ -314,47 +288,79 @@ __device__ __forceinline__ double centre_value(const Geom& G, const Buf<S>& B, s
   return 0.5 * (va + vb) - thr;
 }
 
-// One block: sums the partials in a fixed order (deterministic) and finds the
-// first sign change of the centre line scanning from the inlet.
-// out = {l_centre, l_vol, mass, phi_sum}.
+// Block partial sums in FP64 (see red_add_node), and the first tube column k of
+// the block's share whose centre line changes sign between k and k + 1 (k = 0
+// counts when the inlet is already gas); INT_MAX if none.
+// partials[b * RED_PARTS + k].
 template <int MODEL, class S>
-__global__ void __launch_bounds__(1024) reduce_final_kernel(Geom G, Buf<S> B, double thr, int nparts,
-                                                           const double* __restrict__ partials,
-                                                           double* __restrict__ out) {
+__global__ void __launch_bounds__(RED_THREADS) reduce_partials_kernel(Geom G, Buf<S> B, double rho_l, double rho_g,
+                                                                      double thr, double* __restrict__ partials) {
   const size_t N = (size_t)G.nx * G.ny;
-  __shared__ int first;
-  __shared__ double tot[RED_PARTS];
-  if (threadIdx.x == 0) first = INT_MAX;
-  // warp 0 adds the partials: lane j takes blocks j, j + 32, ... in order, then a
-  // fixed shuffle tree (the result does not depend on scheduling)
-  if (threadIdx.x < 32) {
-    double t[RED_PARTS] = {0.0, 0.0, 0.0};
-    for (int b = threadIdx.x; b < nparts; b += 32)
-      for (int k = 0; k < RED_PARTS; ++k) t[k] += partials[b * RED_PARTS + k];
-    for (int k = 0; k < RED_PARTS; ++k) {
-      const double v = warp_sum(t[k]);
-      if (threadIdx.x == 0) tot[k] = v;
+  RedAcc ra;
+  for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(n % G.nx), y = (int)(n / G.nx);
+    if (is_solid(G, x, y)) continue;
+    red_add_node<MODEL, S>(G, B, N, n, x, y, ra);
+  }
+  int first = INT_MAX;
+  const int L = G.tube_len;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x) {
+    const double c0 = centre_value<MODEL, S>(G, B, N, k, thr);
+    const bool hit = (k == 0 && !(c0 > 0.0)) ||
+                     (k + 1 < L && c0 > 0.0 && !(centre_value<MODEL, S>(G, B, N, k + 1, thr) > 0.0));
+    if (hit) {
+      first = k;  // k grows: the thread's first hit is its smallest
+      break;
     }
   }
-  __syncthreads();
-  const int L = G.tube_len;
-  // candidate k: c(k) > 0 and c(k+1) <= 0, or k == 0 with c(0) <= 0 (inlet already gas)
-  for (int k = threadIdx.x; k < L; k += blockDim.x) {
-    const double c0 = centre_value<MODEL, S>(G, B, N, k, thr);
-    bool hit = false;
-    if (k == 0 && !(c0 > 0.0)) hit = true;
-    if (!hit && k + 1 < L && c0 > 0.0) hit = !(centre_value<MODEL, S>(G, B, N, k + 1, thr) > 0.0);
-    if (hit) atomicMin(&first, k);
+  const double acc[3] = {ra.mass, ra.phi, finish_volume<MODEL>(ra, rho_l, rho_g)};
+  __shared__ double sh[3][RED_THREADS / 32];
+  __shared__ int shf[RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 3; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) sh[k][wid] = v;
   }
+  for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+  if (lane == 0) shf[wid] = first;
   __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < RED_THREADS / 32; ++w) s += sh[threadIdx.x][w];
+    partials[blockIdx.x * RED_PARTS + threadIdx.x] = s;
+  } else if (threadIdx.x == 3) {
+    int f = INT_MAX;
+    for (int w = 0; w < RED_THREADS / 32; ++w) f = min(f, shf[w]);
+    partials[blockIdx.x * RED_PARTS + 3] = (double)f;
+  }
+}
+
+// One block: sums the partials in a fixed order (deterministic), takes the first
+// centre-line sign change over all blocks and interpolates l there.
+// out = {l_centre, l_vol, mass, phi_sum}.
+template <int MODEL, class S>
+__global__ void __launch_bounds__(32) reduce_final_kernel(Geom G, Buf<S> B, double thr, int nparts,
+                                                         const double* __restrict__ partials,
+                                                         double* __restrict__ out) {
+  const size_t N = (size_t)G.nx * G.ny;
+  // lane j takes blocks j, j + 32, ... in order, then a fixed shuffle tree
+  double t[3] = {0.0, 0.0, 0.0};
+  double fm = (double)INT_MAX;
+  for (int b = threadIdx.x; b < nparts; b += 32) {
+    for (int k = 0; k < 3; ++k) t[k] += partials[b * RED_PARTS + k];
+    fm = fmin(fm, partials[b * RED_PARTS + 3]);
+  }
+  for (int k = 0; k < 3; ++k) t[k] = warp_sum(t[k]);
+  for (int o = 16; o > 0; o >>= 1) fm = fmin(fm, __shfl_xor_sync(0xffffffffu, fm, o));
   if (threadIdx.x == 0) {
+    const int L = G.tube_len;
     double l = 0.0;
     if (L <= 0) {
       l = 0.0;
-    } else if (first == INT_MAX) {
+    } else if (fm >= (double)INT_MAX) {
       l = (double)L;
     } else {
-      const int k = first;
+      const int k = (int)fm;
       const double c0 = centre_value<MODEL, S>(G, B, N, k, thr);
       if (k == 0 && !(c0 > 0.0)) {
         l = 0.0;
@@ -364,9 +370,9 @@ __global__ void __launch_bounds__(1024) reduce_final_kernel(Geom G, Buf<S> B, do
       }
     }
     out[0] = l;
-    out[1] = L > 0 ? tot[2] / G.tube_h : 0.0;
-    out[2] = tot[0];
-    out[3] = tot[1];
+    out[1] = L > 0 ? t[2] / G.tube_h : 0.0;
+    out[2] = t[0];
+    out[3] = t[1];
   }
 }
 

@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "lb.h"
-#include "lb_moment.cuh"
+#include "lb_aux.cuh"
 #include "lb_ops.h"
 
 using namespace lbk;
@@ -337,7 +337,7 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
       return LB_ERR_CUDA;
     }
   }
-  c->partials = (double*)dev_alloc_owned(c, kRedParts * 3 * sizeof(double));
+  c->partials = (double*)dev_alloc_owned(c, kRedParts * RED_PARTS * sizeof(double));
   c->red_out = (double*)dev_alloc_owned(c, 4 * sizeof(double));
   c->errflag = (int*)dev_alloc_owned(c, 256);
   if (c->errflag && cudaMemsetAsync(c->errflag, 0, 256, c->stream) != cudaSuccess) c->errflag = NULL;

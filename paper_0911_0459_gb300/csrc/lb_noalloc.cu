@@ -1,12 +1,12 @@
 // lb_filled_length_noalloc: the FP64 reductions of lb_filled_length for callers
 // that cannot allocate device memory.
 //
-// The first reduction pass writes one partial sum per block (mass, sum of phi,
-// filled volume).  lb_filled_length keeps those partials in memory that the
-// context allocated; this entry point keeps them in the file-scope array below
-// instead, so it needs no context and calls no allocator.  Every GPU that loads
-// the library holds the array (LB_NOALLOC_MAX_BLOCKS x 3 doubles) until the
-// process exits.
+// The first reduction pass writes partials per block (mass, sum of phi, filled
+// volume, first meniscus column).  lb_filled_length keeps those partials in
+// memory that the context allocated; this entry point keeps them in the
+// file-scope array below instead, so it needs no context and calls no
+// allocator.  Every GPU that loads the library holds the array
+// (LB_NOALLOC_MAX_BLOCKS x 4 doubles) until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,10 +39,10 @@ lb_status scratch_address(double** out) {
 template <int MODEL, class S>
 cudaError_t reduce(const lbk::Geom& G, const lbk::Buf<S>& B, double rho_l, double rho_g, double thr, int nblocks,
                    double* partials, double* out, cudaStream_t s) {
-  lbk::reduce_partials_kernel<MODEL, S><<<nblocks, lbk::RED_THREADS, 0, s>>>(G, B, rho_l, rho_g, partials);
+  lbk::reduce_partials_kernel<MODEL, S><<<nblocks, lbk::RED_THREADS, 0, s>>>(G, B, rho_l, rho_g, thr, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  lbk::reduce_final_kernel<MODEL, S><<<1, 1024, 0, s>>>(G, B, thr, nblocks, partials, out);
+  lbk::reduce_final_kernel<MODEL, S><<<1, 32, 0, s>>>(G, B, thr, nblocks, partials, out);
   return cudaGetLastError();
 }
 

@@ -129,11 +129,11 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
       pops_in_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.dst), a.in0, a.in1);
       return cudaGetLastError();
     case OP_RED_PARTIALS:
-      reduce_partials_kernel<MODEL, S><<<a.nparts, RED_THREADS, 0, s>>>(G, to_buf<S>(a.src), a.rho_l, a.rho_g,
+      reduce_partials_kernel<MODEL, S><<<a.nparts, RED_THREADS, 0, s>>>(G, to_buf<S>(a.src), a.rho_l, a.rho_g, a.thr,
                                                                         a.partials);
       return cudaGetLastError();
     case OP_RED_FINAL:
-      reduce_final_kernel<MODEL, S><<<1, 1024, 0, s>>>(G, to_buf<S>(a.src), a.thr, a.nparts, a.partials, a.red_out);
+      reduce_final_kernel<MODEL, S><<<1, 32, 0, s>>>(G, to_buf<S>(a.src), a.thr, a.nparts, a.partials, a.red_out);
       return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
