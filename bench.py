@@ -214,6 +214,22 @@ def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
     b.close()
     del b
     torch.cuda.empty_cache()
+    # one launch per run: each capillary alone in the same persistent kernel (a batch of
+    # one, the batch's tile), launched in turn; creation is outside the timed region
+    singles = [Batch([c], storage=storage) for c in caps]
+    for s in singles:
+        s.set_tile(tx, ty)
+        s.run_sampled([2])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in singles:
+        s.run_sampled(at)
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    for s in singles:
+        s.close()
+    del singles
+    torch.cuda.empty_cache()
     t_seq = 0.0
     for c in caps:
         lat = Lattice.from_workload(c, storage=storage)
@@ -229,15 +245,16 @@ def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
         lat.close()
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t_batch, t_seq, float(fluid)], dtype=torch.float64, device="cuda")
+        tt = torch.tensor([t_batch, t_seq, t_one, float(fluid)], dtype=torch.float64, device="cuda")
         mx = tt.clone()
         dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         sm = tt.clone()
         dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        t_batch, t_seq, fluid = float(mx[0]), float(mx[1]), int(sm[2])
+        t_batch, t_seq, t_one, fluid = float(mx[0]), float(mx[1]), float(mx[2]), int(sm[3])
     cs_batch = n * steps / t_batch
     cs_seq = n * steps / t_seq
     return {"capillary_steps_per_s": cs_batch, "sequential_capillary_steps_per_s": cs_seq,
+            "speedup_vs_one_launch_per_run": t_one / t_batch,
             "speedup_vs_one_lattice_per_run": cs_batch / cs_seq,
             "capillaries_per_s_at_20k_steps": cs_batch / 20000.0,
             "sequential_capillaries_per_s_at_20k_steps": cs_seq / 20000.0,
