@@ -55,6 +55,10 @@ GEOMS = {
     # nx % 8 == 0: these run the staged (bulk-copy) kernel; ragged last tile in x and y
     "staged_capillary": lambda p: W.Capillary("sc", 200, 37, 64, 120, 5, 27, 12, 8, p, wall_grad=-0.11),
     "staged_tube_wraps": lambda p: W.Capillary("sw", 144, 30, 104, 90, 27, 20, 0, 0, p, wall_grad=-0.1),
+    # narrower than one warp, and the fewest rows a tube allows (one solid row)
+    "narrow": lambda p: W.Capillary("nw", 20, 12, 6, 10, 2, 7, 2, 3, p, wall_grad=-0.2),
+    "three_rows": lambda p: W.Capillary("tr", 45, 3, 10, 25, 0, 2, 4, 5, p, wall_grad=-0.1),
+    "staged_narrow": lambda p: W.Capillary("sn", 24, 10, 4, 16, 1, 6, 2, 3, p, wall_grad=-0.15),
 }
 
 
