@@ -20,14 +20,14 @@ from typing import Tuple
 import numpy as np
 
 
-def interface_points(phi: np.ndarray, tube_x0: int, tube_len: int, tube_y0: int, tube_h: int
-                     ) -> Tuple[np.ndarray, np.ndarray]:
-    """(x, j) of the phi = 0 crossing in each band row 1 .. H - 2 that has one, with x
-    measured from the tube inlet (x = 0 at column tube_x0)."""
+def interface_points(phi: np.ndarray, tube_x0: int, tube_len: int, tube_y0: int, tube_h: int,
+                     margin: int = 1) -> Tuple[np.ndarray, np.ndarray]:
+    """(x, j) of the phi = 0 crossing in each band row margin .. H - 1 - margin that has
+    one, with x measured from the tube inlet (x = 0 at column tube_x0)."""
     ny, nx = phi.shape
     xs, js = [], []
     cols = (tube_x0 + np.arange(tube_len)) % nx
-    for j in range(1, tube_h - 1):
+    for j in range(margin, tube_h - margin):
         row = phi[(tube_y0 + j) % ny, cols]
         pos = row > 0
         # first liquid -> gas change scanning from the inlet
@@ -49,10 +49,11 @@ def fit_circle(x: np.ndarray, y: np.ndarray) -> Tuple[float, float, float]:
     return float(xc), float(yc), float(math.sqrt(max(xc * xc + yc * yc - F, 0.0)))
 
 
-def contact_angle(phi: np.ndarray, tube_x0: int, tube_len: int, tube_y0: int, tube_h: int) -> float:
-    """Contact angle in degrees from the circular fit of the interface (nan if fewer
-    than three rows have an interface)."""
-    x, j = interface_points(phi, tube_x0, tube_len, tube_y0, tube_h)
+def contact_angle(phi: np.ndarray, tube_x0: int, tube_len: int, tube_y0: int, tube_h: int,
+                  margin: int = 1) -> float:
+    """Contact angle in degrees from the circular fit of the interface rows margin ..
+    H - 1 - margin (nan if fewer than three rows have an interface)."""
+    x, j = interface_points(phi, tube_x0, tube_len, tube_y0, tube_h, margin)
     if len(x) < 3:
         return float("nan")
     if np.ptp(x) <= 1e-9 * max(1.0, float(np.abs(x).max())):

@@ -58,3 +58,12 @@ def test_circle_fit_is_exact_on_a_circle():
     x, y = xc + R * np.cos(t), yc + R * np.sin(t)
     fx, fy, fR = meniscus.fit_circle(x, y)
     assert abs(fx - xc) < 1e-9 and abs(fy - yc) < 1e-9 and abs(fR - R) < 1e-9
+
+
+@pytest.mark.parametrize("margin", [1, 4, 10])
+def test_rows_left_out_next_to_the_walls_do_not_move_an_exact_arc(margin):
+    """The wall planes stay at the boundary-node rows whatever the rows fitted."""
+    phi, geom = synthetic(63.0)
+    assert abs(meniscus.contact_angle(phi, *geom, margin=margin) - 63.0) < 0.1
+    x, j = meniscus.interface_points(phi, *geom, margin=margin)
+    assert j.min() == margin and j.max() == geom[3] - 1 - margin
