@@ -12,7 +12,7 @@ import pytest
 from paper_0911_0459_gb300 import meniscus
 
 
-def synthetic(theta_deg, H=39, nx=300, x0=60, L=230, apex=80.0, jc=None, ny=None):
+def synthetic(theta_deg, H=39, nx=300, x0=60, L=230, apex=80.0, jc=None, ny=None, ramp=False):
     ny = ny or H + 1
     jc = (H - 1) / 2.0 if jc is None else jc
     d = jc   # distance from the centre to the j = 0 wall (the test picks jc so both walls agree)
@@ -30,7 +30,8 @@ def synthetic(theta_deg, H=39, nx=300, x0=60, L=230, apex=80.0, jc=None, ny=None
             else:       # non-wetting: centre on the liquid side, right branch
                 xc = x0 + apex - R
                 xa = xc + math.sqrt(max(R * R - (j - jc) ** 2, 0.0))
-        phi[j] = np.tanh((xa - x) / math.sqrt(2.0))
+        # ramp: a clipped linear profile, on which the interpolated crossing is exact
+        phi[j] = np.clip(xa - x, -3.0, 3.0) if ramp else np.tanh((xa - x) / math.sqrt(2.0))
     return phi, (x0, L, 0, H)
 
 
@@ -62,8 +63,9 @@ def test_circle_fit_is_exact_on_a_circle():
 
 @pytest.mark.parametrize("margin", [1, 4, 10])
 def test_rows_left_out_next_to_the_walls_do_not_move_an_exact_arc(margin):
-    """The wall planes stay at the boundary-node rows whatever the rows fitted."""
-    phi, geom = synthetic(63.0)
-    assert abs(meniscus.contact_angle(phi, *geom, margin=margin) - 63.0) < 0.1
+    """The wall planes stay at the boundary-node rows whatever the rows fitted: with
+    exact interface points the fit of any subset of rows gives the angle exactly."""
+    phi, geom = synthetic(63.0, ramp=True)
+    assert abs(meniscus.contact_angle(phi, *geom, margin=margin) - 63.0) < 1e-6
     x, j = meniscus.interface_points(phi, *geom, margin=margin)
     assert j.min() == margin and j.max() == geom[3] - 1 - margin
