@@ -189,11 +189,11 @@ long lb_fluid_nodes(const lb_ctx *ctx);
 lb_status lb_set_tile(lb_ctx *ctx, int tile_x, int tile_y);
 lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
 
-/* Choose the step kernel: 0 = automatic (the staged kernel whenever nx % 8 ==
- * 0, else the sliding-window kernel), 1 = sliding-window kernel (rows held in
+/* Choose the step kernel: 0 = automatic (the staged kernel whenever it fits,
+ * else the sliding-window kernel), 1 = sliding-window kernel (rows held in
  * registers), 2 = staged kernel (rows brought into shared memory by bulk
- * copies; needs nx % 8 == 0) with its shallow ring of row stages, 3 = staged
- * kernel with its deep ring.  All compute the same update bit for bit.
+ * copies; fits when nx % 8 == 0 and nx * ny <= 477218588, else LB_ERR_ARG)
+ * with its shallow ring of row stages, 3 = staged kernel with its deep ring.  All compute the same update bit for bit.
  * LB_STORAGE_MOMENTS has one kernel of its own (variant 4; 0 and 4 are
  * accepted).  Invalidates the captured step graph. */
 lb_status lb_set_kernel(lb_ctx *ctx, int variant);
@@ -253,10 +253,10 @@ lb_status lb_batch_set_tile(lb_batch *b, int tile_x, int tile_y);
 lb_status lb_batch_autotune(lb_batch *b, int steps, int *tile_x, int *tile_y, double *ms_per_step);
 
 /* Body of the persistent kernel, as lb_set_kernel: 0 = automatic (staged when
- * every lattice has nx % 8 == 0, else sliding-window), 1 = sliding-window body,
- * 2 / 3 = staged body with its shallow / deep ring (bulk copies into a
- * shared-memory ring that runs on across tiles and steps; every nx % 8 == 0,
- * else LB_ERR_ARG).  All give the same result bit for bit.  A batch in
+ * the staged kernel fits every lattice, else sliding-window), 1 = sliding-window
+ * body, 2 / 3 = staged body with its shallow / deep ring (bulk copies into a
+ * shared-memory ring that runs on across tiles and steps; every lattice with
+ * nx % 8 == 0 and nx * ny <= 477218588, else LB_ERR_ARG).  All give the same result bit for bit.  A batch in
  * LB_STORAGE_MOMENTS has one body (4), the single-lattice moment kernel's
  * strips.  get returns the body in use (1, 2, 3 or 4). */
 lb_status lb_batch_set_kernel(lb_batch *b, int variant);

@@ -54,7 +54,7 @@ struct lb_batch {
   int tile_x, tile_y;
   int kernel;      // 0 automatic, 1 sliding-window body, 2 staged body
   int deep;        // staged body: the deeper of its two rings
-  int staged_ok;   // every lattice has nx % 8 == 0
+  int staged_ok;   // every lattice fits the staged body (nx % 8 == 0, 9 nx ny < 2^32)
   int grid_blocks;
   unsigned int extra_arrivals;
   unsigned long long limit_ns;
@@ -504,7 +504,7 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   b->tile_x = 128;
   b->tile_y = 8;
   b->staged_ok = 1;
-  for (int i = 0; i < n; ++i) b->staged_ok = b->staged_ok && grids[i].nx % 8 == 0;
+  for (int i = 0; i < n; ++i) b->staged_ok = b->staged_ok && staged_fits(grids[i].nx, grids[i].ny);
   b->limit_ns = kDefaultLimitNs;
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     berr(NULL, "cudaStreamCreate failed");
@@ -828,7 +828,8 @@ lb_status lb_batch_set_kernel(lb_batch* b, int variant) {
   if (b->storage == LB_STORAGE_MOMENTS)
     return variant == 0 || variant == 4 ? LB_OK : (berr(b, "the moment storage has one body (variant 4)"), LB_ERR_ARG);
   if (variant < 0 || variant > 3) return berr(b, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
-  if (variant >= 2 && !b->staged_ok) return berr(b, "the staged body needs nx %% 8 == 0 in every lattice"), LB_ERR_ARG;
+  if (variant >= 2 && !b->staged_ok)
+    return berr(b, "the staged body needs nx %% 8 == 0 and at most 477218588 nodes in every lattice"), LB_ERR_ARG;
   BCK(cudaStreamSynchronize(b->stream));
   b->kernel = variant == 3 ? 2 : variant;
   if (variant >= 2) b->deep = variant == 3;

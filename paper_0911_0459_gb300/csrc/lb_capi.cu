@@ -133,7 +133,7 @@ static OpArgs base_args(const lb_ctx* c) {
   a.thr = p.model == LB_MODEL_LIQUID_GAS ? 0.5 * (p.rho_l + p.rho_g) : 0.0;
   a.bx = c->tile_x;
   a.yc = c->tile_y;
-  a.staged = c->kernel == 2 || (c->kernel == 0 && c->grid.nx % 8 == 0);
+  a.staged = c->kernel == 2 || (c->kernel == 0 && staged_fits(c->grid.nx, c->grid.ny));
   a.deep = c->deep;
   a.err = c->errflag;
   return a;
@@ -537,7 +537,7 @@ lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
     *variant = 4;
     return LB_OK;
   }
-  const int k = c->kernel == 0 ? (c->grid.nx % 8 == 0 ? 2 : 1) : c->kernel;
+  const int k = c->kernel == 0 ? (staged_fits(c->grid.nx, c->grid.ny) ? 2 : 1) : c->kernel;
   *variant = k == 2 && c->deep ? 3 : k;
   return LB_OK;
 }
@@ -550,6 +550,8 @@ lb_status lb_set_kernel(lb_ctx* c, int variant) {
   if (variant < 0 || variant > 3) return set_err(c, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
   if (variant >= 2 && c->grid.nx % 8 != 0)
     return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
+  if (variant >= 2 && !staged_fits(c->grid.nx, c->grid.ny))
+    return set_err(c, "the staged kernel holds at most 477218588 nodes"), LB_ERR_ARG;
   const int kernel = variant == 3 ? 2 : variant;
   const int deep = variant == 3 ? 1 : (variant == 2 ? 0 : c->deep);
   if (kernel != c->kernel || deep != c->deep) {
@@ -613,9 +615,9 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const int reps = 10, trials = 3;  // each candidate: best of 3 timings of 10 steps
-  // kernel variants: the staged kernel only where rows are 16-byte aligned
-  // variants: sliding window, staged (shallow ring), staged (deep ring)
-  const int nk = moments ? 1 : (c->grid.nx % 8 == 0 ? 3 : 1);
+  // variants: sliding window, staged (shallow ring), staged (deep ring); the staged
+  // kernel only where it fits (16-byte aligned rows, 32-bit offsets)
+  const int nk = moments ? 1 : (staged_fits(c->grid.nx, c->grid.ny) ? 3 : 1);
   for (int ik = 0; ik < nk && e == cudaSuccess && st == LB_OK; ++ik)
   for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
     for (size_t iy = 0; iy < cand_y.size() && e == cudaSuccess && st == LB_OK; ++iy) {

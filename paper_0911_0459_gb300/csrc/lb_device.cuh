@@ -64,6 +64,11 @@ struct SF64 {
   // L2-coherent loads, for buffers written earlier in the same launch
   __device__ static A lfc(const T* f, size_t N, size_t n, int i) { return __ldcg(f + i * N + n); }
   __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
+  // stores at 32-bit element offsets (node n of plane i at i * N + n; needs 9N < 2^32)
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
+    g[i * N + n] = v;
+  }
 };
 
 struct SF32 {
@@ -79,6 +84,10 @@ struct SF32 {
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
   __device__ static A lfc(const T* f, size_t N, size_t n, int i) { return __ldcg(f + i * N + n); }
   __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
+    g[i * N + n] = v;
+  }
 };
 
 struct SF16 {
@@ -106,6 +115,15 @@ struct SF16 {
     return i == 0 ? __ldg(g0 + n) : __half2float(__ldg(g + (i - 1) * N + n));
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__ g0, size_t N, size_t n, int i, A v) {
+    if (i == 0)
+      g0[n] = v;
+    else
+      g[(i - 1) * N + n] = __float2half_rn(v);
+  }
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) {
+    f[i * N + n] = __float2half_rn(v - wstd(i));
+  }
+  __device__ static void sgo(T* __restrict__ g, float* __restrict__ g0, uint32_t N, uint32_t n, int i, A v) {
     if (i == 0)
       g0[n] = v;
     else
@@ -357,6 +375,35 @@ __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int
       const int di = back ? OPPd(i) : i;
       S::sf(dst.f, N, (size_t)dn, di, fs[i]);
       if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, di, ge[i]);
+    }
+  }
+}
+
+// push_node with 32-bit element offsets from the buffer bases (the staged
+// kernels; the host admits them only for lattices with 9 N < 2^32 nodes).
+// rowb/col as in push_node.
+template <int MODEL, class S>
+__device__ __forceinline__ void push_node_u32(const Buf<S>& dst, uint32_t N, const int rowb[3], const int col[3],
+                                              const bool sol[3][3], bool bnd, const typename S::A fs[9],
+                                              const typename S::A ge[9]) {
+  constexpr bool BIN = MODEL == MODEL_BINARY;
+  if (!bnd) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const uint32_t dn = (uint32_t)(rowb[1 + EYd(i)] + col[1 + EXd(i)]);
+      S::sfo(dst.f, N, dn, i, fs[i]);
+      if (BIN) S::sgo(dst.g, dst.g0, N, dn, i, ge[i]);
+    }
+  } else {
+    const uint32_t self = (uint32_t)(rowb[1] + col[1]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int ex = EXd(i), ey = EYd(i);
+      const bool back = sol[1 + ey][1 + ex];
+      const uint32_t dn = back ? self : (uint32_t)(rowb[1 + ey] + col[1 + ex]);
+      const int di = back ? OPPd(i) : i;
+      S::sfo(dst.f, N, dn, di, fs[i]);
+      if (BIN) S::sgo(dst.g, dst.g0, N, dn, di, ge[i]);
     }
   }
 }

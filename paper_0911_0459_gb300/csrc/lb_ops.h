@@ -7,6 +7,12 @@
 
 namespace lbk {
 
+// The staged step kernel reads 16-byte-aligned rows (nx % 8 == 0) and stores at
+// 32-bit element offsets (9 planes of nx * ny nodes below 2^32).
+inline bool staged_fits(int nx, int ny) {
+  return nx % 8 == 0 && 9ull * (unsigned long long)nx * (unsigned long long)ny < (1ull << 32);
+}
+
 enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL, OP_MOMENTS_OUT };
 
 struct OpBufs {

@@ -17,10 +17,13 @@
 //     producer refills a stage once every consumer warp has released it, which
 //     keeps NS - 1 rows in flight;
 //     there is no CTA-wide barrier in the main loop;
-//   - destinations are 32-bit offsets from per-row bases; the wall tests use
-//     column flags computed once per thread and row flags once per row.
-// Requires nx % 8 == 0 (16-byte aligned rows for every storage type) and
-// BX % 32 == 0.  Halo columns at the x-wrap come from a second 16-byte-aligned
+//   - destinations are 32-bit element offsets from the buffer bases; the wall
+//     tests use column flags computed once per thread and row flags once per row;
+//   - a row that is solid under every column a warp reads (inside the tube,
+//     outside the band) is not summed: the wall ghosts replace all its values;
+//     a tile whose nodes are all solid exits at once.
+// Requires nx % 8 == 0 (16-byte aligned rows for every storage type),
+// 9 nx ny < 2^32 (32-bit offsets) and BX % 32 == 0.  Halo columns at the x-wrap come from a second 16-byte-aligned
 // copy of the 8 elements at the other end of the row.
 //
 // Every mbarrier wait gives up after a time limit and records the failure in
@@ -269,7 +272,13 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const bool edge = lane == 0 || lane == 31;
   // Sum this lane's column (f, g keep its populations for the collision); the edge
   // lanes also sum the warp's halo column; then take the neighbours by shuffles.
-  auto sums = [&](int s, A f[9], A g[9], Row& Rw) {
+  // A row solid under all the warp's columns (skip) is left unread.
+  auto sums = [&](int s, A f[9], A g[9], Row& Rw, bool skip) {
+    if (skip) {
+      Rw.rc = Rw.rl = Rw.rr = A(0);
+      Rw.pc = Rw.pl = Rw.pr = A(0);
+      return;
+    }
     load_pop(s, sc, f, g);
     const A r = sum9(f);
     const A p = BIN ? sum9(g) : A(0);
@@ -302,6 +311,11 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   tc[2] = tubed && act && col_in_tube(G, xp);
   const int col[3] = {xm, x, xp};
   const bool warp_tube = __any_sync(0xffffffffu, tc[0] || tc[1] || tc[2]);
+  // every column this warp reads or writes lies in the tube: its rows outside the
+  // band are solid throughout
+  const bool warp_all_tube = __all_sync(0xffffffffu, tc[0] && tc[1] && tc[2]);
+  auto solid_row = [&](int y) { return warp_all_tube && !row_in_band(G, wrapi(y, ny)); };
+  const uint32_t N32 = (uint32_t)N;
 
   // rows k-1, k, k+1 of the stencil window
   Row Rw[3];
@@ -310,7 +324,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   for (int j = 0; j < 2; ++j) {
     const unsigned k = kbase + j;
     if (!__all_sync(0xffffffffu, mbar_wait(&R.full[k % NS], (k / NS) & 1))) return false;
-    sums(k % NS, fa, ga, Rw[j + 1]);
+    sums(k % NS, fa, ga, Rw[j + 1], solid_row(y0 - 1 + j));
     // the populations are in registers now: the stage can be refilled
     __syncwarp();
     if (lane == 0) mbar_arrive(&R.empty[k % NS]);
@@ -324,7 +338,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     Rw[1] = Rw[2];
     if (!__all_sync(0xffffffffu, mbar_wait(&R.full[sn], (kn / NS) & 1))) return false;
     A fn[9], gn[9];
-    sums(sn, fn, gn, Rw[2]);
+    sums(sn, fn, gn, Rw[2], solid_row(y + 1));
     __syncwarp();
     if (lane == 0) mbar_arrive(&R.empty[sn]);
     A vr[3][3], vp[3][3];
@@ -367,7 +381,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       A fs[9], ge[9];
       collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
       const int rowb[3] = {ym * nx, yy * nx, yp * nx};
-      push_node<MODEL, S>(dst, N, rowb, col, sol, bnd, fs, ge);
+      push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, bnd, fs, ge);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -375,6 +389,17 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       if (BIN) ga[i] = gn[i];
     }
   }
+  return true;
+}
+
+// True when every node of columns [xb, xb + w) x rows [y0, y1) is solid.
+__device__ __forceinline__ bool tile_all_solid(const Geom& G, int xb, int w, int y0, int y1) {
+  if (G.tube_len <= 0) return false;
+  int d = xb - G.tube_x0;
+  if (d < 0) d += G.nx;
+  if (d + w > G.tube_len) return false;
+  for (int y = y0; y < y1; ++y)
+    if (row_in_band(G, wrapi(y, G.ny))) return false;
   return true;
 }
 
@@ -391,6 +416,7 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) step_tma_kern
   const int xb = blockIdx.x * BX;
   const int y0 = blockIdx.y * a.yc;
   const int y1 = min(y0 + a.yc, a.G.ny);
+  if (tile_all_solid(a.G, xb, min(BX, a.G.nx - xb), y0, y1)) return;  // CTA-uniform, before any barrier
   if (warp == BX / 32) {
     if (lane != 0) return;
     unsigned issued = 0;
