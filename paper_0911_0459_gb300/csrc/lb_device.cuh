@@ -155,6 +155,14 @@ __device__ __forceinline__ bool is_solid(const Geom& G, int x, int y) {
 }
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// Step launches use a 1-D grid over (column block, row band) tiles, column blocks
+// fastest: a 2-D grid would limit the bands to 65535 (gridDim.y), while the tile
+// count stays below nx * ny < 2^31.  ncb = number of column blocks.
+__device__ __forceinline__ void tile_of_block(int ncb, int& cb, int& band) {
+  band = (int)(blockIdx.x / (unsigned)ncb);
+  cb = (int)blockIdx.x - band * ncb;
+}
+
 // Solid flags of the 3x3 neighbourhood of (x, y), s[j][i] <-> offset (i-1, j-1).
 __device__ __forceinline__ void neighbour_solids(const Geom& G, int x, int y, bool s[3][3], bool& any) {
   bool tc[3], rb[3];
@@ -534,8 +542,10 @@ __device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::
 template <int MODEL, class S, int BX>
 __global__ void __launch_bounds__(BX) step_kernel(StepArgs<MODEL, S> a) {
   __shared__ StepSmem<MODEL, S, BX> sm;
-  const int xb = blockIdx.x * BX;
-  const int y0 = blockIdx.y * a.yc;
+  int cb, band;
+  tile_of_block((a.G.nx + BX - 1) / BX, cb, band);
+  const int xb = cb * BX;
+  const int y0 = band * a.yc;
   const int y1 = min(y0 + a.yc, a.G.ny);
   step_band<MODEL, S, BX>(a.G, a.P, a.src, a.dst, xb, y0, y1, sm);
 }

@@ -485,8 +485,10 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) moment_step_kernel(MomArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int y0 = blockIdx.y * a.yc;
-  moment_strip<false>(a.G, a.P, a.src, a.dst, (blockIdx.x * NW + warp) * kMomCols, y0, min(y0 + a.yc, a.G.ny), lane);
+  int cb, band;
+  tile_of_block((a.G.nx + NW * kMomCols - 1) / (NW * kMomCols), cb, band);
+  const int y0 = band * a.yc;
+  moment_strip<false>(a.G, a.P, a.src, a.dst, (cb * NW + warp) * kMomCols, y0, min(y0 + a.yc, a.G.ny), lane);
 }
 
 }  // namespace lbk

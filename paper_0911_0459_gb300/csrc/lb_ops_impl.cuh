@@ -28,6 +28,11 @@ static Phys<A> to_phys(const OpArgs& a) {
   return p;
 }
 
+// Blocks of a 1-D step grid: column blocks x row bands (see tile_of_block).
+static inline unsigned tiles_1d(int ncb, int ny, int yc) {
+  return (unsigned)ncb * (unsigned)((ny + yc - 1) / yc);
+}
+
 static inline int grid_for(size_t n, int threads) {
   size_t b = (n + threads - 1) / threads;
   return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
@@ -41,7 +46,7 @@ static cudaError_t launch_step(const OpArgs& a, cudaStream_t s) {
   k.src = to_buf<S>(a.src);
   k.dst = to_buf<S>(a.dst);
   k.yc = a.yc;
-  dim3 grid((a.nx + BX - 1) / BX, (a.ny + a.yc - 1) / a.yc);
+  const unsigned grid = tiles_1d((a.nx + BX - 1) / BX, a.ny, a.yc);
   step_kernel<MODEL, S, BX><<<grid, BX, 0, s>>>(k);
   return cudaGetLastError();
 }
@@ -63,7 +68,7 @@ static cudaError_t launch_staged(const OpArgs& a, cudaStream_t s) {
   k.dst = to_buf<S>(a.dst);
   k.yc = a.yc;
   k.err = a.err;
-  dim3 grid((a.nx + BX - 1) / BX, (a.ny + a.yc - 1) / a.yc);
+  const unsigned grid = tiles_1d((a.nx + BX - 1) / BX, a.ny, a.yc);
   step_tma_kernel<MODEL, S, BX, NS><<<grid, BX + 32, L::BYTES, s>>>(k);
   return cudaGetLastError();
 }
@@ -76,7 +81,7 @@ static cudaError_t launch_moment(const OpArgs& a, cudaStream_t s) {
   k.src = (const float*)a.src.f;
   k.dst = (float*)a.dst.f;
   k.yc = a.yc;
-  dim3 grid((a.nx + NW * kMomCols - 1) / (NW * kMomCols), (a.ny + a.yc - 1) / a.yc);
+  const unsigned grid = tiles_1d((a.nx + NW * kMomCols - 1) / (NW * kMomCols), a.ny, a.yc);
   moment_step_kernel<NW><<<grid, NW * 32, 0, s>>>(k);
   return cudaGetLastError();
 }

@@ -413,8 +413,10 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) step_tma_kern
   extern __shared__ __align__(128) unsigned char smem[];
   const Ring<MODEL, S, BX, NS> R = ring_init<MODEL, S, BX, NS>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int xb = blockIdx.x * BX;
-  const int y0 = blockIdx.y * a.yc;
+  int cb, band;
+  tile_of_block((a.G.nx + BX - 1) / BX, cb, band);
+  const int xb = cb * BX;
+  const int y0 = band * a.yc;
   const int y1 = min(y0 + a.yc, a.G.ny);
   if (tile_all_solid(a.G, xb, min(BX, a.G.nx - xb), y0, y1)) return;  // CTA-uniform, before any barrier
   if (warp == BX / 32) {

@@ -23,7 +23,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_0911_0459_gb300 import (Lattice, LbError, STORAGE_F16DEV, STORAGE_F32,  # noqa: E402
-                                   STORAGE_F64)
+                                   STORAGE_F64, STORAGE_MOMENTS)
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
 
 STEP_TOL = {STORAGE_F64: 1e-11, STORAGE_F32: 2e-6, STORAGE_F16DEV: 5e-3}
@@ -91,6 +91,24 @@ def test_one_step_liquid_gas_random_state(geom, storage):
     fo, _ = orc.populations()
     tol = STEP_TOL[storage] * (8 if storage == STORAGE_F32 else 1)   # rho ~ 4: 4x larger ulps
     assert maxdiff(fg, fo) < tol, maxdiff(fg, fo)
+
+
+@pytest.mark.parametrize("storage,variant", [(STORAGE_F32, 1), (STORAGE_F32, 2), (STORAGE_MOMENTS, 0)])
+def test_more_row_bands_than_a_two_dimensional_grid_holds(storage, variant):
+    """A tall periodic box, 8 x 65600, at one-row bands: 65600 bands, more than a grid's
+    y dimension takes (65535).  One step from a random state against the oracle at every
+    node, for the sliding-window, staged and moment kernels."""
+    cap = W.periodic_box(8, 65600, W.binary_params(nu_l=0.4, nu_g=0.05, M=0.2))
+    f = W.random_state_fields(cap.nx, cap.ny, seed=23, model=W.BINARY)
+    lat, orc = pair(cap, storage, f)
+    if variant:
+        lat.set_kernel(variant)
+    lat.set_tile(64, 1)
+    lat.step(1)
+    orc.step(1)
+    g, o = lat.fields(), orc.fields()
+    for k in range(4):
+        assert maxdiff(g[k], o[k]) < 2e-6, (k, maxdiff(g[k], o[k]))
 
 
 def test_default_initial_state_matches_workload_fields():
