@@ -179,3 +179,41 @@ def test_grid_barrier_timeout_is_reported_without_hanging(body):
     b2.step(4)
     assert np.isfinite(b2.lengths()).all()
     b2.close()
+
+
+@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_MOMENTS])
+def test_full_sweep_of_256_capillaries_in_the_benchmarked_configuration(storage):
+    """The seeded sweep at full size (256 capillaries, H 16..128, tubes 1024..8192,
+    about 88 M fluid nodes), autotuned and run through sampled CUDA-graph launches as the
+    benchmark times it.  Six capillaries (the smallest, the largest, four seeded picks)
+    then equal the same capillary run alone bit for bit, with the same l(t) samples, and
+    the smallest one matches the oracle."""
+    caps = W.sweep(seed=0, n=256)
+    b = Batch(caps, storage=storage)
+    b.autotune(steps=2)
+    t0 = b.time
+    at = [10, 20, 30, 40]
+    out = b.run_sampled(at)
+    assert b.time == t0 + 40 and np.isfinite(out).all()
+    sizes = [c.nx * c.ny for c in caps]
+    rng = np.random.default_rng(1)
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), *rng.choice(len(caps), 4, replace=False)})
+    for i in picks:
+        lat = Lattice.from_workload(caps[i], storage=storage)
+        lat.step(t0)
+        for k, n in enumerate(at):
+            lat.step(n - (at[k - 1] if k else 0))
+            assert lat.filled_length()["l"] == out[i, k, 0], (i, k)
+        if storage == STORAGE_MOMENTS:
+            assert np.array_equal(b.moments(i), lat.moments()), i
+        else:
+            fb, gb = b.populations(i, rested=False)
+            fl, gl = lat.populations(rested=False)
+            assert np.array_equal(fb, fl) and np.array_equal(gb, gl), i
+        if i == int(np.argmin(sizes)):
+            orc = oracle.Oracle(caps[i], wall_grad=lat.walls.wall_grad).init_default().step(b.time)
+            g, o = lat.fields(), orc.fields()
+            assert max(np.abs(g[0] - o[0]).max(), np.abs(g[3] - o[3]).max()) < 1e-4
+            assert abs(lat.filled_length()["l"] - orc.filled_length()["l"]) < 0.05
+        lat.close()
+    b.close()
