@@ -340,6 +340,38 @@ def surrogate_metric(torch, threshold=0.02):
             "what": "MLP 4-256-256-64, BF16 tensor cores, 5 members; l(t) at 64 log-spaced times to 20k steps"}
 
 
+def small_capillary_rates(torch, Lattice, steps=10000):
+    """The 2048 x 64 binary FP32 capillary (9.4 MB per state copy, held in L2): the
+    autotuned single-lattice path (replayed 64-step graphs, CUDA events) and one
+    persistent launch of a batch of one (wall clock around the sampled run)."""
+    from paper_0911_0459_gb300 import Batch
+    cap = W.config_binary_2048x64()
+    lat = Lattice.from_workload(cap)
+    tx, ty, _ = lat.autotune()
+    lat.step(64)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(lat.stream)
+    lat.step(steps)
+    b.record(lat.stream)
+    torch.cuda.synchronize()
+    us = 1e3 * a.elapsed_time(b) / steps
+    fluid = lat.fluid_nodes
+    lat.close()
+    bt = Batch([cap])
+    btx, bty, _ = bt.autotune(steps=2)
+    bt.run_sampled([64])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt.run_sampled([steps])
+    us_p = 1e6 * (time.perf_counter() - t0) / steps
+    bt.close()
+    return {"us_per_step": us, "MLUPS": fluid / us, "tile": [tx, ty],
+            "persistent_us_per_step": us_p, "persistent_MLUPS": fluid / us_p, "persistent_tile": [btx, bty],
+            "what": f"{steps} steps; state in L2, so no HBM fraction is quoted"}
+
+
 def timed_steps(lat, torch, K, red_every):
     """K steps with reductions every red_every steps; returns (total_ms, step_ms, launches)."""
     s = lat.stream
@@ -505,6 +537,7 @@ def main():
         torch.cuda.synchronize()
         secondary["lg_256x32_fp64_us_per_step"] = 1e3 * a.elapsed_time(b) / 1984
         l1.close()
+        secondary["binary_2048x64"] = small_capillary_rates(torch, Lattice)
         # the same large capillary with the state held as six FP32 moments per node
         cm = W.config_binary_16384x256(STORAGE_MOMENTS)
         lm = Lattice.from_workload(cm)

@@ -96,3 +96,37 @@ def test_binary_high_viscosity_ratio_dynamic_angle():
         assert early > late[M] + 1.5
         assert abs(late[M] - GOLD["binary_theta_dyn_late"]["value"]) < 6.0
     assert late[0.5] < late[0.1]
+
+
+def test_binary_2048x64_washburn_with_the_gas_column_over_50k_steps():
+    """The 2048 x 64 binary capillary (H = 50, tube L = 1792, nu 0.83 / 0.083, 60 degrees),
+    50 000 steps.  Integrating Washburn's law with the gas column's dissipation (Eq. 3 with
+    eta_g over the gas part of the tube) gives t = a (l_eff^2 + beta l_eff) + c with
+    beta = 2 eta_g (L + H/2) / (eta_l - eta_g) fixed by the viscosities and the geometry:
+    l(t) must follow it, and a must give a dynamic angle a little above 60 degrees."""
+    cap = W.config_binary_2048x64()
+    Hc, L = cap.tube_h, cap.tube_len
+    eta_l, eta_g = cap.params.nu_l, cap.params.nu_g
+    lat = Lattice.from_workload(cap)
+    lat.autotune()
+    ts, ls = [], []
+    while lat.time < 50000:
+        lat.step(1000)
+        ts.append(lat.time)
+        ls.append(lat.filled_length()["l"])
+    ts, ls = np.array(ts, float), np.array(ls)
+    leff = ls + Hc / 2
+    beta = 2 * eta_g * (L + Hc / 2) / (eta_l - eta_g)
+    k = len(ts) // 5   # past the start-up of the flow
+    X = leff[k:] ** 2 + beta * leff[k:]
+    a, c = np.polyfit(X, ts[k:], 1)
+    r2 = 1 - np.sum((ts[k:] - (a * X + c)) ** 2) / np.sum((ts[k:] - ts[k:].mean()) ** 2)
+    theta = math.degrees(math.acos(3 * (eta_l - eta_g) / (GOLD["binary_gamma"]["value"] * (Hc - 1) * a)))
+    # the plain l^2 ~ t form, for the record: the gas column dominates at this ratio
+    m2, c2 = np.polyfit(ts[k:], leff[k:] ** 2, 1)
+    r2_plain = 1 - np.sum((leff[k:] ** 2 - (m2 * ts[k:] + c2)) ** 2) / np.sum((leff[k:] ** 2 - (leff[k:] ** 2).mean()) ** 2)
+    print(f"l: {ls[0]:.1f} -> {ls[-1]:.1f}; Washburn with gas: R^2 {r2:.6f}, theta_dyn {theta:.1f}; "
+          f"plain l_eff^2 ~ t: R^2 {r2_plain:.5f}")
+    assert ls[-1] > ls[0] + 20
+    assert r2 > 0.999
+    assert 60.0 < theta < 75.0
