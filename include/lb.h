@@ -61,8 +61,11 @@ typedef enum {
 typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
 
 /* Storage of the distributions.  Arithmetic is FP64 for LB_STORAGE_F64 and FP32
- * otherwise.  LB_STORAGE_F16DEV keeps f_i - w_i rho0 (w = 4/9, 1/9, 1/36,
- * rho0 = 1) and g_1..g_8 in FP16 and g_0 in FP32.
+ * otherwise.  LB_STORAGE_F16DEV keeps f_i - w_i rho0 and g_1..g_8 in FP16 and
+ * g_0 in FP32, with rho0 = 1 and w_i the rest weights of the binary model's
+ * equilibrium (Eq. (equilibrium), App. A) in the bulk phases, where
+ * P0 = 1/3 + A/4: w_0 = 1 - 5 P0/3, w_1..w_4 = P0/3, w_5..w_8 = P0/12 (the
+ * standard 4/9, 1/9, 1/36 for A = 0).
  *
  * LB_STORAGE_MOMENTS (binary model only) keeps six FP32 numbers per node
  * instead of the populations: rho, jx, jy, pxx - pyy, pxy of f and phi of g.
@@ -289,7 +292,8 @@ const char *lb_batch_last_error(const lb_batch *b);
  * are device pointers to a state in the library's layout for params->storage:
  * plane-major (9, ny, nx) arrays of double (LB_STORAGE_F64) or float
  * (LB_STORAGE_F32); for LB_STORAGE_F16DEV, f holds 9 FP16 planes of
- * f_i - w_i (w = 4/9, 1/9, 1/36), g holds 8 FP16 planes g_1..g_8 and g0 one
+ * f_i - w_i (w_i the rest weights of params->A, as for LB_STORAGE_F16DEV
+ * above), g holds 8 FP16 planes g_1..g_8 and g0 one
  * FP32 plane of g_0.  g is ignored for the liquid-gas model, g0 unless the
  * storage is LB_STORAGE_F16DEV.  out is a device pointer to 4 doubles that
  * receives {l_centre, l_vol, mass, phi_sum} (definitions as in

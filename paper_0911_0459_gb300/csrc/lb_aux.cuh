@@ -36,7 +36,7 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
         mom_store(B.f, N, n, z);
       } else {
         for (int i = 0; i < 9; ++i) {
-          S::sf(B.f, N, n, i, A(0));
+          S::sf(B.f, N, n, i, A(0), B.r);
           if (BIN) S::sg(B.g, B.g0, N, n, i, A(0));
         }
       }
@@ -76,7 +76,7 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
       mom_store(B.f, N, n, m);
     } else {
       for (int i = 0; i < 9; ++i) {
-        S::sf(B.f, N, n, i, fe[i]);
+        S::sf(B.f, N, n, i, fe[i], B.r);
         if (BIN) S::sg(B.g, B.g0, N, n, i, ge[i]);
       }
     }
@@ -169,7 +169,7 @@ __global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, 
       mom_store(B.f, N, n, mf);
     } else {
       for (int i = 0; i < 9; ++i) {
-        S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]));
+        S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]), B.r);
         if (MODEL == MODEL_BINARY) S::sg(B.g, B.g0, N, n, i, sol ? A(0) : A(gi[i * N + n]));
       }
     }

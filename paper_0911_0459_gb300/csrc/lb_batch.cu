@@ -442,6 +442,7 @@ static void fill_caps(lb_batch* b, std::vector<CapDesc<A>>& caps) {
     c.off_f = b->off_f[i];
     c.off_g = b->off_g[i];
     c.off_g0 = b->off_g0[i];
+    c.r = rest_offsets_binary(p.A);
     c.thr = 0.0;
     c.rho_l = p.rho_l;
     c.rho_g = p.rho_g;

@@ -21,6 +21,7 @@ struct CapDesc {
   size_t off_f;     // offset of this lattice's f planes in a buffer's f arena (elements)
   size_t off_g;     // offset of its g planes in the g arena
   size_t off_g0;    // offset of its g_0 plane (FP16 storage)
+  Rest r;           // its FP16 deviation offsets
   double thr, rho_l, rho_g;
 };
 
@@ -88,7 +89,7 @@ struct BatchArgs {
 template <class S>
 __device__ __forceinline__ Buf<S> cap_buf(typename S::T* f, typename S::T* g, float* g0,
                                           const CapDesc<typename S::A>& c) {
-  return Buf<S>{f + c.off_f, g ? g + c.off_g : nullptr, g0 ? g0 + c.off_g0 : nullptr};
+  return Buf<S>{f + c.off_f, g ? g + c.off_g : nullptr, g0 ? g0 + c.off_g0 : nullptr, c.r};
 }
 
 template <class S, int BX>

@@ -44,28 +44,41 @@ struct Phys {
 
 // ------------------------------------------------------------------ storage
 
-// Rest weights of the standard D2Q9 equilibrium, used as the offset of the
-// FP16 deviation storage: f_i is stored as f_i - WSTD_i * rho0 with rho0 = 1.
-__device__ __forceinline__ float wstd(int i) {
-  return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+// Offsets of the FP16 deviation storage: f_i is stored as f_i - w_i rho0 with
+// rho0 = 1 and w_i the rest weights of Eq. (equilibrium) for the bulk phases,
+// i.e. f^eq at rest and without gradients, where P0 = p0(rho0, phi = +-1):
+// w_0 = 1 - 5 P0 / 3, w_1..4 = P0 / 3, w_5..8 = P0 / 12 (the standard 4/9,
+// 1/9, 1/36 when P0 = rho0 / 3).  Unused by the other storages.
+struct Rest {
+  float w0, w1, w5;
+};
+__device__ __forceinline__ float rest_w(const Rest& r, int i) { return i == 0 ? r.w0 : (i < 5 ? r.w1 : r.w5); }
+// Binary model: p0 = rho/3 + A (-phi^2/2 + 3 phi^4/4) = 1/3 + A/4 at rho0 = 1, phi = +-1.
+inline Rest rest_offsets_binary(double A) {
+  const double P0 = 1.0 / 3.0 + 0.25 * A;
+  return Rest{float(1.0 - 5.0 * P0 / 3.0), float(P0 / 3.0), float(P0 / 12.0)};
 }
 
 struct SF64 {
   using T = double;
   using A = double;
-  __device__ static A pf(const T* f, int W, int c, int i) { return f[i * W + c]; }
+  __device__ static A pf(const T* f, int W, int c, int i, const Rest&) { return f[i * W + c]; }
   __device__ static A pg(const T* g, const float*, int W, int c, int i) { return g[i * W + c]; }
-  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) { return __ldg(f + i * N + n); }
-  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
+    return __ldg(f + i * N + n);
+  }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) { f[i * N + n] = v; }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
     return __ldg(g + i * N + n);
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
   // L2-coherent loads, for buffers written earlier in the same launch
-  __device__ static A lfc(const T* f, size_t N, size_t n, int i) { return __ldcg(f + i * N + n); }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) { return __ldcg(f + i * N + n); }
   __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
   // stores at 32-bit element offsets (node n of plane i at i * N + n; needs 9N < 2^32)
-  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
+    f[i * N + n] = v;
+  }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
     g[i * N + n] = v;
   }
@@ -74,17 +87,21 @@ struct SF64 {
 struct SF32 {
   using T = float;
   using A = float;
-  __device__ static A pf(const T* f, int W, int c, int i) { return f[i * W + c]; }
+  __device__ static A pf(const T* f, int W, int c, int i, const Rest&) { return f[i * W + c]; }
   __device__ static A pg(const T* g, const float*, int W, int c, int i) { return g[i * W + c]; }
-  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) { return __ldg(f + i * N + n); }
-  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
+    return __ldg(f + i * N + n);
+  }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) { f[i * N + n] = v; }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
     return __ldg(g + i * N + n);
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
-  __device__ static A lfc(const T* f, size_t N, size_t n, int i) { return __ldcg(f + i * N + n); }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) { return __ldcg(f + i * N + n); }
   __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
-  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) { f[i * N + n] = v; }
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
+    f[i * N + n] = v;
+  }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
     g[i * N + n] = v;
   }
@@ -94,18 +111,20 @@ struct SF16 {
   using T = __half;
   using A = float;
   // plain loads (shared memory): planes of W elements
-  __device__ static A pf(const T* f, int W, int c, int i) { return __half2float(f[i * W + c]) + wstd(i); }
+  __device__ static A pf(const T* f, int W, int c, int i, const Rest& r) {
+    return __half2float(f[i * W + c]) + rest_w(r, i);
+  }
   __device__ static A pg(const T* g, const float* g0, int W, int c, int i) {
     return i == 0 ? g0[c] : __half2float(g[(i - 1) * W + c]);
   }
-  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i) {
-    return __half2float(__ldg(f + i * N + n)) + wstd(i);
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest& r) {
+    return __half2float(__ldg(f + i * N + n)) + rest_w(r, i);
   }
-  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v) {
-    f[i * N + n] = __float2half_rn(v - wstd(i));
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest& r) {
+    f[i * N + n] = __float2half_rn(v - rest_w(r, i));
   }
-  __device__ static A lfc(const T* f, size_t N, size_t n, int i) {
-    return __half2float(__ldcg(f + i * N + n)) + wstd(i);
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest& r) {
+    return __half2float(__ldcg(f + i * N + n)) + rest_w(r, i);
   }
   __device__ static A lgc(const T* g, const float* g0, size_t N, size_t n, int i) {
     return i == 0 ? __ldcg(g0 + n) : __half2float(__ldcg(g + (i - 1) * N + n));
@@ -120,8 +139,8 @@ struct SF16 {
     else
       g[(i - 1) * N + n] = __float2half_rn(v);
   }
-  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) {
-    f[i * N + n] = __float2half_rn(v - wstd(i));
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest& r) {
+    f[i * N + n] = __float2half_rn(v - rest_w(r, i));
   }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__ g0, uint32_t N, uint32_t n, int i, A v) {
     if (i == 0)
@@ -136,6 +155,7 @@ struct Buf {
   typename S::T* f;
   typename S::T* g;
   float* g0;
+  Rest r;  // FP16 deviation offsets of this lattice
 };
 
 // ----------------------------------------------------------------- geometry
@@ -370,7 +390,7 @@ __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int dn = rowb[1 + EYd(i)] + col[1 + EXd(i)];
-      S::sf(dst.f, N, (size_t)dn, i, fs[i]);
+      S::sf(dst.f, N, (size_t)dn, i, fs[i], dst.r);
       if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, i, ge[i]);
     }
   } else {
@@ -381,7 +401,7 @@ __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int
       const bool back = sol[1 + ey][1 + ex];
       const int dn = back ? self : rowb[1 + ey] + col[1 + ex];
       const int di = back ? OPPd(i) : i;
-      S::sf(dst.f, N, (size_t)dn, di, fs[i]);
+      S::sf(dst.f, N, (size_t)dn, di, fs[i], dst.r);
       if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, di, ge[i]);
     }
   }
@@ -399,7 +419,7 @@ __device__ __forceinline__ void push_node_u32(const Buf<S>& dst, uint32_t N, con
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const uint32_t dn = (uint32_t)(rowb[1 + EYd(i)] + col[1 + EXd(i)]);
-      S::sfo(dst.f, N, dn, i, fs[i]);
+      S::sfo(dst.f, N, dn, i, fs[i], dst.r);
       if (BIN) S::sgo(dst.g, dst.g0, N, dn, i, ge[i]);
     }
   } else {
@@ -410,7 +430,7 @@ __device__ __forceinline__ void push_node_u32(const Buf<S>& dst, uint32_t N, con
       const bool back = sol[1 + ey][1 + ex];
       const uint32_t dn = back ? self : (uint32_t)(rowb[1 + ey] + col[1 + ex]);
       const int di = back ? OPPd(i) : i;
-      S::sfo(dst.f, N, dn, di, fs[i]);
+      S::sfo(dst.f, N, dn, di, fs[i], dst.r);
       if (BIN) S::sgo(dst.g, dst.g0, N, dn, di, ge[i]);
     }
   }
@@ -436,7 +456,7 @@ template <int MODEL, class S, bool COHERENT = false>
 __device__ __forceinline__ void load_node(const Buf<S>& B, size_t N, size_t n, typename S::A f[9],
                                           typename S::A g[9]) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = COHERENT ? S::lfc(B.f, N, n, i) : S::lf(B.f, N, n, i);
+  for (int i = 0; i < 9; ++i) f[i] = COHERENT ? S::lfc(B.f, N, n, i, B.r) : S::lf(B.f, N, n, i, B.r);
   if (MODEL == MODEL_BINARY) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = COHERENT ? S::lgc(B.g, B.g0, N, n, i) : S::lg(B.g, B.g0, N, n, i);

@@ -89,7 +89,8 @@ extern "C" lb_status lb_filled_length_noalloc(const lb_grid* grid, const lb_wall
     lbk::Buf<lbk::SF32> B{(float*)f, (float*)g, nullptr};
     e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
   } else if (bin && params->storage == LB_STORAGE_F16DEV) {
-    lbk::Buf<lbk::SF16> B{(__half*)f, (__half*)g, g0f};
+    // the stored deviations are taken from the bulk rest weights of this lattice's A
+    lbk::Buf<lbk::SF16> B{(__half*)f, (__half*)g, g0f, lbk::rest_offsets_binary(params->A)};
     e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
   } else {
     return LB_ERR_ARG;

@@ -9,8 +9,8 @@
 namespace lbk {
 
 template <class S>
-static Buf<S> to_buf(const OpBufs& b) {
-  return Buf<S>{(typename S::T*)b.f, (typename S::T*)b.g, b.g0};
+static Buf<S> to_buf(const OpBufs& b, const OpArgs& a) {
+  return Buf<S>{(typename S::T*)b.f, (typename S::T*)b.g, b.g0, rest_offsets_binary(a.Acoef)};
 }
 
 static inline Geom to_geom(const OpArgs& a) {
@@ -43,8 +43,8 @@ static cudaError_t launch_step(const OpArgs& a, cudaStream_t s) {
   StepArgs<MODEL, S> k;
   k.G = to_geom(a);
   k.P = to_phys<typename S::A>(a);
-  k.src = to_buf<S>(a.src);
-  k.dst = to_buf<S>(a.dst);
+  k.src = to_buf<S>(a.src, a);
+  k.dst = to_buf<S>(a.dst, a);
   k.yc = a.yc;
   const unsigned grid = tiles_1d((a.nx + BX - 1) / BX, a.ny, a.yc);
   step_kernel<MODEL, S, BX><<<grid, BX, 0, s>>>(k);
@@ -64,8 +64,8 @@ static cudaError_t launch_staged(const OpArgs& a, cudaStream_t s) {
   TmaArgs<MODEL, S> k;
   k.G = to_geom(a);
   k.P = to_phys<typename S::A>(a);
-  k.src = to_buf<S>(a.src);
-  k.dst = to_buf<S>(a.dst);
+  k.src = to_buf<S>(a.src, a);
+  k.dst = to_buf<S>(a.dst, a);
   k.yc = a.yc;
   k.err = a.err;
   const unsigned grid = tiles_1d((a.nx + BX - 1) / BX, a.ny, a.yc);
@@ -117,28 +117,28 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
       }
       return cudaErrorInvalidValue;
     case OP_INIT:
-      init_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_phys<A>(a), to_buf<S>(a.dst), a.in0, a.in1,
+      init_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_phys<A>(a), to_buf<S>(a.dst, a), a.in0, a.in1,
                                                               a.in2, a.in3);
       return cudaGetLastError();
     case OP_FIELDS:
-      fields_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.out0, a.out1, a.out2, a.out3);
+      fields_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src, a), a.out0, a.out1, a.out2, a.out3);
       return cudaGetLastError();
     case OP_POPS_OUT:
       if constexpr (!is_moments<S>::value)
-        pops_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.flag, a.out0, a.out1);
+        pops_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src, a), a.flag, a.out0, a.out1);
       return cudaGetLastError();
     case OP_MOMENTS_OUT:
-      moments_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src), a.out0);
+      moments_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src, a), a.out0);
       return cudaGetLastError();
     case OP_POPS_IN:
-      pops_in_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.dst), a.in0, a.in1);
+      pops_in_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.dst, a), a.in0, a.in1);
       return cudaGetLastError();
     case OP_RED_PARTIALS:
-      reduce_partials_kernel<MODEL, S><<<a.nparts, RED_THREADS, 0, s>>>(G, to_buf<S>(a.src), a.rho_l, a.rho_g, a.thr,
+      reduce_partials_kernel<MODEL, S><<<a.nparts, RED_THREADS, 0, s>>>(G, to_buf<S>(a.src, a), a.rho_l, a.rho_g, a.thr,
                                                                         a.partials);
       return cudaGetLastError();
     case OP_RED_FINAL:
-      reduce_final_kernel<MODEL, S><<<1, 32, 0, s>>>(G, to_buf<S>(a.src), a.thr, a.nparts, a.partials, a.red_out);
+      reduce_final_kernel<MODEL, S><<<1, 32, 0, s>>>(G, to_buf<S>(a.src, a), a.thr, a.nparts, a.partials, a.red_out);
       return cudaGetLastError();
   }
   return cudaErrorInvalidValue;

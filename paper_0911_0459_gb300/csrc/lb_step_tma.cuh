@@ -256,7 +256,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
 
   auto load_pop = [&](int s, int c, A f[9], A g[9]) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = S::pf(R.f(s), W, c, i);
+    for (int i = 0; i < 9; ++i) f[i] = S::pf(R.f(s), W, c, i, dst.r);  // the stage holds this lattice
     if (BIN) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = S::pg(R.g(s), R.g0(s), W, c, i);

@@ -1,4 +1,6 @@
 """Batched persistent kernel against independent lattices and the oracle (needs a GPU)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -16,9 +18,9 @@ from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STO
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
 
 
-def small_sweep(seed=7, n=6, align=8):
+def small_sweep(seed=7, n=6, align=8, vary_gamma=False):
     """Uneven capillaries shaped like the sweep, shortened so the oracle keeps up."""
-    caps = W.sweep(seed=seed, n=n, lengths=(96, 300), align=align)
+    caps = W.sweep(seed=seed, n=n, lengths=(96, 300), align=align, vary_gamma=vary_gamma)
     out = []
     for c in caps:
         c.nx = c.tube_x0 + c.tube_len   # keep the reservoirs, short tubes
@@ -54,6 +56,24 @@ def test_batch_is_bitwise_identical_to_independent_lattices(storage, body):
         assert red[i, 0] == d["l"], i
         np.testing.assert_allclose(red[i, 1:], [d["l_vol"], d["mass"], d["phi_sum"]], rtol=1e-12,
                                    atol=1e-12 * c.nodes)
+        lat.close()
+    b.close()
+
+
+def test_fp16_batch_with_a_different_free_energy_per_lattice():
+    """FP16 deviations are taken from each lattice's own bulk rest weights (they depend on
+    A): a sweep with A = kappa drawn per capillary evolves bit for bit as each alone."""
+    caps = small_sweep(seed=8, n=5, vary_gamma=True)
+    assert len({c.params.A for c in caps}) == len(caps)
+    caps = [dataclasses.replace(c, params=dataclasses.replace(c.params, storage=STORAGE_F16DEV)) for c in caps]
+    b = Batch(caps)
+    b.step(37)
+    for i, c in enumerate(caps):
+        lat = Lattice.from_workload(c)
+        lat.step(37)
+        fb, gb = b.populations(i, rested=False)
+        fl, gl = lat.populations(rested=False)
+        assert np.array_equal(fb, fl) and np.array_equal(gb, gl), i
         lat.close()
     b.close()
 

@@ -5,8 +5,10 @@ Tolerances (per node, absolute):
                   different summation order and collision formulation);
   FP32 storage  : 2e-6 after one step; the method's bar of 1e-4 for rho and phi
                   after 2000 steps and 0.05 lattice units for l(t);
-  FP16 deviation: reported, with a loose bound (5e-3 per step-state), since FP16
-                  keeps ~11 bits of each stored deviation.
+  FP16 deviation: 1e-4 after one step (FP16 keeps ~11 bits of each stored
+                  deviation from the bulk rest populations, which are below
+                  ~2e-2); after 2000 steps 2e-3 for rho and phi and the method's
+                  0.05 lattice units for l(t).
 """
 import math
 
@@ -26,7 +28,7 @@ from paper_0911_0459_gb300 import (Lattice, LbError, STORAGE_F16DEV, STORAGE_F32
                                    STORAGE_F64, STORAGE_MOMENTS)
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
 
-STEP_TOL = {STORAGE_F64: 1e-11, STORAGE_F32: 2e-6, STORAGE_F16DEV: 5e-3}
+STEP_TOL = {STORAGE_F64: 1e-11, STORAGE_F32: 2e-6, STORAGE_F16DEV: 1e-4}
 
 
 def pair(cap, storage=None, fields=None):
@@ -185,8 +187,9 @@ def test_fp16_deviation_storage_error_is_bounded():
     r_rho, _, _, r_phi = orc.fields()
     err = max(maxdiff(rho, r_rho), maxdiff(phi, r_phi))
     print(f"FP16-deviation storage: max |d rho|, |d phi| after 2000 steps = {err:.3e}")
-    assert err < 5e-2
-    assert abs(ls[-1][0]["l"] - ls[-1][1]["l"]) < 0.5
+    assert err < 2e-3
+    for g, o in ls:
+        assert abs(g["l"] - o["l"]) < 0.05
 
 
 @pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F16DEV])
@@ -206,7 +209,7 @@ def test_full_size_16384x256_one_step_from_gpu_state(storage):
     orc.step(1)
     fg, gg = lat.populations(rested=True)
     fo, go = orc.populations()
-    tol = 2e-6 if storage == STORAGE_F32 else 2e-3
+    tol = 2e-6 if storage == STORAGE_F32 else 1e-4
     assert maxdiff(fg, fo) < tol and maxdiff(gg, go) < tol
     d, do = lat.filled_length(), orc.filled_length()
     # total mass over 3.3 M nodes: FP32 (FP16) rounding of each node's populations

@@ -89,3 +89,32 @@ def test_noalloc_matches_filled_length_on_two_calls_in_a_row():
     assert call(a, fa, ga, 0, out) == lbmod.LB_ERR_ARG
     a.close()
     b.close()
+
+
+def test_noalloc_reads_the_fp16_deviation_layout():
+    """A caller-owned state in the FP16 layout the header documents: f_i - w_i rho0 in FP16
+    with the bulk rest weights of the lattice's A (P0 = 1/3 + A/4), g_1..g_8 in FP16, g_0 in
+    FP32.  The state is the lattice's own, rebuilt from its populations."""
+    from paper_0911_0459_gb300 import STORAGE_F16DEV
+    cap = W.Capillary("nh", 300, 36, 60, 230, 4, 28, 20, 10,
+                      W.binary_params(nu_l=0.5, nu_g=0.05, A=0.035, kappa=0.035, storage=STORAGE_F16DEV),
+                      theta_deg=50.0)
+    lat = Lattice.from_workload(cap)
+    lat.step(120)
+    f, g = lat.populations(rested=False)
+    P0 = 1.0 / 3.0 + 0.25 * cap.params.A
+    w = np.array([1 - 5 * P0 / 3] + [P0 / 3] * 4 + [P0 / 12] * 4, dtype=np.float32)
+    dev = (f.astype(np.float32) - w[:, None, None]).astype(np.float16)
+    fd = torch.tensor(dev, device="cuda").contiguous()
+    gd = torch.tensor(g[1:].astype(np.float16), device="cuda").contiguous()
+    g0d = torch.tensor(g[0].astype(np.float32), device="cuda").contiguous()
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    fn = noalloc_fn()
+    st = fn(C.byref(lat.grid), C.byref(lat.walls), C.byref(lat.params), C.c_void_p(fd.data_ptr()),
+            C.c_void_p(gd.data_ptr()), C.c_void_p(g0d.data_ptr()), 64, C.c_void_p(out.data_ptr()),
+            C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == lbmod.LB_OK
+    torch.cuda.synchronize()
+    ref = lat.filled_length()
+    for k, v in zip(("l", "l_vol", "mass", "phi_sum"), out.cpu().numpy()):
+        assert abs(v - ref[k]) <= 1e-9 * max(1.0, abs(ref[k])), (k, v, ref[k])
