@@ -10,21 +10,25 @@ namespace lbk {
 
 // Gather the 3x3 neighbourhood of a double field around fluid node (x, y).
 template <typename A>
-__device__ __forceinline__ void gather_field(const Geom& G, const double* __restrict__ v, int x, int y, A out[3][3]) {
+// 3x3 neighbourhood of a field with row stride sy (nx: a full field; 0: one value per
+// column); solid nodes read as 0 (the wall ghosts replace them).
+__device__ __forceinline__ void gather_field(const Geom& G, const double* __restrict__ v, size_t sy, int x, int y,
+                                             A out[3][3]) {
 #pragma unroll
   for (int j = 0; j < 3; ++j)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int xx = wrapi(x + i - 1, G.nx), yy = wrapi(y + j - 1, G.ny);
-      out[j][i] = is_solid(G, xx, yy) ? A(0) : A(v[(size_t)yy * G.nx + xx]);
+      out[j][i] = is_solid(G, xx, yy) ? A(0) : A(v[(size_t)yy * sy + xx]);
     }
 }
 
-// f = f^eq and g = g^eq of the given fields (stencils with the wall ghosts).
+// f = f^eq and g = g^eq of the given fields (stencils with the wall ghosts); the
+// fields have row stride sy (nx, or 0 for fields given as one value per column).
 template <int MODEL, class S>
 __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const double* __restrict__ rho_in,
                             const double* __restrict__ ux_in, const double* __restrict__ uy_in,
-                            const double* __restrict__ phi_in) {
+                            const double* __restrict__ phi_in, size_t sy) {
   using A = typename S::A;
   constexpr bool BIN = MODEL == MODEL_BINARY;
   const size_t N = (size_t)G.nx * G.ny;
@@ -45,15 +49,16 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
     bool sol[3][3], bnd;
     neighbour_solids(G, x, y, sol, bnd);
     A vr[3][3], vp[3][3];
-    gather_field(G, rho_in, x, y, vr);
-    if (BIN) gather_field(G, phi_in, x, y, vp);
+    gather_field(G, rho_in, sy, x, y, vr);
+    if (BIN) gather_field(G, phi_in, sy, x, y, vp);
     if (bnd) {
       apply_ghosts(vr, sol, BIN ? A(0) : P.h);
       if (BIN) apply_ghosts(vp, sol, P.h);
     }
     A rdx, rdy, rlap;
     stencil3(vr, rdx, rdy, rlap);
-    const A rho = vr[1][1], ux = A(ux_in[n]), uy = A(uy_in[n]);
+    const size_t nin = (size_t)y * sy + x;
+    const A rho = vr[1][1], ux = A(ux_in[nin]), uy = A(uy_in[nin]);
     const A jx = rho * ux, jy = rho * uy;
     A fe[9], ge[9];
     if (BIN) {
@@ -72,7 +77,7 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
     if constexpr (is_moments<S>::value) {
       A m[M_PLANES];
       pops_to_moments(fe, ge, m);
-      m[M_RHO] = (A)(rho_in[n] - 1.0);  // stored as rho - 1
+      m[M_RHO] = (A)(rho_in[nin] - 1.0);  // stored as rho - 1
       mom_store(B.f, N, n, m);
     } else {
       for (int i = 0; i < 9; ++i) {

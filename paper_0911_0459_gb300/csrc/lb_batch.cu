@@ -151,18 +151,17 @@ static lb_status init_lattice(lb_batch* b, int i) {
   const lb_grid& g = b->grids[i];
   const lb_walls& w = b->walls[i];
   const lb_params& p = b->params[i];
-  const size_t N = (size_t)g.nx * g.ny;
+  // the initial state as for lb_create: at rest, tanh profiles along x, one value per
+  // column (the init kernel takes no input at solid nodes)
+  const size_t N = (size_t)g.nx;
   std::vector<double> host(4 * N, 0.0);
   const double wdt = sqrt(2.0);
   const double xa = w.gas_cols, xb = (double)w.tube_x0 + p.l0;
-  for (int y = 0; y < g.ny; ++y)
-    for (int x = 0; x < g.nx; ++x) {
-      const size_t n = (size_t)y * g.nx + x;
-      const double chi = 0.5 * (tanh((x - xa) / wdt) - tanh((x - xb) / wdt));
-      const int sol = solid_h(g, w, x, y);
-      host[n] = sol ? 0.0 : 1.0;
-      host[3 * N + n] = sol ? 0.0 : 2.0 * chi - 1.0;
-    }
+  for (int x = 0; x < g.nx; ++x) {
+    const double chi = 0.5 * (tanh((x - xa) / wdt) - tanh((x - xb) / wdt));
+    host[x] = 1.0;
+    host[3 * N + x] = 2.0 * chi - 1.0;
+  }
   double* d = NULL;
   if (b->have_alloc)
     d = (double*)b->alloc.malloc_fn(4 * N * sizeof(double), (void*)b->stream, b->alloc.user);
@@ -172,6 +171,7 @@ static lb_status init_lattice(lb_batch* b, int i) {
   cudaError_t e = cudaMemcpyAsync(d, host.data(), 4 * N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
   OpArgs a = lattice_args(b, i, 0);
   a.in0 = d; a.in1 = d + N; a.in2 = d + 2 * N; a.in3 = d + 3 * N;
+  a.in_cols = 1;
   if (e == cudaSuccess) e = batch_ops(b->storage)(OP_INIT, a, b->stream);
   cudaError_t e2 = cudaStreamSynchronize(b->stream);
   if (b->have_alloc)
@@ -212,8 +212,7 @@ static cudaError_t run_sliding(lb_batch* b, int nsteps, cudaStream_t s, int* per
   if (per) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_step_kernel<S, BX>, BX, 0);
   BatchArgs<S> a;
   fill_args(b, nsteps, a);
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid_blocks);
   cfg.blockDim = dim3(BX);
   cfg.stream = s;
@@ -238,8 +237,7 @@ static cudaError_t run_staged(lb_batch* b, int nsteps, cudaStream_t s, int* per)
   if (per) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_tma_kernel<S, BX, NS>, BX + 32, L::BYTES);
   BatchArgs<S> a;
   fill_args(b, nsteps, a);
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid_blocks);
   cfg.blockDim = dim3(BX + 32);
   cfg.dynamicSmemBytes = L::BYTES;
@@ -257,8 +255,7 @@ static cudaError_t run_moment(lb_batch* b, int nsteps, cudaStream_t s, int* per)
   if (per) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_moment_kernel<NW>, NW * 32, 0);
   BatchArgs<SM32> a;
   fill_args(b, nsteps, a);
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid_blocks);
   cfg.blockDim = dim3(NW * 32);
   cfg.stream = s;
@@ -525,10 +522,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
     of += (nf * N + 63) / 64 * 64;
     og += (ng * N + 63) / 64 * 64;
     o0 += (N + 63) / 64 * 64;
-    long fl = 0;
-    for (int y = 0; y < grids[i].ny; ++y)
-      for (int x = 0; x < grids[i].nx; ++x) fl += !solid_h(grids[i], walls[i], x, y);
-    b->fluid.push_back(fl);
+    // solid nodes: the tube's columns outside its band
+    b->fluid.push_back((long)N - (walls[i].tube_len > 0 ? (long)walls[i].tube_len * (grids[i].ny - walls[i].tube_h) : 0));
   }
   for (int k = 0; k < 2; ++k) {
     b->f[k] = balloc(b, of * el);

@@ -107,14 +107,6 @@ static OpsFn pick_ops(int model, int storage) {
   return NULL;
 }
 
-static int is_solid_h(const lb_ctx* c, int x, int y) {
-  const lb_walls& w = c->walls;
-  if (w.tube_len <= 0) return 0;
-  int dx = ((x - w.tube_x0) % c->grid.nx + c->grid.nx) % c->grid.nx;
-  int dy = ((y - w.tube_y0) % c->grid.ny + c->grid.ny) % c->grid.ny;
-  return dx < w.tube_len && dy >= w.tube_h;
-}
-
 static OpArgs base_args(const lb_ctx* c) {
   OpArgs a;
   memset(&a, 0, sizeof a);
@@ -225,9 +217,10 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
   return LB_OK;
 }
 
+// cols: the four fields are given as one value per column (every row alike)
 static lb_status upload_and_init(lb_ctx* c, const double* rho, const double* ux, const double* uy,
-                                 const double* phi) {
-  const size_t N = (size_t)c->grid.nx * c->grid.ny;
+                                 const double* phi, bool cols = false) {
+  const size_t N = cols ? (size_t)c->grid.nx : (size_t)c->grid.nx * c->grid.ny;
   double* d = (double*)dev_alloc(c, 4 * N * sizeof(double));
   if (!d) return set_err(c, "device allocation of %zu bytes failed", 4 * N * sizeof(double)), LB_ERR_NOMEM;
   lb_status st = LB_OK;
@@ -247,6 +240,7 @@ static lb_status upload_and_init(lb_ctx* c, const double* rho, const double* ux,
     a.in1 = d + N;
     a.in2 = d + 2 * N;
     a.in3 = d + 3 * N;
+    a.in_cols = cols;
     cudaError_t e = c->ops(OP_INIT, a, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -264,27 +258,25 @@ static lb_status upload_and_init(lb_ctx* c, const double* rho, const double* ux,
   return st;
 }
 
+// The initial state of Sec. 2.2 / 3.2: at rest, with tanh profiles along x (so one
+// value per column; solid nodes take no input values, the init kernel zeroes them).
 static lb_status default_state(lb_ctx* c) {
-  const int nx = c->grid.nx, ny = c->grid.ny;
-  const size_t N = (size_t)nx * ny;
-  std::vector<double> rho(N), z(N, 0.0), phi(N);
+  const int nx = c->grid.nx;
+  std::vector<double> rho(nx), z(nx, 0.0), phi(nx);
   const lb_params& p = c->prm;
   const double wdt = p.model == LB_MODEL_LIQUID_GAS ? 2.0 : sqrt(2.0);
   const double xa = c->walls.gas_cols, xb = (double)c->walls.tube_x0 + p.l0;
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x) {
-      const double chi = 0.5 * (tanh((x - xa) / wdt) - tanh((x - xb) / wdt));
-      const size_t n = (size_t)y * nx + x;
-      const int sol = is_solid_h(c, x, y);
-      if (p.model == LB_MODEL_LIQUID_GAS) {
-        rho[n] = sol ? 0.0 : p.rho_g + (p.rho_l - p.rho_g) * chi;
-        phi[n] = 0.0;
-      } else {
-        rho[n] = sol ? 0.0 : 1.0;
-        phi[n] = sol ? 0.0 : 2.0 * chi - 1.0;
-      }
+  for (int x = 0; x < nx; ++x) {
+    const double chi = 0.5 * (tanh((x - xa) / wdt) - tanh((x - xb) / wdt));
+    if (p.model == LB_MODEL_LIQUID_GAS) {
+      rho[x] = p.rho_g + (p.rho_l - p.rho_g) * chi;
+      phi[x] = 0.0;
+    } else {
+      rho[x] = 1.0;
+      phi[x] = 2.0 * chi - 1.0;
     }
-  return upload_and_init(c, rho.data(), z.data(), z.data(), phi.data());
+  }
+  return upload_and_init(c, rho.data(), z.data(), z.data(), phi.data(), true);
 }
 
 extern "C" {
@@ -346,10 +338,8 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
     lb_destroy(c);
     return LB_ERR_NOMEM;
   }
-  long fluid = 0;
-  for (int y = 0; y < grid->ny; ++y)
-    for (int x = 0; x < grid->nx; ++x) fluid += !is_solid_h(c, x, y);
-  c->fluid = fluid;
+  // solid nodes: the tube's columns outside its band
+  c->fluid = (long)grid->nx * grid->ny - (walls->tube_len > 0 ? (long)walls->tube_len * (grid->ny - walls->tube_h) : 0);
   st = default_state(c);
   if (st != LB_OK) {
     snprintf(g_create_err, sizeof g_create_err, "%s", c->err);

@@ -37,6 +37,7 @@ struct OpArgs {
   int* err;      // device error word (a device-side wait gave up)
   // field / population / reduction arguments (device pointers)
   const double *in0, *in1, *in2, *in3;
+  int in_cols;   // OP_INIT: in0..in3 hold one value per column (every row alike)
   double *out0, *out1, *out2, *out3;  // OP_MOMENTS_OUT: out0 holds 6 planes
   int flag;      // rested flag for OP_POPS_OUT
   int nparts;    // reduction partial blocks

@@ -118,7 +118,7 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
       return cudaErrorInvalidValue;
     case OP_INIT:
       init_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_phys<A>(a), to_buf<S>(a.dst, a), a.in0, a.in1,
-                                                              a.in2, a.in3);
+                                                              a.in2, a.in3, a.in_cols ? size_t(0) : size_t(a.nx));
       return cudaGetLastError();
     case OP_FIELDS:
       fields_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src, a), a.out0, a.out1, a.out2, a.out3);
