@@ -473,12 +473,19 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   if (!out || n < 1 || !grids || !walls || !params) return berr(NULL, "invalid arguments"), LB_ERR_ARG;
   *out = NULL;
   const int storage = params[0].storage;
+  if (storage != LB_STORAGE_F64 && storage != LB_STORAGE_F32 && storage != LB_STORAGE_F16DEV &&
+      storage != LB_STORAGE_MOMENTS)
+    return berr(NULL, "unknown storage %d", storage), LB_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (params[i].model != LB_MODEL_BINARY) return berr(NULL, "batches hold binary lattices"), LB_ERR_ARG;
     if (params[i].storage != storage) return berr(NULL, "all lattices of a batch share one storage"), LB_ERR_ARG;
     const lb_grid& g = grids[i];
     const lb_walls& w = walls[i];
     if (g.nx < 3 || g.ny < 3 || (long)g.nx * g.ny > (1L << 31) - 1) return berr(NULL, "lattice %d: bad grid", i), LB_ERR_ARG;
+    if (storage == LB_STORAGE_MOMENTS && (unsigned long long)M_PLANES * g.nx * g.ny >= (1ull << 32))
+      return berr(NULL, "lattice %d: the moment storage holds at most 715827882 nodes", i), LB_ERR_ARG;
+    if (!isfinite(w.wall_grad)) return berr(NULL, "lattice %d: wall_grad not finite", i), LB_ERR_ARG;
+    if (!(params[i].M >= 0)) return berr(NULL, "lattice %d: mobility must be >= 0", i), LB_ERR_ARG;
     if (w.tube_len < 0 || w.tube_len > g.nx) return berr(NULL, "lattice %d: tube_len outside [0, nx]", i), LB_ERR_ARG;
     if (w.tube_len > 0 && (w.tube_x0 < 0 || w.tube_x0 >= g.nx || w.tube_y0 < 0 || w.tube_y0 >= g.ny ||
                            w.tube_h < 2 || w.tube_h >= g.ny || (w.tube_len < g.nx && g.nx - w.tube_len < 2)))

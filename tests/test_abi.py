@@ -84,3 +84,85 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(lb, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         lb.library()
+
+
+def _create_status(lib, grid, walls, params):
+    ctx = ctypes.c_void_p()
+    st = lib.lb_create(ctypes.byref(grid), ctypes.byref(walls), ctypes.byref(params), None, None, ctypes.byref(ctx))
+    return st, ctx.value, lib.lb_last_error(None).decode()
+
+
+def test_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
+    """Argument checks of lb_create run on the host before the first CUDA call: every
+    invalid lattice returns LB_ERR_ARG with a message and no context (no GPU needed)."""
+    import workloads as W
+    from paper_0911_0459_gb300 import lb
+    lib = lb.library()
+    cap = W.Capillary("v", 96, 24, 24, 64, 3, 18, 8, 6, W.binary_params(), theta_deg=45.0)
+
+    def edits():
+        yield "nx < 3", lambda g, w, p: setattr(g, "nx", 2)
+        yield "more than 2^31 - 1 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 32769))
+        yield "moments above 715827882 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 10923),
+                                                               setattr(p, "storage", lb.STORAGE_MOMENTS))
+        yield "liquid-gas in FP16", lambda g, w, p: (setattr(p, "model", 0), setattr(p, "storage", lb.STORAGE_F16DEV))
+        yield "unknown storage", lambda g, w, p: setattr(p, "storage", 9)
+        yield "tube longer than the grid", lambda g, w, p: setattr(w, "tube_len", 97)
+        yield "band as tall as the grid", lambda g, w, p: setattr(w, "tube_h", 24)
+        yield "band of one row", lambda g, w, p: setattr(w, "tube_h", 1)
+        yield "one reservoir column", lambda g, w, p: setattr(w, "tube_len", 95)
+        yield "wall gradient NaN", lambda g, w, p: setattr(w, "wall_grad", float("nan"))
+        yield "viscosity table of one entry", lambda g, w, p: setattr(p, "nu_table", 1)
+        yield "zero liquid viscosity", lambda g, w, p: setattr(p, "nu_l", 0.0)
+        yield "negative mobility", lambda g, w, p: setattr(p, "M", -0.1)
+
+    for what, edit in edits():
+        g, w, p = lb._structs_for(cap)
+        edit(g, w, p)
+        st, ctx, msg = _create_status(lib, g, w, p)
+        assert st == lb.LB_ERR_ARG and ctx is None and msg, what
+    # a mobility of zero is valid: the check is on the sign
+    g, w, p = lb._structs_for(cap)
+    p.M = 0.0
+    p.nu_table = -1
+    assert _create_status(lib, g, w, p)[0] == lb.LB_ERR_ARG
+
+
+def test_batch_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
+    import workloads as W
+    from paper_0911_0459_gb300 import lb
+    lib = lb.library()
+    caps = [W.Capillary("b", 96, 24, 24, 64, 3, 18, 8, 6, W.binary_params(), theta_deg=45.0),
+            W.Capillary("c", 104, 30, 24, 72, 3, 22, 8, 6, W.binary_params(), theta_deg=60.0)]
+
+    def status(edit=None, n=None):
+        s = [lb._structs_for(c) for c in caps]
+        if edit:
+            edit(s)
+        m = len(s) if n is None else n
+        G = (lb.LbGrid * len(s))(*[x[0] for x in s])
+        Wl = (lb.LbWalls * len(s))(*[x[1] for x in s])
+        P = (lb.LbParams * len(s))(*[x[2] for x in s])
+        out = ctypes.c_void_p()
+        st = lib.lb_batch_create(m, G, Wl, P, None, None, ctypes.byref(out))
+        return st, out.value, lib.lb_batch_last_error(None).decode()
+
+    def setp(i, k, v):
+        return lambda s: setattr(s[i][2], k, v)
+
+    cases = {
+        "no lattices": (None, 0),
+        "unknown storage": (lambda s: [setattr(x[2], "storage", 9) for x in s], None),
+        "liquid-gas lattice": (setp(1, "model", 0), None),
+        "mixed storages": (setp(1, "storage", lb.STORAGE_F64), None),
+        "moments above 715827882 nodes": (lambda s: ([setattr(x[2], "storage", lb.STORAGE_MOMENTS) for x in s],
+                                                    setattr(s[1][0], "nx", 65536), setattr(s[1][0], "ny", 10923),
+                                                    setattr(s[1][1], "tube_len", 0)), None),
+        "wall gradient NaN": (lambda s: setattr(s[0][1], "wall_grad", float("nan")), None),
+        "negative mobility": (setp(0, "M", -1.0), None),
+        "viscosity table of one entry": (setp(1, "nu_table", 1), None),
+        "tube longer than the grid": (lambda s: setattr(s[1][1], "tube_len", 200), None),
+    }
+    for what, (edit, n) in cases.items():
+        st, h, msg = status(edit, n)
+        assert st == lb.LB_ERR_ARG and h is None and msg, what
