@@ -5,6 +5,9 @@
 // and FP32 accumulation.  A 64x64 tile per CTA (4 warps of 32x32), K in steps
 // of 16 staged through shared memory; operands are addressed through element
 // strides, so the transposed products of the backward pass need no copies.
+// The weight gradients contract over the batch (K up to max_batch rows) into
+// small outputs: they split K over blockIdx.z and add the FP32 partials in a
+// fixed order afterwards (split-K, deterministic).
 // Epilogues fuse the bias and tanh (forward), the tanh derivative (backward)
 // and the BF16 rounding of activations.  Ensemble members run in the z
 // dimension of every launch.  One training iteration (forward, loss, backward,
@@ -43,6 +46,9 @@ struct GemmArgs {
   long ldcb, cb_mem;
   const bf16* H;  // activation whose tanh derivative multiplies (EPI_DTANH)
   long ldh, h_mem;
+  int ks;         // K splits: blockIdx.z = member * ks + split; split s takes K rows [s kc, (s + 1) kc)
+  int kc;
+  long cf_split;  // offset of split s's partial output from split 0's
 };
 
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
@@ -61,7 +67,8 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
   constexpr int TM = 64, TN = 64, TK = 16;
   __shared__ bf16 As[TM][TK + 8];
   __shared__ bf16 Bs[TK][TN + 8];
-  const int mem = blockIdx.z;
+  const int mem = blockIdx.z / g.ks, split = blockIdx.z - mem * g.ks;
+  const int kb = split * g.kc, ke = min(g.K, kb + g.kc);
   const bf16* A = g.A + mem * g.a_mem;
   const bf16* B = g.B + mem * g.b_mem;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
 
-  for (int k0 = 0; k0 < g.K; k0 += TK) {
+  for (int k0 = kb; k0 < ke; k0 += TK) {
     // stage the A (TM x TK) and B (TK x TN) tiles; consecutive threads walk the
     // unit-stride direction of each operand
     for (int e = tid; e < TM * TK; e += 128) {
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
         c = e % TK;
       }
       const int m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < g.K) ? A[m * g.sam + k * g.sak] : zero;
+      As[r][c] = (m < g.M && k < ke) ? A[m * g.sam + k * g.sak] : zero;
     }
     for (int e = tid; e < TK * TN; e += 128) {
       int r, c;
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
         c = e % TN;
       }
       const int k = k0 + r, n = n0 + c;
-      Bs[r][c] = (k < g.K && n < g.N) ? B[k * g.sbk + n * g.sbn] : zero;
+      Bs[r][c] = (k < ke && n < g.N) ? B[k * g.sbk + n * g.sbn] : zero;
     }
     __syncthreads();
 #pragma unroll
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
   }
 
   const float* bias = g.bias ? g.bias + mem * g.bias_mem : nullptr;
-  float* Cf = g.Cf ? g.Cf + mem * g.cf_mem : nullptr;
+  float* Cf = g.Cf ? g.Cf + mem * g.cf_mem + split * g.cf_split : nullptr;
   bf16* Cb = g.Cb ? g.Cb + mem * g.cb_mem : nullptr;
   const bf16* H = g.H ? g.H + mem * g.h_mem : nullptr;
 #pragma unroll
@@ -151,6 +158,20 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
 }
 
 // dY = 2 (Y - T) / (n n_out) in FP32 and BF16; per-member loss accumulated.
+// out[m][n] (row stride ldo, member stride o_mem) = sum over s = 0 .. ks - 1, in that
+// order, of the split-K partials part[member][s][m][n] (dense M x N).
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int ks, int M, int N, float* out, long ldo,
+                                  long o_mem) {
+  const int mem = blockIdx.y;
+  const long MN = (long)M * N;
+  const float* pm = part + (long)mem * ks * MN;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < MN; e += (long)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int s = 0; s < ks; ++s) v += pm[s * MN + e];
+    out[mem * o_mem + (e / N) * ldo + (e % N)] = v;
+  }
+}
+
 __global__ void loss_grad_kernel(const float* Y, const float* T, int n, int nout, long mem_stride, float* dYf,
                                  bf16* dYb, float* loss) {
   const int mem = blockIdx.y;
@@ -297,6 +318,8 @@ struct lb_mlp {
   // activations (per member)
   bf16 *xb, *xbp, *h1, *h2, *dyb, *dz2b, *dz1b;
   float *y, *dyf, *dz2f, *dz1f, *t;
+  float* part;  // split-K partials of the weight gradients
+  int ks_max;   // largest K split the partial buffer holds
   int n;  // rows of the loaded data
   cudaGraphExec_t gexec;
   int graph_n;
@@ -337,9 +360,35 @@ static cudaError_t gemm(lb_mlp* m, cudaStream_t s, int M, int N, int K, const bf
                         long bias_mem, float* Cf, long ldcf, long cf_mem, bf16* Cb, long ldcb, long cb_mem,
                         const bf16* H, long ldh, long h_mem) {
   GemmArgs g = {M, N, K, A, sam, sak, a_mem, B, sbk, sbn, b_mem, epi, bias, bias_mem,
-                Cf, ldcf, cf_mem, Cb, ldcb, cb_mem, H, ldh, h_mem};
+                Cf, ldcf, cf_mem, Cb, ldcb, cb_mem, H, ldh, h_mem, 1, K, 0};
   dim3 grid((N + 63) / 64, (M + 63) / 64, m->K);
   gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// A weight gradient C (M x N, FP32, row stride ldc, member stride c_mem) = A B with K
+// the batch: split-K over about 128 rows per split when K is long, then the fixed-order
+// sum of the partials into C.
+static cudaError_t gemm_wgrad(lb_mlp* m, cudaStream_t s, int M, int N, int K, const bf16* A, long sam, long sak,
+                              long a_mem, const bf16* B, long sbk, long sbn, long b_mem, float* C, long ldc,
+                              long c_mem) {
+  int ks = (K + 127) / 128;
+  if (ks > m->ks_max) ks = m->ks_max;
+  if (ks <= 1)
+    return gemm(m, s, M, N, K, A, sam, sak, a_mem, B, sbk, sbn, b_mem, EPI_F32, NULL, 0, C, ldc, c_mem, NULL, 0, 0,
+                NULL, 0, 0);
+  const int kc = ((K + ks - 1) / ks + 15) / 16 * 16;
+  ks = (K + kc - 1) / kc;
+  const long MN = (long)M * N;
+  GemmArgs g = {M, N, K, A, sam, sak, a_mem, B, sbk, sbn, b_mem, EPI_F32, NULL, 0,
+                m->part, N, ks * MN, NULL, 0, 0, NULL, 0, 0, ks, kc, MN};
+  dim3 grid((N + 63) / 64, (M + 63) / 64, m->K * ks);
+  gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e) return e;
+  const long blocks = (MN + 255) / 256;
+  splitk_sum_kernel<<<dim3((unsigned)(blocks < 1024 ? blocks : 1024), m->K), 256, 0, s>>>(m->part, ks, M, N, C, ldc,
+                                                                                          c_mem);
   return cudaGetLastError();
 }
 
@@ -368,8 +417,7 @@ static cudaError_t backward(lb_mlp* m, cudaStream_t s) {
   loss_grad_kernel<<<dim3(64, m->K), 256, 0, s>>>(m->y, m->t, n, m->nout, B * O, m->dyf, m->dyb, m->loss);
   if ((e = cudaGetLastError())) return e;
   // dW3 = dY^T H2, db3 = colsum dY
-  e = gemm(m, s, m->nout, m->nh, n, m->dyb, 1, O, B * O, m->h2, H, 1, B * H, EPI_F32, NULL, 0, m->g + m->ow3, H, m->P,
-           NULL, 0, 0, NULL, 0, 0);
+  e = gemm_wgrad(m, s, m->nout, m->nh, n, m->dyb, 1, O, B * O, m->h2, H, 1, B * H, m->g + m->ow3, H, m->P);
   if (e) return e;
   colsum_kernel<<<dim3(m->nout, m->K), 256, 0, s>>>(m->dyf, n, m->nout, B * O, m->g + m->ob3, m->P);
   if ((e = cudaGetLastError())) return e;
@@ -378,8 +426,7 @@ static cudaError_t backward(lb_mlp* m, cudaStream_t s) {
            B * H, m->dz2b, H, B * H, m->h2, H, B * H);
   if (e) return e;
   // dW2 = dZ2^T H1, db2
-  e = gemm(m, s, m->nh, m->nh, n, m->dz2b, 1, H, B * H, m->h1, H, 1, B * H, EPI_F32, NULL, 0, m->g + m->ow2, H, m->P,
-           NULL, 0, 0, NULL, 0, 0);
+  e = gemm_wgrad(m, s, m->nh, m->nh, n, m->dz2b, 1, H, B * H, m->h1, H, 1, B * H, m->g + m->ow2, H, m->P);
   if (e) return e;
   colsum_kernel<<<dim3(m->nh, m->K), 256, 0, s>>>(m->dz2f, n, m->nh, B * H, m->g + m->ob2, m->P);
   if ((e = cudaGetLastError())) return e;
@@ -388,8 +435,7 @@ static cudaError_t backward(lb_mlp* m, cudaStream_t s) {
            B * H, m->dz1b, H, B * H, m->h1, H, B * H);
   if (e) return e;
   // dW1 = dZ1^T X, db1
-  e = gemm(m, s, m->nh, m->nin, n, m->dz1b, 1, H, B * H, m->xb, 16, 1, 0, EPI_F32, NULL, 0, m->g + m->ow1, m->nin,
-           m->P, NULL, 0, 0, NULL, 0, 0);
+  e = gemm_wgrad(m, s, m->nh, m->nin, n, m->dz1b, 1, H, B * H, m->xb, 16, 1, 0, m->g + m->ow1, m->nin, m->P);
   if (e) return e;
   colsum_kernel<<<dim3(m->nh, m->K), 256, 0, s>>>(m->dz1f, n, m->nh, B * H, m->g + m->ob1, m->P);
   return cudaGetLastError();
@@ -449,7 +495,18 @@ lb_status lb_mlp_create(int nin, int nh, int nout, int members, int max_batch, u
   m->dyf = (float*)malloc_dev(m, members * B * nout * 4);
   m->dyb = (bf16*)malloc_dev(m, members * B * nout * 2);
   m->t = (float*)malloc_dev(m, B * nout * 4);
-  bool ok = m->p && m->g && m->m1 && m->m2 && m->pb && m->sched && m->loss && m->xb && m->xbp && m->h1 && m->h2 && m->dz2b &&
+  // split-K partials of the largest weight gradient (nh x max(nh, nout)), about 128
+  // batch rows per split, at most 32 splits and 256 MB
+  {
+    const long mn = (long)nh * (nh > nout ? nh : nout);
+    long ks = (B + 127) / 128;
+    if (ks > 32) ks = 32;
+    const long cap = (256L << 20) / (4L * members * mn);
+    if (ks > cap) ks = cap;
+    m->ks_max = ks > 1 ? (int)ks : 1;
+    m->part = m->ks_max > 1 ? (float*)malloc_dev(m, 4L * members * m->ks_max * mn) : NULL;
+  }
+  bool ok = (m->ks_max == 1 || m->part) && m->p && m->g && m->m1 && m->m2 && m->pb && m->sched && m->loss && m->xb && m->xbp && m->h1 && m->h2 && m->dz2b &&
             m->dz1b && m->dz2f && m->dz1f && m->y && m->dyf && m->dyb && m->t;
   if (!ok) {
     lb_mlp_destroy(m);
