@@ -1,0 +1,28 @@
+"""The Python example of README.md runs as written (needs a GPU)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_readme_example_runs():
+    text = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```python\n(.*?)```", text, flags=re.S)
+    assert blocks
+    env = {}
+    exec(compile(blocks[0], "README.md", "exec"), env)
+    d, theta, l_t = env["d"], env["theta"], env["l_t"]
+    assert d["l"] > 10.0 and np.isfinite(theta) and 0.0 < theta < 90.0
+    assert l_t.shape == (256, 3, 4) and np.isfinite(l_t).all()
+    assert np.all(l_t[:, 2, 0] >= l_t[:, 0, 0] - 1e-9)   # every meniscus moved in (or stayed)
+    env["lat"].close()
+    env["b"].close()
