@@ -34,7 +34,8 @@ typedef struct lb_mlp lb_mlp;
 /* Create members with Glorot-uniform weights from a counter-based generator
  * seeded by seed (member m uses seed + m), zero biases.  n_in <= 16,
  * n_hidden % 64 == 0 and <= 1024, n_out % 8 == 0 and <= 1024, 1 <= members
- * <= 16, max_batch >= 1.  Device memory through alloc (may be NULL). */
+ * <= 16, 1 <= max_batch <= 4194240 (65535 row tiles of 64), else
+ * LB_ERR_ARG.  Device memory through alloc (may be NULL). */
 lb_status lb_mlp_create(int n_in, int n_hidden, int n_out, int members, int max_batch,
                         unsigned long long seed, const lb_alloc *alloc, void *stream, lb_mlp **out);
 void lb_mlp_destroy(lb_mlp *m);

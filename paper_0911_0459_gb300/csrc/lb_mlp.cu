@@ -459,7 +459,7 @@ lb_status lb_mlp_create(int nin, int nh, int nout, int members, int max_batch, u
   if (!out) return LB_ERR_ARG;
   *out = NULL;
   if (nin < 1 || nin > 16 || nh < 64 || nh % 64 || nh > 1024 || nout < 8 || nout % 8 || nout > 1024 || members < 1 ||
-      members > 16 || max_batch < 1 || max_batch > (1 << 22))
+      members > 16 || max_batch < 1 || max_batch > 65535 * 64)  // row tiles of 64 on gridDim.y
     return merr(NULL, "invalid network shape"), LB_ERR_ARG;
   if (alloc && (!alloc->malloc_fn || !alloc->free_fn)) return merr(NULL, "incomplete allocator"), LB_ERR_ARG;
   m = new (std::nothrow) lb_mlp();

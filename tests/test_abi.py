@@ -166,3 +166,18 @@ def test_batch_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
     for what, (edit, n) in cases.items():
         st, h, msg = status(edit, n)
         assert st == lb.LB_ERR_ARG and h is None and msg, what
+
+
+def test_mlp_create_rejects_invalid_shapes_before_any_cuda_call(libpath):
+    """lb_mlp_create checks the network shape on the host: the largest batch is 65535 row
+    tiles of 64 (the GEMMs put row tiles on the grid's y dimension)."""
+    from paper_0911_0459_gb300 import lb
+    from paper_0911_0459_gb300.mlp import _lib
+    L = _lib()
+    bad = [(4, 256, 64, 5, 65535 * 64 + 1), (4, 256, 64, 5, 0), (17, 256, 64, 5, 4096), (4, 100, 64, 5, 4096),
+           (4, 256, 60, 5, 4096), (4, 256, 64, 17, 4096), (4, 2048, 64, 5, 4096), (0, 256, 64, 5, 4096)]
+    for shape in bad:
+        out = ctypes.c_void_p()
+        st = L.lb_mlp_create(*shape, 0, None, None, ctypes.byref(out))
+        assert st == lb.LB_ERR_ARG and out.value is None, shape
+        assert L.lb_mlp_last_error(None).decode()
