@@ -372,11 +372,13 @@ __device__ __forceinline__ void collide_node(const Phys<A>& P, A vr[3][3], A vp[
   const A c = (A(1) - omega) * A(0.25);
   const A mxx = c * (((fa[1] + fa[2]) - (fa[3] + fa[4])) - ((fe[1] + fe[2]) - (fe[3] + fe[4])));
   const A mxy = c * (((fa[5] + fa[6]) - (fa[7] + fa[8])) - ((fe[5] + fe[6]) - (fe[7] + fe[8])));
-  fs[0] = fe[0];
   fs[1] = fe[1] + mxx; fs[2] = fe[2] + mxx;
   fs[3] = fe[3] - mxx; fs[4] = fe[4] - mxx;
   fs[5] = fe[5] + mxy; fs[6] = fe[6] + mxy;
   fs[7] = fe[7] - mxy; fs[8] = fe[8] - mxy;
+  // the rest population from the rounded moving ones: the node's stored populations
+  // add up to rho to one rounding (in exact arithmetic it equals f^eq_0)
+  fs[0] = rho - (((fs[1] + fs[2]) + (fs[3] + fs[4])) + ((fs[5] + fs[6]) + (fs[7] + fs[8])));
 }
 
 // Push streaming from node (col[1], row yy) with bounce-back into solid
