@@ -544,3 +544,23 @@ def test_viscosity_table_picks_the_nearest_entry():
             bound = 0.5 * step * 12.0 / (6.0 * 0.0166 + 1.0) ** 2   # |d omega / d nu| <= 12 / (6 nu_g + 1)^2
             d = np.abs(om_t - om_exact)[fluid]
             assert d.max() <= bound * (1 + 1e-9) and d.max() > 0
+
+
+@pytest.mark.parametrize("A", [0.03, 0.04, 0.05])
+@pytest.mark.parametrize("phi0", [1.0, -1.0])
+def test_bulk_rest_populations_are_the_fp16_offsets(A, phi0):
+    """The FP16 deviation storage subtracts the rest weights of the bulk phases:
+    with u = 0 and no gradients Eq. (equilibrium) leaves f_i = w_i 3 P0 for i >= 1
+    (w = 1/9, 1/36) and f_0 = rho - sum, with the binary bulk pressure of Sec. 3.1,
+    P0 = rho/3 + A(-phi^2/2 + 3 phi^4/4) = 1/3 + A/4 at rho = 1, phi = +-1.  The
+    oracle's equilibrium of a uniform bulk at rest, before and after 50 steps, is that."""
+    cap = W.periodic_box(12, 10, W.binary_params(A=A, kappa=A, nu_l=0.4, nu_g=0.1))
+    o = oracle.Oracle(cap)
+    z = np.zeros((10, 12))
+    o.init_fields(np.ones_like(z), z, z, np.full_like(z, phi0))
+    P0 = 1.0 / 3.0 + A / 4.0
+    w = np.array([1 - 5 * P0 / 3] + [P0 / 3] * 4 + [P0 / 12] * 4)
+    for _ in range(2):
+        f, _ = o.populations()
+        assert np.abs(f - w[:, None, None]).max() < 1e-15
+        o.step(50)
