@@ -1,0 +1,62 @@
+"""Mistakes planted in a copy of the oracle, on the CPU: every one must fail a pin of
+tests/test_oracle_pins.py, so that the pins would catch it in the oracle itself.
+
+Each case copies oracle/, workloads/ and the pins into a scratch directory, changes
+one line of the C source (the change must apply exactly once), rebuilds the copy and
+runs the pins against it in a separate process.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = [
+    ("wall gradient of the wetting ghosts with the wrong sign (Sec. 2.2)",
+     "out[jy][jx] = raw[1 - dy][1] - 2.0 * h;", "out[jy][jx] = raw[1 - dy][1] + 2.0 * h;"),
+    ("xy weights of Eq. (equilibrium) on the wrong diagonals",
+     "static const double WXY[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.25, 0.25, -0.25, -0.25};",
+     "static const double WXY[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.25, -0.25, 0.25, -0.25};"),
+    ("lambda term of Eq. (equilibrium) without its u . grad rho trace",
+     "lambda * (u[a] * dr[b] + u[b] * dr[a] + (a == b ? udr : 0.0))", "lambda * (u[a] * dr[b] + u[b] * dr[a])"),
+    ("binary pressure without -kappa phi lap phi (Sec. 3.1)",
+     "const double P0 = p0 - p->kappa * ph * s->plap[k];", "const double P0 = p0;"),
+    ("g^eq with M mu instead of 2 M mu (App. A)", "double s = 2.0 * Mob * mu;", "double s = Mob * mu;"),
+    ("no rest rule at boundary nodes (Sec. 2.2)", "if (s->bnd[k]) rest_node(s->ft + 9 * (size_t)k);", "(void)0;"),
+    ("a wrong row of M (App. A)", "{0, 1, -1, 0, 0, 1, -1, -1, 1},", "{0, 1, -1, 0, 0, 1, -1, 1, -1},"),
+]
+
+
+def run_pins(tmp_path, mutate=None):
+    """Copy the oracle and its pins to tmp_path, apply mutate to the C source, run the pins."""
+    for d in ("oracle", "workloads"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
+    (tmp_path / "tests").mkdir()
+    for f in ("test_oracle_pins.py", "conftest.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
+    if mutate:
+        src = tmp_path / "oracle" / "lb_oracle.c"
+        src.write_text(mutate(src.read_text()))
+    return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q", "-p",
+                           "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=900,
+                          env={**os.environ, "PYTHONPATH": str(tmp_path)})
+
+
+def test_unchanged_copy_passes_the_pins(tmp_path):
+    """The control: the scratch copy itself passes, so a failure below is the mistake's."""
+    r = run_pins(tmp_path)
+    assert r.returncode == 0, r.stdout[-800:]
+
+
+@pytest.mark.parametrize("what,old,new", MUTATIONS, ids=[m[0][:40] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(tmp_path, what, old, new):
+    def mutate(text):
+        assert text.count(old) == 1, f"mutation no longer applies: {what}"
+        return text.replace(old, new)
+    r = run_pins(tmp_path, mutate)
+    assert r.returncode != 0 and " failed" in r.stdout, f"no pin caught: {what}\n{r.stdout[-800:]}"
