@@ -13,7 +13,7 @@ def test_backward_matches_finite_differences():
     t = rng.normal(0, 1, (n, nout))
     loss, g = mlp.loss_and_grads(p, x, t, nin, nh, nout)
     eps = 1e-6
-    for i in rng.choice(P, 40, replace=False):
+    for i in range(P):   # every parameter of every tensor
         e = np.zeros(P)
         e[i] = eps
         lp = mlp.loss_and_grads(p + e, x, t, nin, nh, nout)[0]

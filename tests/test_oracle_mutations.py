@@ -1,8 +1,9 @@
-"""Mistakes planted in a copy of the oracle, on the CPU: every one must fail a pin of
-tests/test_oracle_pins.py, so that the pins would catch it in the oracle itself.
+"""Mistakes planted in a copy of the oracle, on the CPU: every one must fail a pin
+(tests/test_oracle_pins.py for the lattice Boltzmann oracle, tests/test_mlp_oracle.py for
+the FP64 network), so that the pins would catch it in the oracle itself.
 
 Each case copies oracle/, workloads/ and the pins into a scratch directory, changes
-one line of the C source (the change must apply exactly once), rebuilds the copy and
+one line of the source (the change must apply exactly once), rebuilds the copy and
 runs the pins against it in a separate process.
 """
 import os
@@ -30,19 +31,19 @@ MUTATIONS = [
 ]
 
 
-def run_pins(tmp_path, mutate=None):
-    """Copy the oracle and its pins to tmp_path, apply mutate to the C source, run the pins."""
+def run_pins(tmp_path, mutate=None, source="lb_oracle.c", pins="test_oracle_pins.py"):
+    """Copy the oracle and its pins to tmp_path, apply mutate to one oracle source, run the pins."""
     for d in ("oracle", "workloads"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
     (tmp_path / "tests").mkdir()
-    for f in ("test_oracle_pins.py", "conftest.py"):
+    for f in (pins, "conftest.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests" / f)
     shutil.copytree(os.path.join(ROOT, "tests", "golden"), tmp_path / "tests" / "golden")
     if mutate:
-        src = tmp_path / "oracle" / "lb_oracle.c"
+        src = tmp_path / "oracle" / source
         src.write_text(mutate(src.read_text()))
-    return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q", "-p",
+    return subprocess.run([sys.executable, "-m", "pytest", "tests/" + pins, "-x", "-q", "-p",
                            "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=900,
                           env={**os.environ, "PYTHONPATH": str(tmp_path)})
 
@@ -59,4 +60,22 @@ def test_planted_mistake_fails_a_pin(tmp_path, what, old, new):
         assert text.count(old) == 1, f"mutation no longer applies: {what}"
         return text.replace(old, new)
     r = run_pins(tmp_path, mutate)
+    assert r.returncode != 0 and " failed" in r.stdout, f"no pin caught: {what}\n{r.stdout[-800:]}"
+
+
+MLP_MUTATIONS = [
+    ("tanh derivative without the square", "dz2 = (dy @ W3) * (1.0 - h2 * h2)", "dz2 = (dy @ W3) * (1.0 - h2)"),
+    ("loss gradient without its factor 2", "dy = 2.0 * d / (n * nout)", "dy = d / (n * nout)"),
+    ("transposed W2 in the backward pass", "dz1 = (dz2 @ W2) * (1.0 - h1 * h1)", "dz1 = (dz2 @ W2.T) * (1.0 - h1 * h1)"),
+    ("output-bias gradient averaged over rows", "gb3 = dy.sum(0)", "gb3 = dy.mean(0)"),
+    ("first-layer gradient from the wrong activations", "gW1 = dz1.T @ x", "gW1 = dz1.T @ np.tanh(x)"),
+]
+
+
+@pytest.mark.parametrize("what,old,new", MLP_MUTATIONS, ids=[m[0][:40] for m in MLP_MUTATIONS])
+def test_planted_mistake_in_the_network_reference_fails_a_pin(tmp_path, what, old, new):
+    def mutate(text):
+        assert text.count(old) == 1, f"mutation no longer applies: {what}"
+        return text.replace(old, new)
+    r = run_pins(tmp_path, mutate, source="mlp.py", pins="test_mlp_oracle.py")
     assert r.returncode != 0 and " failed" in r.stdout, f"no pin caught: {what}\n{r.stdout[-800:]}"
