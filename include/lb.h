@@ -25,8 +25,11 @@
  *   - Work is issued on the stream passed to lb_create (a cudaStream_t, NULL for
  *     the default stream).  lb_step returns without waiting; every call that
  *     returns data to the host waits for the stream.
- *   - After LB_ERR_NONFINITE or LB_ERR_TIMEOUT the context accepts only
- *     lb_fields, lb_get_populations, lb_last_error and lb_destroy.
+ *   - After LB_ERR_NONFINITE or LB_ERR_TIMEOUT, lb_step and lb_autotune return
+ *     LB_ERR_STATE until the state is replaced (lb_init_fields or
+ *     lb_set_populations, which clear the condition); the reading calls
+ *     (lb_fields, lb_get_populations, lb_get_moments, lb_filled_length),
+ *     lb_last_error and lb_destroy remain available.
  *
  * Geometry (Sec. 2.2, Fig. 1b): the grid is periodic in x and y.  The tube
  * occupies the columns [tube_x0, tube_x0 + tube_len) (mod nx); inside them the
@@ -53,7 +56,7 @@ typedef enum {
   LB_ERR_ARG = 1,       /* invalid argument; nothing was changed */
   LB_ERR_CUDA = 2,      /* a CUDA call failed; see lb_last_error */
   LB_ERR_NONFINITE = 3, /* a reduction found a NaN or Inf in the state */
-  LB_ERR_TIMEOUT = 4,   /* a device-side wait gave up (batched persistent kernel) */
+  LB_ERR_TIMEOUT = 4,   /* a device-side wait gave up (staged or persistent kernel) */
   LB_ERR_STATE = 5,     /* call not allowed in the context's current state */
   LB_ERR_NOMEM = 6      /* device allocation failed */
 } lb_status;

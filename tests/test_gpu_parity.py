@@ -271,6 +271,7 @@ def test_nonfinite_state_is_detected_and_poisons_the_context():
     cap = W.Capillary("n", 64, 20, 16, 40, 2, 16, 8, 6, W.binary_params(), theta_deg=60.0)
     lat = Lattice.from_workload(cap)
     f, g = lat.populations(False)
+    f0, g0 = f.copy(), g.copy()
     f[3, 10, 5] = np.nan
     lat.set_populations(f, g)
     lat.step(2)
@@ -281,6 +282,11 @@ def test_nonfinite_state_is_detected_and_poisons_the_context():
         lat.step(1)
     assert e.value.status == lbmod.LB_ERR_STATE
     lat.fields()   # still readable
+    # replacing the state clears the condition: the lattice steps again from it
+    lat.set_populations(f0, g0)
+    lat.step(3)
+    d = lat.filled_length()
+    assert np.isfinite(d["mass"]) and np.isfinite(d["l"])
 
 
 def test_invalid_arguments_are_rejected():
