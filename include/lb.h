@@ -199,9 +199,10 @@ lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
  * else the sliding-window kernel), 1 = sliding-window kernel (rows held in
  * registers), 2 = staged kernel (rows brought into shared memory by bulk
  * copies; fits when nx % 8 == 0 and nx * ny <= 477218588, else LB_ERR_ARG)
- * with its shallow ring of row stages, 3 = staged kernel with its deep ring.  All compute the same update bit for bit.
- * LB_STORAGE_MOMENTS has one kernel of its own (variant 4; 0 and 4 are
- * accepted).  Invalidates the captured step graph. */
+ * with its shallow ring of row stages, 3 = staged kernel with its deep ring.
+ * All compute the same update bit for bit.  LB_STORAGE_MOMENTS has one kernel
+ * of its own (variant 4; 0 and 4 are accepted).  Invalidates the captured step
+ * graph. */
 lb_status lb_set_kernel(lb_ctx *ctx, int variant);
 /* The kernel variant in use (1, 2, 3 or 4; automatic selection resolved). */
 lb_status lb_get_kernel(const lb_ctx *ctx, int *variant);
