@@ -5,8 +5,8 @@
  * compares with Washburn's law (Eqs. 1-3).  This library learns the map from a
  * capillary's parameters to its filling curve from runs of the batched lattice
  * Boltzmann sweep (lb_batch_run_sampled), so that a sweep over parameters can
- * be answered without running the LB, and falls back to the LB (the judge of
- * its error) wherever its ensemble disagrees.
+ * be answered without running the LB, and falls back to the LB (the reference
+ * for its error) wherever its ensemble disagrees.
  *
  * Network (per ensemble member): x (n_in) -> tanh(W1 x + b1) (n_hidden) ->
  * tanh(W2 h1 + b2) (n_hidden) -> W3 h2 + b3 (n_out).  The contractions run on

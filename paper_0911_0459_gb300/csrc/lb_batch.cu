@@ -651,7 +651,7 @@ lb_status lb_batch_run_sampled(lb_batch* b, int nsamples, const long* at, double
   if (e == cudaSuccess) {
     e = cudaGraphLaunch(exec, b->stream);
   } else {
-    // the driver refused the graph: issue the same sequence directly
+    // CUDA refused the graph: issue the same sequence directly
     cudaGetLastError();
     parity = b->parity;
     t = 0;
