@@ -180,6 +180,18 @@ lb_status lb_set_populations(lb_ctx *ctx, const double *f, const double *g);
  * stream. */
 lb_status lb_get_moments(lb_ctx *ctx, double *m);
 
+/* Checkpoints: the stored state exactly as the storage holds it (the f
+ * planes, then the g planes, then the FP32 g_0 plane of LB_STORAGE_F16DEV; for
+ * LB_STORAGE_MOMENTS the three moment planes), lb_state_bytes bytes in host
+ * memory the caller owns.  lb_load_state takes such bytes from a lattice of the
+ * same grid, walls and params (LB_ERR_ARG if the size differs), sets the step
+ * counter to time and clears a non-finite or timed-out condition; the
+ * continued run is bit for bit the run that was saved.  Both wait for the
+ * stream. */
+size_t lb_state_bytes(const lb_ctx *ctx);
+lb_status lb_save_state(lb_ctx *ctx, void *host, size_t bytes);
+lb_status lb_load_state(lb_ctx *ctx, const void *host, size_t bytes, long time);
+
 /* Wait for all work issued on the context's stream. */
 lb_status lb_sync(lb_ctx *ctx);
 
@@ -258,6 +270,14 @@ lb_status lb_batch_moments(lb_batch *b, int i, double *m);
  * tile) on the batch itself for 2*steps steps each (this advances the state). */
 lb_status lb_batch_set_tile(lb_batch *b, int tile_x, int tile_y);
 lb_status lb_batch_autotune(lb_batch *b, int steps, int *tile_x, int *tile_y, double *ms_per_step);
+
+/* Checkpoints of the whole batch, as lb_save_state / lb_load_state: every
+ * lattice's state in the batch's own arena layout (lattices one after the
+ * other, offsets padded to 64 elements), for a batch created with the same
+ * lattices and storage.  lb_batch_load_state does not clear a timed-out batch. */
+size_t lb_batch_state_bytes(const lb_batch *b);
+lb_status lb_batch_save_state(lb_batch *b, void *host, size_t bytes);
+lb_status lb_batch_load_state(lb_batch *b, const void *host, size_t bytes, long time);
 
 /* Body of the persistent kernel, as lb_set_kernel: 0 = automatic (staged when
  * the staged kernel fits every lattice, else sliding-window), 1 = sliding-window

@@ -39,8 +39,10 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
         const float z[M_PLANES] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         mom_store(B.f, N, n, z);
       } else {
+        // zero bits in every plane (with the FP16 offsets a stored 0 would not be),
+        // the same as a fresh buffer: no step reads or writes a solid node
         for (int i = 0; i < 9; ++i) {
-          S::sf(B.f, N, n, i, A(0), B.r);
+          B.f[i * N + n] = typename S::T(0.0f);
           if (BIN) S::sg(B.g, B.g0, N, n, i, A(0));
         }
       }
@@ -174,7 +176,10 @@ __global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, 
       mom_store(B.f, N, n, mf);
     } else {
       for (int i = 0; i < 9; ++i) {
-        S::sf(B.f, N, n, i, sol ? A(0) : A(fi[i * N + n]), B.r);
+        if (sol)
+          B.f[i * N + n] = typename S::T(0.0f);  // zero bits, as in init_kernel
+        else
+          S::sf(B.f, N, n, i, A(fi[i * N + n]), B.r);
         if (MODEL == MODEL_BINARY) S::sg(B.g, B.g0, N, n, i, sol ? A(0) : A(gi[i * N + n]));
       }
     }

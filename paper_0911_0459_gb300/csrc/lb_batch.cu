@@ -37,6 +37,7 @@ struct lb_batch {
   void* f[2];
   void* g[2];
   float* g0[2];
+  size_t bytes_f, bytes_g, bytes_g0;  // arena sizes
   void* d_caps;
   TileDesc* d_tiles;   // tiles in schedule order: CTA k takes d_tiles[start[k] .. start[k+1])
   int* d_start;
@@ -536,6 +537,9 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
     b->f[k] = balloc(b, of * el);
     b->g[k] = og ? balloc(b, og * el) : NULL;
     b->g0[k] = storage == LB_STORAGE_F16DEV ? (float*)balloc(b, o0 * sizeof(float)) : NULL;
+    b->bytes_f = of * el;
+    b->bytes_g = og ? og * el : 0;
+    b->bytes_g0 = storage == LB_STORAGE_F16DEV ? o0 * sizeof(float) : 0;
     if (!b->f[k] || (og && !b->g[k]) || (storage == LB_STORAGE_F16DEV && !b->g0[k])) {
       snprintf(g_batch_create_err, sizeof g_batch_create_err, "device allocation of the batch state failed");
       lb_batch_destroy(b);
@@ -601,6 +605,36 @@ lb_status lb_batch_step(lb_batch* b, long n) {
   BCK(launch_batch(b, (int)n, b->stream));
   b->parity = (b->parity + (int)(n & 1)) & 1;
   b->t += n;
+  return LB_OK;
+}
+
+size_t lb_batch_state_bytes(const lb_batch* b) { return b ? b->bytes_f + b->bytes_g + b->bytes_g0 : 0; }
+
+// The arenas of the current state as they are held on the device: f, then g, then g_0.
+lb_status lb_batch_save_state(lb_batch* b, void* host, size_t bytes) {
+  if (!b || !host) return b ? (berr(b, "host is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
+  if (bytes != lb_batch_state_bytes(b)) return berr(b, "bytes must equal lb_batch_state_bytes"), LB_ERR_ARG;
+  const int k = b->parity;
+  unsigned char* h = static_cast<unsigned char*>(host);
+  BCK(cudaMemcpyAsync(h, b->f[k], b->bytes_f, cudaMemcpyDeviceToHost, b->stream));
+  if (b->bytes_g) BCK(cudaMemcpyAsync(h + b->bytes_f, b->g[k], b->bytes_g, cudaMemcpyDeviceToHost, b->stream));
+  if (b->bytes_g0)
+    BCK(cudaMemcpyAsync(h + b->bytes_f + b->bytes_g, b->g0[k], b->bytes_g0, cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  return LB_OK;
+}
+
+lb_status lb_batch_load_state(lb_batch* b, const void* host, size_t bytes, long time) {
+  if (!b || !host || time < 0) return b ? (berr(b, "host is NULL or time < 0"), LB_ERR_ARG) : LB_ERR_ARG;
+  if (bytes != lb_batch_state_bytes(b)) return berr(b, "bytes must equal lb_batch_state_bytes"), LB_ERR_ARG;
+  const unsigned char* h = static_cast<const unsigned char*>(host);
+  BCK(cudaMemcpyAsync(b->f[0], h, b->bytes_f, cudaMemcpyHostToDevice, b->stream));
+  if (b->bytes_g) BCK(cudaMemcpyAsync(b->g[0], h + b->bytes_f, b->bytes_g, cudaMemcpyHostToDevice, b->stream));
+  if (b->bytes_g0)
+    BCK(cudaMemcpyAsync(b->g0[0], h + b->bytes_f + b->bytes_g, b->bytes_g0, cudaMemcpyHostToDevice, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  b->parity = 0;
+  b->t = time;
   return LB_OK;
 }
 

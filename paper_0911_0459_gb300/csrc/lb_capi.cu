@@ -498,6 +498,45 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
   return LB_OK;
 }
 
+size_t lb_state_bytes(const lb_ctx* c) {
+  if (!c) return 0;
+  size_t fb, gb, g0b;
+  return state_bytes(c->prm.model, c->prm.storage, (size_t)c->grid.nx * c->grid.ny, &fb, &gb, &g0b);
+}
+
+// The stored state as the storage holds it: the f planes, then the g planes, then the
+// FP32 g_0 plane (FP16 storage), each as in device memory.
+lb_status lb_save_state(lb_ctx* c, void* host, size_t bytes) {
+  if (!c || !host) return c ? (set_err(c, "host is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
+  size_t fb, gb, g0b;
+  const size_t total = state_bytes(c->prm.model, c->prm.storage, (size_t)c->grid.nx * c->grid.ny, &fb, &gb, &g0b);
+  if (bytes != total) return set_err(c, "bytes must equal lb_state_bytes (%zu)", total), LB_ERR_ARG;
+  const OpBufs& b = c->buf[c->cur];
+  unsigned char* h = static_cast<unsigned char*>(host);
+  CK(cudaMemcpyAsync(h, b.f, fb, cudaMemcpyDeviceToHost, c->stream));
+  if (gb) CK(cudaMemcpyAsync(h + fb, b.g, gb, cudaMemcpyDeviceToHost, c->stream));
+  if (g0b) CK(cudaMemcpyAsync(h + fb + gb, b.g0, g0b, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return LB_OK;
+}
+
+lb_status lb_load_state(lb_ctx* c, const void* host, size_t bytes, long time) {
+  if (!c || !host || time < 0) return c ? (set_err(c, "host is NULL or time < 0"), LB_ERR_ARG) : LB_ERR_ARG;
+  size_t fb, gb, g0b;
+  const size_t total = state_bytes(c->prm.model, c->prm.storage, (size_t)c->grid.nx * c->grid.ny, &fb, &gb, &g0b);
+  if (bytes != total) return set_err(c, "bytes must equal lb_state_bytes (%zu)", total), LB_ERR_ARG;
+  const OpBufs& b = c->buf[0];
+  const unsigned char* h = static_cast<const unsigned char*>(host);
+  CK(cudaMemcpyAsync(b.f, h, fb, cudaMemcpyHostToDevice, c->stream));
+  if (gb) CK(cudaMemcpyAsync(b.g, h + fb, gb, cudaMemcpyHostToDevice, c->stream));
+  if (g0b) CK(cudaMemcpyAsync(b.g0, h + fb + gb, g0b, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  c->t = time;
+  c->poisoned = 0;
+  return LB_OK;
+}
+
 lb_status lb_get_moments(lb_ctx* c, double* m) {
   if (!c || !m) return c ? (set_err(c, "m is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
   const size_t N = (size_t)c->grid.nx * c->grid.ny;

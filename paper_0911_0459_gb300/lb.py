@@ -81,6 +81,9 @@ def library():
         "lb_get_moments": (C.c_int, [vp, dp]),
         "lb_set_populations": (C.c_int, [vp, dp, dp]),
         "lb_sync": (C.c_int, [vp]),
+        "lb_state_bytes": (C.c_size_t, [vp]),
+        "lb_save_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "lb_load_state": (C.c_int, [vp, vp, C.c_size_t, C.c_long]),
         "lb_time": (C.c_long, [vp]),
         "lb_fluid_nodes": (C.c_long, [vp]),
         "lb_set_tile": (C.c_int, [vp, C.c_int, C.c_int]),
@@ -106,6 +109,9 @@ def library():
         "lb_batch_time": (C.c_long, [vp]),
         "lb_batch_fluid_nodes": (C.c_long, [vp, C.c_int]),
         "lb_batch_last_error": (C.c_char_p, [vp]),
+        "lb_batch_state_bytes": (C.c_size_t, [vp]),
+        "lb_batch_save_state": (C.c_int, [vp, vp, C.c_size_t]),
+        "lb_batch_load_state": (C.c_int, [vp, vp, C.c_size_t, C.c_long]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -121,7 +127,9 @@ def exported_symbols():
             "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
             "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
             "lb_batch_populations", "lb_batch_moments", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
-            "lb_batch_set_kernel", "lb_batch_get_kernel", "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error"]
+            "lb_batch_set_kernel", "lb_batch_get_kernel", "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error",
+            "lb_state_bytes", "lb_save_state", "lb_load_state", "lb_batch_state_bytes", "lb_batch_save_state",
+            "lb_batch_load_state"]
 
 
 class _TorchAllocator:
@@ -296,6 +304,32 @@ class Lattice:
         _check(library().lb_get_moments(self.h, _p(m)), self.h)
         return m
 
+    def save_state(self):
+        """Checkpoint: (bytes of the stored state as a uint8 array, step count)."""
+        L = library()
+        buf = np.empty(L.lb_state_bytes(self.h), dtype=np.uint8)
+        _check(L.lb_save_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes), self.h)
+        return buf, self.time
+
+    def load_state(self, buf, time):
+        """Resume from save_state's bytes (a lattice of the same description)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(library().lb_load_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, int(time)), self.h)
+        return self
+
+    def save(self, path):
+        """save_state to an .npz file, with the grid, model and storage that must match on load."""
+        buf, t = self.save_state()
+        np.savez(path, state=buf, time=t, nx=self.grid.nx, ny=self.grid.ny, model=self.params.model,
+                 storage=self.params.storage)
+
+    def load(self, path):
+        d = np.load(path)
+        if (int(d["nx"]), int(d["ny"]), int(d["model"]), int(d["storage"])) != \
+                (self.grid.nx, self.grid.ny, self.params.model, self.params.storage):
+            raise ValueError(f"{path}: checkpoint of another grid, model or storage")
+        return self.load_state(d["state"], int(d["time"]))
+
     def set_populations(self, f, g=None):
         s = (9,) + self.shape
         f = _host(f, s)
@@ -418,6 +452,20 @@ class Batch:
         m = np.empty((6, c.ny, c.nx))
         _bcheck(library().lb_batch_moments(self.h, int(i), _p(m)), self.h)
         return m
+
+    def save_state(self):
+        """Checkpoint of every lattice: (bytes of the batch's state as a uint8 array, step count)."""
+        L = library()
+        buf = np.empty(L.lb_batch_state_bytes(self.h), dtype=np.uint8)
+        _bcheck(L.lb_batch_save_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes), self.h)
+        return buf, self.time
+
+    def load_state(self, buf, time):
+        """Resume from save_state's bytes (a batch of the same lattices and storage)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _bcheck(library().lb_batch_load_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, int(time)),
+                self.h)
+        return self
 
     def set_tile(self, tx, ty):
         _bcheck(library().lb_batch_set_tile(self.h, int(tx), int(ty)), self.h)
