@@ -14,7 +14,8 @@ if not torch.cuda.is_available():
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_readme_example_runs():
+def test_readme_example_runs(tmp_path, monkeypatch):
+    monkeypatch.chdir(tmp_path)   # the example writes a checkpoint file
     text = open(os.path.join(ROOT, "README.md")).read()
     blocks = re.findall(r"```python\n(.*?)```", text, flags=re.S)
     assert blocks
@@ -26,5 +27,6 @@ def test_readme_example_runs():
     # early on the flat initial meniscus curves and its centre falls back: l may drop;
     # the mass of every capillary is kept up to the FP32 storage's rounding
     np.testing.assert_allclose(l_t[:, 2, 2], l_t[:, 0, 2], rtol=1e-5)   # FP32 rounding: ~3e-9 per step
+    assert (tmp_path / "fill.npz").exists()
     env["lat"].close()
     env["b"].close()
