@@ -1,5 +1,10 @@
 """Checkpoints: a run saved, resumed in a fresh lattice or batch and continued equals the
 uninterrupted run bit for bit, for every storage (needs a GPU)."""
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -88,3 +93,23 @@ def test_batch_checkpoint_resumes_bit_for_bit(storage):
         b2.load_state(buf[:-16], 0)
     b1.close()
     b2.close()
+
+
+def test_runner_resumes_from_its_checkpoint(tmp_path):
+    """python -m paper_0911_0459_gb300.run: 300 steps saved and resumed to 500 log the same
+    last line as 500 steps in one go."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+    def run(*args):
+        r = subprocess.run([sys.executable, "-m", "paper_0911_0459_gb300.run", "--config", "binary_crop_1024x64",
+                            "--every", "100", *args], capture_output=True, text=True, cwd=tmp_path, timeout=600,
+                           env={**os.environ, "PYTHONPATH": root})
+        assert r.returncode == 0, r.stderr[-2000:]
+        return [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    first = run("--steps", "300", "--save", "ck.npz")
+    assert [x["step"] for x in first] == [100, 200, 300]
+    resumed = run("--steps", "500", "--resume", "ck.npz")
+    assert [x["step"] for x in resumed] == [400, 500]
+    direct = run("--steps", "500")
+    for k in ("l", "l_vol", "mass", "phi_sum"):
+        assert resumed[-1][k] == direct[-1][k], k
