@@ -95,6 +95,7 @@ def test_binary_high_viscosity_ratio_dynamic_angle():
         assert 60.0 < late[M] < 70.0
         assert early > late[M] + 1.5
         assert abs(late[M] - GOLD["binary_theta_dyn_late"]["value"]) < 6.0
+        assert abs(early - GOLD["binary_theta_dyn_early"]["value"]) < 6.0
     assert late[0.5] < late[0.1]
 
 

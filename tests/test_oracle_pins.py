@@ -325,6 +325,11 @@ def test_binary_flat_interface_profile():
     lo = an.crossings_along_x(ph[None, :48], -0.8)[0][0]
     hi = an.crossings_along_x(ph[None, :48], 0.8)[0][0]
     assert abs((hi - lo) - 2 * math.sqrt(2) * math.atanh(0.8)) < 0.15
+    # the printed "about 4 lattice sites" is the width between phi = -0.9 and 0.9
+    # (2 sqrt2 atanh(0.9) = 4.2 for the continuum profile)
+    lo9 = an.crossings_along_x(ph[None, :48], -0.9)[0][0]
+    hi9 = an.crossings_along_x(ph[None, :48], 0.9)[0][0]
+    assert abs((hi9 - lo9) - GOLD["binary_interface_width"]["value"]) < 0.5
 
 
 @pytest.mark.slow
@@ -564,3 +569,16 @@ def test_bulk_rest_populations_are_the_fp16_offsets(A, phi0):
         f, _ = o.populations()
         assert np.abs(f - w[:, None, None]).max() < 1e-15
         o.step(50)
+
+
+def test_workload_parameters_are_the_printed_ones():
+    """The inputs use the parameter values the paper prints (Sec. 2, Sec. 3.1, Sec. 3.2)."""
+    lg, g = W.lg_params(), GOLD["lg_params"]
+    assert (lg.kappa, lg.a, lg.b, lg.T) == (g["kappa"], g["a"], g["b"], g["T"])
+    assert abs(g["a"] - 9 / 49) < 1e-15 and abs(g["b"] - 2 / 21) < 1e-15
+    bp, gb = W.binary_params(), GOLD["binary_params"]
+    assert (bp.A, bp.kappa) == (gb["A"], gb["kappa"])
+    run = pytest.importorskip("paper_0911_0459_gb300.run")   # absent from the oracle-only copies
+    p = run.paper_700x40(1).params
+    v = GOLD["viscosity_ratio_washburn"]
+    assert (p.nu_l, p.nu_g) == (v["nu_l"], v["nu_g"]) and 60 < v["nu_l"] / v["nu_g"] < 80
