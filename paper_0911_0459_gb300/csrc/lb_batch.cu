@@ -1,4 +1,15 @@
 // Host side of the batched capillary sweep (lb_batch_* in include/lb.h).
+//
+// lb_batch_create validates every lattice, lays the lattices out one after the
+// other in one arena per buffer (offsets padded to 64 elements, zeroed), builds
+// the flat tile list (capillary, column block, row band; all-solid tiles left
+// out) and the reduction chunks, and sets each lattice's default initial state.
+// A launch runs n steps of the persistent kernel of the chosen body (sliding
+// window, staged shallow or deep ring, or the moment strips): the tiles are
+// assigned to CTAs on the host, longest estimated cost first, so that every CTA
+// carries about the same work each step.  lb_batch_run_sampled captures the
+// launches between samples and the FP64 reductions at each sample into one CUDA
+// graph.  The autotuner times every body and tile on the batch itself.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>

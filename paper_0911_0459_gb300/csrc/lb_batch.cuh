@@ -2,9 +2,9 @@
 // sweep.  The lattices live in one arena (two buffers); a flat list of tiles
 // (capillary, column block, row band) covers all of them.  Each CTA processes
 // its own list of tiles (balanced on the host) every time step, then waits at
-// a grid barrier before the next step.  The launch is cooperative, so all CTAs are resident; the barrier still
-// gives up after a time limit, records LB_ERR_TIMEOUT in the error word and
-// every CTA returns.
+// a grid barrier before the next step.  The launch is cooperative, so all CTAs
+// are resident; the barrier still gives up after a time limit, records
+// LB_ERR_TIMEOUT in the error word and every CTA returns.
 #pragma once
 
 #include "lb_aux.cuh"
