@@ -1,5 +1,6 @@
 // Host library behind include/lb.h: context, device memory, stream, CUDA-graph
-// replay of the step kernel, reductions, tile autotuner.
+// replay of the step kernel, reductions, kernel and tile autotuner, state import,
+// export and byte-exact checkpoints.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
