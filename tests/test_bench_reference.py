@@ -20,3 +20,12 @@ def test_reference_arm_prints_one_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_bench_options():
+    """The options the benchmark contract and the profiles' commands use."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True,
+                         text=True, timeout=120, cwd=ROOT).stdout
+    for opt in ("--gpus", "--steps", "--warmup", "--impl", "--tile", "--storage", "--profile", "--no-cpu-baseline",
+                "--no-batch", "--no-surrogate"):
+        assert opt in out, opt
