@@ -28,6 +28,14 @@ MUTATIONS = [
     ("g^eq with M mu instead of 2 M mu (App. A)", "double s = 2.0 * Mob * mu;", "double s = Mob * mu;"),
     ("no rest rule at boundary nodes (Sec. 2.2)", "if (s->bnd[k]) rest_node(s->ft + 9 * (size_t)k);", "(void)0;"),
     ("a wrong row of M (App. A)", "{0, 1, -1, 0, 0, 1, -1, -1, 1},", "{0, 1, -1, 0, 0, 1, -1, 1, -1},"),
+    ("Eq. (nu) interpolated in the square of (phi + 1)/2 (right only at phi = +-1)",
+     "double c = 0.5 * (phi + 1.0);", "double c = 0.25 * (phi + 1.0) * (phi + 1.0);"),
+    ("liquid-gas l(t) threshold at rho_l / 2 instead of (rho_l + rho_g) / 2 (Sec. 1)",
+     "const double thr = p->model == 0 ? 0.5 * (p->rho_l + p->rho_g) : 0.0;",
+     "const double thr = p->model == 0 ? 0.5 * p->rho_l : 0.0;"),
+    ("liquid-gas liquid fraction measured from rho_l instead of rho_g",
+     "vol += p->model == 0 ? (q - p->rho_g) / (p->rho_l - p->rho_g) : 0.5 * (q + 1.0);",
+     "vol += p->model == 0 ? (p->rho_l - q) / (p->rho_l - p->rho_g) : 0.5 * (q + 1.0);"),
 ]
 
 

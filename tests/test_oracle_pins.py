@@ -239,9 +239,16 @@ def test_uniform_fluid_in_capillary_stays_at_rest():
 # ------------------------------------------------ continuum limits (Eqs. 9, 15)
 
 
-@pytest.mark.parametrize("model,phi0,nu", [("binary", 1.0, 0.1), ("binary", -1.0, 0.02), ("lg", None, 1 / 6)])
+@pytest.mark.parametrize("model,phi0,nu", [("binary", 1.0, 0.1), ("binary", -1.0, 0.02), ("lg", None, 1 / 6),
+                                           # the interior of Eq. (nu): nu_g + (phi + 1)/2 (nu_l - nu_g)
+                                           ("binary", 0.0, 0.06), ("binary", 0.5, 0.08)])
 def test_shear_wave_decays_at_the_viscosity_of_omega(model, phi0, nu):
-    """Eq. (nsfinal2) with omega = 2/(6 nu + 1): u_x = U sin(k y) decays as exp(-nu k^2 t)."""
+    """Eq. (nsfinal2) with omega = 2/(6 nu + 1): u_x = U sin(k y) decays as exp(-nu k^2 t).
+
+    In the binary model nu follows phi by Eq. (nu), linear between nu_g = 0.02 (phi = -1)
+    and nu_l = 0.1 (phi = 1); a uniform phi = 0 or 0.5 is a (slowly unstable) equilibrium
+    of the phi^4 free energy that the shear flow leaves uniform, so the wave decays at the
+    interpolated viscosity: 0.06 and 0.08."""
     ny = 64
     p = W.binary_params(nu_l=0.1, nu_g=0.02) if model == "binary" else W.lg_params()
     o = oracle.Oracle(W.periodic_box(4, ny, p))
@@ -477,6 +484,34 @@ def test_filled_length_on_known_fields():
     tube = slice(16, 56)
     assert abs(d["l_vol"] - np.sum((phi[2:10, tube] + 1) / 2) / 8) < 1e-12
     assert abs(d["mass"] - np.sum(np.where(o.node_kinds() < 2, 1.0, 0.0))) < 1e-9
+
+
+def test_liquid_gas_filled_length_on_known_fields():
+    """The liquid-gas branch of l(t) (Sec. 1): the meniscus is where rho crosses
+    (rho_l + rho_g)/2 along the middle row, and the liquid fraction is
+    (rho - rho_g)/(rho_l - rho_g).  Two fields with known answers:
+    - a step, liquid (rho_l) in the first 17 tube columns and gas (rho_g) after them:
+      the middle-row crossing lies half way between the last liquid and the first gas
+      column (l = 16.5), the filled volume is 17 columns, and the mass counts every
+      fluid node at its density;
+    - a linear ramp through the midpoint density at x* = x0 + 13.3: l = 13.3 exactly."""
+    p = W.lg_params()
+    x0, L, H = 16, 40, 8
+    cap = W.Capillary("lgl", 64, 12, x0, L, 2, H, 4, 4, p, wall_grad=0.0)
+    o = oracle.Oracle(cap)
+    x = np.arange(64)[None, :] * np.ones((12, 1))
+    z = np.zeros_like(x)
+    rho = np.where(x < x0 + 17, p.rho_l, p.rho_g)
+    o.init_fields(rho, z, z)
+    d = o.filled_length()
+    assert abs(d["l"] - 16.5) < 1e-12
+    assert abs(d["l_vol"] - 17.0) < 1e-12
+    fluid = o.node_kinds() < 2
+    assert abs(d["mass"] - rho[fluid].sum()) < 1e-9
+    mid = 0.5 * (p.rho_l + p.rho_g)
+    ramp = np.clip(mid - (x - (x0 + 13.3)) * 0.1, p.rho_g, p.rho_l)
+    o.init_fields(ramp, z, z)
+    assert abs(o.filled_length()["l"] - 13.3) < 1e-12
 
 
 # ------------------------------------------------------- capillary dynamics
