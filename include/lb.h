@@ -26,8 +26,8 @@
  *     the default stream).  lb_step returns without waiting; every call that
  *     returns data to the host waits for the stream.
  *   - After LB_ERR_NONFINITE or LB_ERR_TIMEOUT, lb_step and lb_autotune return
- *     LB_ERR_STATE until the state is replaced (lb_init_fields or
- *     lb_set_populations, which clear the condition); the reading calls
+ *     LB_ERR_STATE until the state is replaced (lb_init_fields,
+ *     lb_set_populations or lb_load_state, which clear the condition); the reading calls
  *     (lb_fields, lb_get_populations, lb_get_moments, lb_filled_length),
  *     lb_last_error and lb_destroy remain available.
  *
@@ -192,8 +192,17 @@ size_t lb_state_bytes(const lb_ctx *ctx);
 lb_status lb_save_state(lb_ctx *ctx, void *host, size_t bytes);
 lb_status lb_load_state(lb_ctx *ctx, const void *host, size_t bytes, long time);
 
-/* Wait for all work issued on the context's stream. */
+/* Wait for all work issued on the context's stream; LB_ERR_TIMEOUT if a
+ * device-side wait of the step kernel gave up since the state was set. */
 lb_status lb_sync(lb_ctx *ctx);
+
+/* Failure injection on the host, for tests of the recovery path: marks the
+ * context's device error word exactly as a staged-kernel wait that gave up
+ * marks it, with no kernel running.  The next call that waits (lb_sync,
+ * lb_filled_length) returns LB_ERR_TIMEOUT and poisons the context; a new
+ * state (lb_init_fields, lb_set_populations, lb_load_state) clears both the
+ * word and the condition.  Waits for the stream. */
+lb_status lb_inject_wait_timeout(lb_ctx *ctx);
 
 /* Time steps taken since the last initialisation. */
 long lb_time(const lb_ctx *ctx);
@@ -333,15 +342,20 @@ const char *lb_batch_last_error(const lb_batch *b);
  * different streams or from different host threads without ordering) race on
  * the scratch and may return wrong values: issue them in order on one stream.
  *
- * The first call on a device looks up the scratch array's device address on the
- * device current at that time (cudaGetSymbolAddress) and keeps it for later
- * calls; make that first call before any stream capture begins.
+ * The first call in a CUDA context looks up the scratch array's device address
+ * in that context (cudaGetSymbolAddress on the current device) and keeps it,
+ * keyed by the device and the context's unique ID, for later calls; make that
+ * first call before any stream capture begins.  A call made in another
+ * context of the same device (after cudaDeviceReset, or under a context the
+ * caller made current through the driver API) sees a different ID and looks
+ * the address up again, so the same rule applies to its first call there.
  *
  * Asynchronous on stream (a cudaStream_t or NULL); out is valid once the stream
  * reaches the call.  No NaN check is made (there is no context to poison):
  * inspect mass and phi_sum.  Returns LB_ERR_ARG for a NULL required pointer, an
- * invalid geometry, model or storage, or nblocks out of range, and LB_ERR_CUDA
- * if the device query, the address lookup or a kernel launch fails.
+ * invalid geometry, model or storage, nblocks out of range, or (liquid-gas
+ * model) densities that are not finite with rho_l > rho_g, and LB_ERR_CUDA if
+ * the device or context query, the address lookup or a kernel launch fails.
  * ------------------------------------------------------------------------ */
 #define LB_NOALLOC_MAX_BLOCKS 2048
 

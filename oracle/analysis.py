@@ -111,7 +111,8 @@ def binary_contact_angle(wall_grad, A=0.04, kappa=0.04):
 def binary_wall_gradient_for_angle(theta_deg, A=0.04, kappa=0.04):
     c = math.cos(math.radians(theta_deg))
     lim = math.sqrt(A / (2.0 * kappa))  # Omega = 1
-    return optimize.brentq(lambda g: binary_cos_theta(g, A, kappa) - c, -lim + 1e-12, lim - 1e-12)
+    return optimize.brentq(lambda g: binary_cos_theta(g, A, kappa) - c, -lim + 1e-12, lim - 1e-12,
+                           xtol=1e-16, rtol=8.9e-16, maxiter=500)
 
 
 def binary_profile(x, A=0.04, kappa=0.04):

@@ -20,7 +20,7 @@ using namespace lbk;
 namespace {
 
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
-constexpr int kRedParts = 152 * 4;
+constexpr int kRedPartsPerSM = 4;  // blocks of the first reduction pass per SM
 
 thread_local char g_create_err[512] = "";
 
@@ -40,6 +40,7 @@ struct lb_ctx {
   long t;
   long fluid;
   double* partials;
+  int nparts;    // blocks of the first reduction pass (partials holds nparts x RED_PARTS)
   double* red_out;
   int tile_x, tile_y;
   int kernel;   // 0 auto, 1 sliding window, 2 staged
@@ -144,6 +145,12 @@ static lb_status check_device_error(lb_ctx* c) {
   return LB_OK;
 }
 
+// A new state clears a timed-out condition: the device error word as well as the
+// host flag, or the next waiting call would report the old timeout again.
+static cudaError_t clear_device_error(lb_ctx* c) {
+  return cudaMemsetAsync(c->errflag, 0, sizeof(int), c->stream);
+}
+
 static lb_status launch_one(lb_ctx* c, cudaStream_t s, int from) {
   OpArgs a = base_args(c);
   a.src = c->buf[from];
@@ -243,6 +250,7 @@ static lb_status upload_and_init(lb_ctx* c, const double* rho, const double* ux,
     a.in3 = d + 3 * N;
     a.in_cols = cols;
     cudaError_t e = c->ops(OP_INIT, a, c->stream);
+    if (e == cudaSuccess) e = clear_device_error(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       set_err(c, "init failed: %s", cudaGetErrorString(e));
@@ -330,7 +338,8 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
       return LB_ERR_CUDA;
     }
   }
-  c->partials = (double*)dev_alloc_owned(c, kRedParts * RED_PARTS * sizeof(double));
+  c->nparts = kRedPartsPerSM * device_sm_count();
+  c->partials = (double*)dev_alloc_owned(c, (size_t)c->nparts * RED_PARTS * sizeof(double));
   c->red_out = (double*)dev_alloc_owned(c, 4 * sizeof(double));
   c->errflag = (int*)dev_alloc_owned(c, 256);
   if (c->errflag && cudaMemsetAsync(c->errflag, 0, 256, c->stream) != cudaSuccess) c->errflag = NULL;
@@ -430,7 +439,7 @@ lb_status lb_filled_length(lb_ctx* c, double* l_centre, double* l_vol, double* m
   if (!c) return LB_ERR_ARG;
   OpArgs a = base_args(c);
   a.src = c->buf[c->cur];
-  a.nparts = kRedParts;
+  a.nparts = c->nparts;
   a.partials = c->partials;
   a.red_out = c->red_out;
   CK(c->ops(OP_RED_PARTIALS, a, c->stream));
@@ -490,6 +499,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, const double* g) {
   a.in0 = d;
   a.in1 = bin ? d + 9 * N : NULL;
   if (e == cudaSuccess) e = c->ops(OP_POPS_IN, a, c->stream);
+  if (e == cudaSuccess) e = clear_device_error(c);
   cudaError_t e2 = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = e2;
   dev_free(c, d);
@@ -531,6 +541,7 @@ lb_status lb_load_state(lb_ctx* c, const void* host, size_t bytes, long time) {
   CK(cudaMemcpyAsync(b.f, h, fb, cudaMemcpyHostToDevice, c->stream));
   if (gb) CK(cudaMemcpyAsync(b.g, h + fb, gb, cudaMemcpyHostToDevice, c->stream));
   if (g0b) CK(cudaMemcpyAsync(b.g0, h + fb + gb, g0b, cudaMemcpyHostToDevice, c->stream));
+  CK(clear_device_error(c));
   CK(cudaStreamSynchronize(c->stream));
   c->cur = 0;
   c->t = time;
@@ -552,6 +563,14 @@ lb_status lb_get_moments(lb_ctx* c, double* m) {
   if (e == cudaSuccess) e = e2;
   dev_free(c, d);
   if (e != cudaSuccess) return set_err(c, "lb_get_moments: %s", cudaGetErrorString(e)), LB_ERR_CUDA;
+  return LB_OK;
+}
+
+lb_status lb_inject_wait_timeout(lb_ctx* c) {
+  if (!c) return LB_ERR_ARG;
+  const int one = 1;
+  CK(cudaMemcpyAsync(c->errflag, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return LB_OK;
 }
 

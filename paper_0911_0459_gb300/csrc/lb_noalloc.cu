@@ -7,7 +7,10 @@
 // file-scope array below instead, so it needs no context and calls no
 // allocator.  Every GPU that loads the library holds the array
 // (LB_NOALLOC_MAX_BLOCKS x 4 doubles) until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <math.h>
 
 #include <mutex>
 
@@ -20,19 +23,69 @@ static __device__ __align__(256) double lb_noalloc_partials[LB_NOALLOC_MAX_BLOCK
 
 constexpr int kMaxDevices = 256;
 std::mutex g_mu;
-double* g_scratch[kMaxDevices];  // device address of lb_noalloc_partials, per device
+// Device address of lb_noalloc_partials per device, with the unique ID of the
+// context it was looked up in: a module's symbols get new addresses in a new
+// context (after cudaDeviceReset, or in a context made current through the
+// driver API), so an address is reused only in the context that produced it.
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  double* addr;
+};
+ScratchEntry g_scratch[kMaxDevices];
 
-// Resolve the device address of the scratch array on the current device, once.
+// The two driver functions that identify the current context, taken from the
+// driver through the runtime (the library does not link the driver library
+// itself, so that it still loads on a machine without a GPU driver).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current;
+CtxGetIdFn g_ctx_get_id;
+
+lb_status driver_functions() {  // called with g_mu held
+  if (g_ctx_get_current && g_ctx_get_id) return LB_OK;
+  void* a = nullptr;
+  void* b = nullptr;
+  cudaDriverEntryPointQueryResult qa, qb;
+  if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+      cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+      qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+    return LB_ERR_CUDA;
+  g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+  g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(b);
+  return LB_OK;
+}
+
+lb_status current_context_id(unsigned long long* id, bool* have) {  // called with g_mu held
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return LB_ERR_CUDA;
+  *have = ctx != nullptr;
+  if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return LB_ERR_CUDA;
+  return LB_OK;
+}
+
+// Resolve the device address of the scratch array in the current context, once
+// per (device, context).
 lb_status scratch_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LB_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
+  lb_status st = driver_functions();
+  if (st != LB_OK) return st;
+  unsigned long long id = 0;
+  bool have = false;
+  st = current_context_id(&id, &have);
+  if (st != LB_OK) return st;
+  if (!have || !g_scratch[dev].addr || g_scratch[dev].ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, lb_noalloc_partials) != cudaSuccess || !p) return LB_ERR_CUDA;
-    g_scratch[dev] = static_cast<double*>(p);
+    if (!have) {  // the lookup made the device's primary context current
+      st = current_context_id(&id, &have);
+      if (st != LB_OK || !have) return LB_ERR_CUDA;
+    }
+    g_scratch[dev].ctx_id = id;
+    g_scratch[dev].addr = static_cast<double*>(p);
   }
-  *out = g_scratch[dev];
+  *out = g_scratch[dev].addr;
   return LB_OK;
 }
 
@@ -66,8 +119,15 @@ extern "C" lb_status lb_filled_length_noalloc(const lb_grid* grid, const lb_wall
   if (!geometry_ok(grid, walls)) return LB_ERR_ARG;
   const int bin = params->model == LB_MODEL_BINARY;
   if (!bin && params->model != LB_MODEL_LIQUID_GAS) return LB_ERR_ARG;
+  // population storages only (the moment storage keeps no populations); FP16 is binary only
+  const int st_ok = params->storage == LB_STORAGE_F64 || params->storage == LB_STORAGE_F32 ||
+                    (bin && params->storage == LB_STORAGE_F16DEV);
+  if (!st_ok) return LB_ERR_ARG;
   if (bin && !g) return LB_ERR_ARG;
   if (bin && params->storage == LB_STORAGE_F16DEV && !g0) return LB_ERR_ARG;
+  // the liquid fraction of the liquid-gas model divides by rho_l - rho_g
+  if (!bin && !(isfinite(params->rho_l) && isfinite(params->rho_g) && params->rho_l > params->rho_g))
+    return LB_ERR_ARG;
   double* partials = nullptr;
   lb_status st = scratch_address(&partials);
   if (st != LB_OK) return st;

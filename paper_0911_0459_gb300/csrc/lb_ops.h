@@ -13,6 +13,20 @@ inline bool staged_fits(int nx, int ny) {
   return nx % 8 == 0 && 9ull * (unsigned long long)nx * (unsigned long long)ny < (1ull << 32);
 }
 
+// Streaming multiprocessors of the current device (queried once per device;
+// 152 on GB300, but nothing assumes it).
+inline int device_sm_count() {
+  static int cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (cache[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL, OP_MOMENTS_OUT };
 
 struct OpBufs {

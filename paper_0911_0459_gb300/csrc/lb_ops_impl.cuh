@@ -33,9 +33,12 @@ static inline unsigned tiles_1d(int ncb, int ny, int yc) {
   return (unsigned)ncb * (unsigned)((ny + yc - 1) / yc);
 }
 
+// Grid of a grid-stride kernel over n items: at most 16 blocks per SM of the
+// current device.
 static inline int grid_for(size_t n, int threads) {
+  const size_t cap = 16 * (size_t)device_sm_count();
   size_t b = (n + threads - 1) / threads;
-  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+  return (int)(b > cap ? cap : (b < 1 ? 1 : b));
 }
 
 template <int MODEL, class S, int BX>

@@ -9,7 +9,6 @@ library has not been built, importing a Lattice raises.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 from typing import Optional
 
@@ -81,6 +80,7 @@ def library():
         "lb_get_moments": (C.c_int, [vp, dp]),
         "lb_set_populations": (C.c_int, [vp, dp, dp]),
         "lb_sync": (C.c_int, [vp]),
+        "lb_inject_wait_timeout": (C.c_int, [vp]),
         "lb_state_bytes": (C.c_size_t, [vp]),
         "lb_save_state": (C.c_int, [vp, vp, C.c_size_t]),
         "lb_load_state": (C.c_int, [vp, vp, C.c_size_t, C.c_long]),
@@ -123,7 +123,7 @@ def library():
 
 def exported_symbols():
     return ["lb_create", "lb_destroy", "lb_init_fields", "lb_step", "lb_fields", "lb_filled_length",
-            "lb_get_populations", "lb_set_populations", "lb_get_moments", "lb_sync", "lb_time", "lb_fluid_nodes",
+            "lb_get_populations", "lb_set_populations", "lb_get_moments", "lb_sync", "lb_inject_wait_timeout", "lb_time", "lb_fluid_nodes",
             "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
             "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
             "lb_batch_populations", "lb_batch_moments", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
@@ -153,28 +153,6 @@ class _TorchAllocator:
         self._m = MALLOC_FN(_malloc)
         self._f = FREE_FN(_free)
         self.struct = LbAlloc(self._m, self._f, None)
-
-
-def binary_wall_gradient(theta_deg: float, A: float = 0.04, kappa: float = 0.04) -> float:
-    """Wall gradient d_n phi|_b giving the equilibrium angle theta for the phi^4 model.
-
-    Young's law with Cahn's wall energy -h phi_s (h = -kappa d_n phi|_b) gives
-    cos(theta) = ((1 + W)^1.5 - (1 - W)^1.5) / 2 with W = h / sqrt(kappa A / 2);
-    solved here by bisection.
-    """
-    c = math.cos(math.radians(theta_deg))
-
-    def cosw(w):
-        return 0.5 * ((1 + w) ** 1.5 - (1 - w) ** 1.5)
-    lo, hi = -1.0, 1.0
-    for _ in range(200):
-        mid = 0.5 * (lo + hi)
-        if cosw(mid) < c:
-            lo = mid
-        else:
-            hi = mid
-    w = 0.5 * (lo + hi)
-    return -w * math.sqrt(kappa * A / 2.0) / kappa
 
 
 def _check(status, ctx):
@@ -226,14 +204,7 @@ class Lattice:
     def from_workload(cls, cap, storage=None, **kw):
         """Build from a workloads.Capillary description."""
         p = cap.params
-        if cap.wall_grad is not None:
-            wg = cap.wall_grad
-        elif cap.theta_deg is not None:
-            if p.model != MODEL_BINARY:
-                raise ValueError("liquid-gas workloads must give wall_grad directly")
-            wg = binary_wall_gradient(cap.theta_deg, p.A, p.kappa)
-        else:
-            wg = 0.0
+        wg = cap.wall_gradient()
         return cls(cap.nx, cap.ny, model=p.model, storage=p.storage if storage is None else storage,
                    tube_x0=cap.tube_x0, tube_len=cap.tube_len, tube_y0=cap.tube_y0, tube_h=cap.tube_h,
                    gas_cols=cap.gas_cols, wall_grad=wg, kappa=p.kappa, a=p.a, b=p.b, T=p.T, A=p.A,
@@ -268,6 +239,10 @@ class Lattice:
     def step(self, n=1):
         _check(library().lb_step(self.h, int(n)), self.h)
         return self
+
+    def inject_wait_timeout(self):
+        """Failure injection for tests: mark the device error word as a timed-out wait does."""
+        _check(library().lb_inject_wait_timeout(self.h), self.h)
 
     def sync(self):
         _check(library().lb_sync(self.h), self.h)
@@ -364,14 +339,7 @@ class Lattice:
 def _structs_for(cap, storage=None):
     """lb_grid / lb_walls / lb_params for a workloads.Capillary description."""
     p = cap.params
-    if cap.wall_grad is not None:
-        wg = cap.wall_grad
-    elif cap.theta_deg is not None:
-        if p.model != MODEL_BINARY:
-            raise ValueError("liquid-gas workloads must give wall_grad directly")
-        wg = binary_wall_gradient(cap.theta_deg, p.A, p.kappa)
-    else:
-        wg = 0.0
+    wg = cap.wall_gradient()
     grid = LbGrid(cap.nx, cap.ny)
     walls = LbWalls(cap.tube_x0, cap.tube_len, cap.tube_y0, cap.tube_h, cap.gas_cols, float(wg))
     params = LbParams(p.model, p.storage if storage is None else storage, p.kappa, p.a, p.b, p.T, p.A, p.M,

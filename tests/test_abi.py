@@ -70,12 +70,14 @@ def test_struct_layouts_match_header(libpath, tmp_path):
             assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, (s, f)
 
 
-def test_product_wall_gradient_matches_oracle_closed_form():
+def test_workload_wall_gradient_matches_oracle_closed_form():
+    """The input conversion theta -> d_n phi|_b of the workloads (bisection) and the oracle's
+    own root of the same closed form agree to rounding."""
+    import workloads as W
     from oracle import analysis as an
-    from paper_0911_0459_gb300 import binary_wall_gradient
     for th in (30.0, 45.0, 60.0, 80.0):
         for A in (0.03, 0.04, 0.05):
-            assert abs(binary_wall_gradient(th, A, A) - an.binary_wall_gradient_for_angle(th, A, A)) < 1e-10
+            assert abs(W.binary_wall_gradient(th, A, A) - an.binary_wall_gradient_for_angle(th, A, A)) < 1e-14
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
@@ -181,3 +183,48 @@ def test_mlp_create_rejects_invalid_shapes_before_any_cuda_call(libpath):
         st = L.lb_mlp_create(*shape, 0, None, None, ctypes.byref(out))
         assert st == lb.LB_ERR_ARG and out.value is None, shape
         assert L.lb_mlp_last_error(None).decode()
+
+
+def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
+    """lb_filled_length_noalloc checks its arguments on the host and returns LB_ERR_ARG
+    before its first CUDA call (so this runs without a GPU; the device pointers below are
+    never dereferenced): NULL pointers, block counts outside [1, LB_NOALLOC_MAX_BLOCKS],
+    the moment storage (it keeps no populations), a liquid-gas lattice in FP16, a binary
+    call without g, an FP16 call without g0, and liquid-gas densities that are not finite
+    with rho_l > rho_g (its liquid fraction divides by rho_l - rho_g)."""
+    import workloads as W
+    from paper_0911_0459_gb300 import lb
+    lib = lb.library()
+    fn = lib.lb_filled_length_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(lb.LbGrid), ctypes.POINTER(lb.LbWalls), ctypes.POINTER(lb.LbParams),
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    fake = ctypes.c_void_p(0x1000)
+    binary = W.Capillary("v", 96, 24, 24, 64, 3, 18, 8, 6, W.binary_params(), theta_deg=45.0)
+    lg = W.config_lg_256x32()
+
+    def call(cap, f=fake, g=fake, g0=fake, nblocks=64, out=fake, **edit):
+        gr, w, p = lb._structs_for(cap)
+        for k, v in edit.items():
+            setattr(p, k, v)
+        return fn(ctypes.byref(gr), ctypes.byref(w), ctypes.byref(p), f, g, g0, nblocks, out, None)
+
+    cases = {
+        "f NULL": call(binary, f=None),
+        "out NULL": call(binary, out=None),
+        "no blocks": call(binary, nblocks=0),
+        "too many blocks": call(binary, nblocks=2049),
+        "moment storage": call(binary, storage=lb.STORAGE_MOMENTS),
+        "unknown storage": call(binary, storage=7),
+        "liquid-gas in FP16": call(lg, storage=lb.STORAGE_F16DEV),
+        "binary without g": call(binary, g=None),
+        "FP16 without g0": call(binary, g0=None, storage=lb.STORAGE_F16DEV),
+        "rho_l == rho_g": call(lg, rho_l=3.0, rho_g=3.0),
+        "rho_l < rho_g": call(lg, rho_l=2.59, rho_g=4.54),
+        "rho_l NaN": call(lg, rho_l=float("nan")),
+        "rho_g infinite": call(lg, rho_g=float("-inf")),
+        "unknown model": call(binary, model=5),
+    }
+    bad = {k: v for k, v in cases.items() if v != lb.LB_ERR_ARG}
+    assert not bad, bad

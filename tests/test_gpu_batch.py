@@ -153,7 +153,7 @@ def test_batch_sampled_run_matches_oracle():
     out = b.run_sampled(at)
     assert out.shape == (4, 5, 4)
     for i, c in enumerate(caps):
-        orc = oracle.Oracle(c, wall_grad=lbmod.binary_wall_gradient(c.theta_deg, c.params.A, c.params.kappa))
+        orc = oracle.Oracle(c)
         orc.init_default()
         t = 0
         for k, s in enumerate(at):
@@ -231,7 +231,7 @@ def test_full_sweep_of_256_capillaries_in_the_benchmarked_configuration(storage)
             fl, gl = lat.populations(rested=False)
             assert np.array_equal(fb, fl) and np.array_equal(gb, gl), i
         if i == int(np.argmin(sizes)):
-            orc = oracle.Oracle(caps[i], wall_grad=lat.walls.wall_grad).init_default().step(b.time)
+            orc = oracle.Oracle(caps[i]).init_default().step(b.time)
             g, o = lat.fields(), orc.fields()
             assert max(np.abs(g[0] - o[0]).max(), np.abs(g[3] - o[3]).max()) < 1e-4
             assert abs(lat.filled_length()["l"] - orc.filled_length()["l"]) < 0.05

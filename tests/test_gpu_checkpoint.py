@@ -62,6 +62,44 @@ def test_lattice_checkpoint_resumes_bit_for_bit(storage, tmp_path):
         x.close()
 
 
+@pytest.mark.parametrize("route", ["load_state", "set_populations", "init_fields"])
+def test_a_new_state_clears_a_timed_out_condition(route):
+    """A device-side wait that gave up (injected on the host: the context's error word is
+    set as the staged kernel sets it) makes the next waiting call return LB_ERR_TIMEOUT and
+    refuses steps; each way of giving the lattice a new state clears the word as well as
+    the condition, after which reductions and steps work and the run is the saved one."""
+    from paper_0911_0459_gb300 import lb as lbmod
+    cap = capillary(STORAGE_F32)
+    a = Lattice.from_workload(cap)
+    a.step(20)
+    saved, t = a.save_state()
+    f, g = a.populations(False)
+    a.step(10)
+    ref, _ = a.save_state()
+    a.load_state(saved, t)
+    a.inject_wait_timeout()
+    with pytest.raises(LbError) as e:
+        a.filled_length()
+    assert e.value.status == lbmod.LB_ERR_TIMEOUT
+    with pytest.raises(LbError) as e:
+        a.step(1)
+    assert e.value.status == lbmod.LB_ERR_STATE
+    if route == "load_state":
+        a.load_state(saved, t)
+    elif route == "set_populations":
+        a.set_populations(f, g)
+    else:
+        a.init_fields(*W.initial_fields(cap))
+    a.sync()
+    a.filled_length()               # the old timeout is not reported again
+    a.filled_length()
+    a.step(10)
+    if route == "load_state":
+        assert np.array_equal(a.save_state()[0], ref)
+    assert np.isfinite(a.filled_length()["mass"])
+    a.close()
+
+
 def test_liquid_gas_checkpoint_resumes_bit_for_bit():
     cap = W.config_lg_256x32()
     a = Lattice.from_workload(cap)

@@ -78,7 +78,7 @@ TILES = ((64, 1), (128, 5), (256, 16), (64, 1000))
 
 def pair(cap, fields):
     lat = Lattice.from_workload(cap, storage=STORAGE_MOMENTS)
-    orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad)
+    orc = oracle.Oracle(cap)
     lat.init_fields(*fields)
     orc.init_fields(*fields)
     return lat, orc
@@ -128,7 +128,7 @@ def test_2000_steps_of_a_filling_capillary_stay_within_the_method_tolerance():
     cap = W.Capillary("f", 300, 30, 60, 230, 4, 22, 20, 10, W.binary_params(nu_l=0.5, nu_g=0.05),
                       theta_deg=45.0)
     lat = Lattice.from_workload(cap, storage=STORAGE_MOMENTS)
-    orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad)
+    orc = oracle.Oracle(cap)
     orc.init_default()
     lat.step(2000)
     orc.step(2000)
@@ -162,7 +162,7 @@ def test_full_size_16384x256_one_step_from_gpu_state():
     lat.autotune()
     lat.step(200)
     f, g = populations_with(lat.moments())
-    orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad)
+    orc = oracle.Oracle(cap)
     orc.set_populations(f, g, apply_rest=True)
     del f, g
     kinds = orc.node_kinds()

@@ -33,7 +33,7 @@ STEP_TOL = {STORAGE_F64: 1e-11, STORAGE_F32: 2e-6, STORAGE_F16DEV: 1e-4}
 
 def pair(cap, storage=None, fields=None):
     lat = Lattice.from_workload(cap, storage=storage)
-    orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad)
+    orc = oracle.Oracle(cap)
     if fields is None:
         orc.init_default()
     else:
@@ -117,7 +117,7 @@ def test_default_initial_state_matches_workload_fields():
     for cap in (W.config_lg_256x32(), W.Capillary("b", 200, 30, 50, 120, 4, 22, 16, 10,
                                                   W.binary_params(), theta_deg=50.0)):
         lat = Lattice.from_workload(cap)
-        orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad).init_default()
+        orc = oracle.Oracle(cap).init_default()
         fg, gg = lat.populations()
         fo, go = orc.populations()
         tol = 1e-12 if cap.params.storage == STORAGE_F64 else 2e-7
@@ -202,7 +202,7 @@ def test_full_size_16384x256_one_step_from_gpu_state(storage):
     lat.autotune()
     lat.step(200)
     f0, g0 = lat.populations(rested=False)
-    orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad)
+    orc = oracle.Oracle(cap)
     orc.set_populations(f0, g0, apply_rest=True)
     del f0, g0
     lat.step(1)

@@ -35,7 +35,7 @@ def test_one_step_with_a_viscosity_table_matches_oracle(K, storage):
     cap = W.Capillary("t", 203, 37, 61, 120, 5, 27, 12, 8, p, wall_grad=-0.11)
     fields = W.random_state_fields(cap.nx, cap.ny, seed=11, model=W.BINARY)
     lat = Lattice.from_workload(cap, storage=storage).init_fields(*fields)
-    orc = oracle.Oracle(cap, wall_grad=lat.walls.wall_grad).init_fields(*fields)
+    orc = oracle.Oracle(cap).init_fields(*fields)
     lat.step(1)
     orc.step(1)
     kinds = orc.node_kinds()
@@ -45,8 +45,8 @@ def test_one_step_with_a_viscosity_table_matches_oracle(K, storage):
     assert d.max() < 2e-6
     # and the table is in use: the exact viscosity gives a different step
     exact = oracle.Oracle(W.Capillary("t", 203, 37, 61, 120, 5, 27, 12, 8,
-                                      W.binary_params(nu_l=0.7, nu_g=0.05, M=0.2), wall_grad=-0.11),
-                          wall_grad=lat.walls.wall_grad).init_fields(*fields).step(1)
+                                      W.binary_params(nu_l=0.7, nu_g=0.05, M=0.2), wall_grad=-0.11)
+                          ).init_fields(*fields).step(1)
     assert np.abs(moments_of(*exact.populations()) - moments_of(*orc.populations())).max() > 1e-5
 
 

@@ -118,3 +118,40 @@ def test_noalloc_reads_the_fp16_deviation_layout():
     ref = lat.filled_length()
     for k, v in zip(("l", "l_vol", "mass", "phi_sum"), out.cpu().numpy()):
         assert abs(v - ref[k]) <= 1e-9 * max(1.0, abs(ref[k])), (k, v, ref[k])
+
+
+def test_noalloc_wrapped_liquid_gas_tube_and_argument_errors():
+    """A liquid-gas FP32 state whose tube starts at a nonzero offset and wraps through
+    x = 0 (with a y offset) gives lb_filled_length's values; the header's argument errors
+    (moment storage, binary without g, FP16 without g0) return LB_ERR_ARG with real
+    device pointers too, and leave the output untouched."""
+    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_MOMENTS
+    cap = W.Capillary("lw", 160, 24, 120, 100, 3, 18, 8, 10, W.lg_params(storage=STORAGE_F32), wall_grad=-0.1)
+    lat = Lattice.from_workload(cap)
+    lat.step(57)
+    fd, _ = device_state(lat, STORAGE_F32)
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    assert call(lat, fd, None, 96, out) == lbmod.LB_OK
+    torch.cuda.synchronize()
+    check(out.cpu().numpy(), lat.filled_length())
+    lat.close()
+    binary = W.Capillary("nb", 300, 36, 60, 230, 4, 28, 20, 10, W.binary_params(), theta_deg=50.0)
+    b = Lattice.from_workload(binary)
+    fb, gb = device_state(b, STORAGE_F32)
+    sentinel = torch.full((4,), 7.0, dtype=torch.float64, device="cuda")
+    fn = noalloc_fn()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def status(params, g, g0):
+        return fn(C.byref(b.grid), C.byref(b.walls), C.byref(params), C.c_void_p(fb.data_ptr()), g, g0, 64,
+                  C.c_void_p(sentinel.data_ptr()), stream)
+    pm = lbmod.LbParams.from_buffer_copy(b.params)
+    pm.storage = STORAGE_MOMENTS
+    assert status(pm, C.c_void_p(gb.data_ptr()), None) == lbmod.LB_ERR_ARG
+    assert status(b.params, None, None) == lbmod.LB_ERR_ARG
+    ph = lbmod.LbParams.from_buffer_copy(b.params)
+    ph.storage = STORAGE_F16DEV
+    assert status(ph, C.c_void_p(gb.data_ptr()), None) == lbmod.LB_ERR_ARG
+    torch.cuda.synchronize()
+    assert (sentinel.cpu().numpy() == 7.0).all()
+    b.close()

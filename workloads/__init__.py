@@ -88,6 +88,40 @@ class Capillary:
     def nodes(self) -> int:
         return self.nx * self.ny
 
+    def wall_gradient(self) -> float:
+        """The wall gradient this workload gives the library: wall_grad when set, else (binary
+        model) the one that makes theta_deg the equilibrium angle, else 0."""
+        if self.wall_grad is not None:
+            return float(self.wall_grad)
+        if self.theta_deg is None:
+            return 0.0
+        if self.params.model != BINARY:
+            raise ValueError("liquid-gas workloads must give wall_grad directly")
+        return binary_wall_gradient(self.theta_deg, self.params.A, self.params.kappa)
+
+
+def binary_wall_gradient(theta_deg: float, A: float = 0.04, kappa: float = 0.04) -> float:
+    """Input conversion: the wall gradient d_n phi|_b (inward normal) that sets the
+    equilibrium contact angle theta of the phi^4 binary model (Sec. 3.2).
+
+    Cahn's wall energy -h phi_s with h = -kappa d_n phi|_b and Young's law give
+    cos(theta) = ((1 + W)^1.5 - (1 - W)^1.5) / 2, W = h / sqrt(kappa A / 2); W is
+    found by bisection on [-1, 1], where the right-hand side increases.
+    """
+    c = math.cos(math.radians(theta_deg))
+
+    def cos_of(w):
+        return 0.5 * ((1.0 + w) ** 1.5 - (1.0 - w) ** 1.5)
+    lo, hi = -1.0, 1.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if cos_of(mid) < c:
+            lo = mid
+        else:
+            hi = mid
+    w = 0.5 * (lo + hi)
+    return -w * math.sqrt(kappa * A / 2.0) / kappa
+
 
 # ---------------------------------------------------------------------------
 # The paper-shaped workloads.
