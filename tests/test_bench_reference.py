@@ -20,6 +20,12 @@ def test_reference_arm_prints_one_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the same workload object as the GPU arm's line
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    assert d["config"] == bench.bench_config(W.config_binary_16384x256(), 1)
+    assert d["metric"] == bench.METRIC
 
 
 def test_bench_options():
