@@ -223,13 +223,15 @@ def cpu_baseline(sample_steps=2000, copy_steps=500):
 
 def precision_report(Lattice, orc, steps):
     """Error of each storage against the FP64 oracle on the crop after `steps` steps."""
-    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STORAGE_MOMENTS
+    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_GELIM, STORAGE_F64, STORAGE_MOMENTS,
+                                       STORAGE_MOMENTS_F16)
     rho_o, _, _, phi_o = orc.fields()
     l_o = orc.filled_length()["l"]
     out = {"workload": "1024x64 crop of the large capillary, default initial state", "steps": steps}
     import dataclasses
     for name, st, table in (("f64", STORAGE_F64, 0), ("f32", STORAGE_F32, 0), ("f16dev", STORAGE_F16DEV, 0),
-                            ("moments_f32", STORAGE_MOMENTS, 0), ("f32_nu_table_1e4", STORAGE_F32, 10000)):
+                            ("moments_f32", STORAGE_MOMENTS, 0), ("moments_f16", STORAGE_MOMENTS_F16, 0),
+                            ("f32_g_eliminated", STORAGE_F32_GELIM, 0), ("f32_nu_table_1e4", STORAGE_F32, 10000)):
         cap = W.config_binary_crop_1024x64(st)
         cap.params = dataclasses.replace(cap.params, nu_table=table)
         lat = Lattice.from_workload(cap)
@@ -585,24 +587,31 @@ def main():
         secondary["lg_256x32_fp64_us_per_step"] = 1e3 * a.elapsed_time(b) / 1984
         l1.close()
         secondary["binary_2048x64"] = small_capillary_rates(torch, Lattice)
-        # the same large capillary with the state held as six FP32 moments per node
-        cm = W.config_binary_16384x256(STORAGE_MOMENTS)
-        lm = Lattice.from_workload(cm)
-        mtx, mty, _ = lm.autotune()
-        lm.step(8)
-        torch.cuda.synchronize()
-        a.record(lm.stream)
-        lm.step(512)
-        b.record(lm.stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 512
-        gbs = lm.fluid_nodes * 48 / (ms * 1e-3) / 1e9
-        secondary["moments_16384x256"] = {
-            "MLUPS": lm.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "tile": [mtx, mty],
-            "bytes_per_lu": 48, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
-            "what": "moment storage (rho-1, j, pxx-pyy, pxy, phi in FP32), moment_step_kernel, 512 steps, "
-                    "CUDA events; the same update as the FP32 population kernel in exact arithmetic"}
-        lm.close()
+        # the same large capillary with the reduced states of the pull kernel
+        from paper_0911_0459_gb300 import STORAGE_F32_GELIM, STORAGE_MOMENTS_F16
+        for key, st, bpl, what in (
+                ("moments_16384x256", STORAGE_MOMENTS, 48,
+                 "six FP32 moments per node (rho-1, j, pxx-pyy, pxy, phi)"),
+                ("moments_f16_16384x256", STORAGE_MOMENTS_F16, 28,
+                 "FP16 rho-1, j, pxx-pyy, pxy and FP32 phi per node"),
+                ("g_eliminated_16384x256", STORAGE_F32_GELIM, 80,
+                 "nine FP32 f populations and phi per node (g replaced by phi)")):
+            lm = Lattice.from_workload(W.config_binary_16384x256(st))
+            mtx, mty, _ = lm.autotune()
+            lm.step(8)
+            torch.cuda.synchronize()
+            a.record(lm.stream)
+            lm.step(512)
+            b.record(lm.stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 512
+            gbs = lm.fluid_nodes * bpl / (ms * 1e-3) / 1e9
+            secondary[key] = {
+                "MLUPS": lm.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "tile": [mtx, mty],
+                "bytes_per_lu": bpl, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
+                "what": what + "; the pull kernel (moment_step_kernel), 512 steps, CUDA events; the same "
+                               "update as the FP32 population kernel in exact arithmetic"}
+            lm.close()
     except Exception as ex:  # secondary numbers never block the headline line
         secondary["error"] = repr(ex)
     if not args.no_batch:

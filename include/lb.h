@@ -80,12 +80,25 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
  * lb_get_moments reads the state), and lb_set_populations stores their
  * moments.  The density is held as rho - 1 (the binary model keeps rho near
  * 1), which lb_get_moments, lb_fields and the reductions add back in FP64.  At
- * most 715827882 nodes (6 nx ny < 2^32). */
+ * most 715827882 nodes (6 nx ny < 2^32).
+ *
+ * LB_STORAGE_MOMENTS_F16 (binary model only) keeps the same six moments with
+ * rho - 1, jx, jy, pxx - pyy and pxy in FP16 and phi in FP32 (FP32 arithmetic):
+ * 28 bytes per node update.  Like LB_STORAGE_MOMENTS it keeps no populations.
+ *
+ * LB_STORAGE_F32_GELIM (binary model only) keeps the nine f populations in FP32,
+ * as deviations f_i - w_i from w = 4/9, 1/9, 1/36, and phi in place of the nine
+ * g populations, which all relax fully to g^eq (App. A, Eq. (latbolt2)):
+ * 80 bytes per node update.  lb_get_populations returns f and, for g, the
+ * populations (phi, 0, ..., 0), whose phi is the only moment of g a step uses.
+ * At most 429496729 nodes (10 nx ny < 2^32). */
 typedef enum {
   LB_STORAGE_F64 = 0,
   LB_STORAGE_F32 = 1,
   LB_STORAGE_F16DEV = 2,
-  LB_STORAGE_MOMENTS = 3
+  LB_STORAGE_MOMENTS = 3,
+  LB_STORAGE_MOMENTS_F16 = 4,
+  LB_STORAGE_F32_GELIM = 5
 } lb_storage;
 
 typedef struct {
@@ -174,7 +187,8 @@ lb_status lb_set_populations(lb_ctx *ctx, const double *f, const double *g);
 /* The six moments of the stored state, host array (6, ny, nx) of doubles in
  * the order rho, jx, jy, pxx - pyy, pxy (of f), phi (sum of g; 0 for the
  * liquid-gas model): for the population storages they are summed in FP64
- * from the stored populations, for LB_STORAGE_MOMENTS they are the state.  As
+ * from the stored populations (LB_STORAGE_F32_GELIM: from f, and phi), for the
+ * moment storages they are the state.  As
  * lb_get_populations with rested = 0, boundary nodes are returned before the
  * rest rule (which would set j = 0).  Solid nodes give zeros.  Waits for the
  * stream. */
@@ -182,7 +196,8 @@ lb_status lb_get_moments(lb_ctx *ctx, double *m);
 
 /* Checkpoints: the stored state exactly as the storage holds it (the f
  * planes, then the g planes, then the FP32 g_0 plane of LB_STORAGE_F16DEV; for
- * LB_STORAGE_MOMENTS the three moment planes), lb_state_bytes bytes in host
+ * the storages advanced by the pull kernel their planes as the device holds
+ * them), lb_state_bytes bytes in host
  * memory the caller owns.  lb_load_state takes such bytes from a lattice of the
  * same grid, walls and params (LB_ERR_ARG if the size differs), sets the step
  * counter to time and clears a non-finite or timed-out condition; the
@@ -221,8 +236,9 @@ lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
  * registers), 2 = staged kernel (rows brought into shared memory by bulk
  * copies; fits when nx % 8 == 0 and nx * ny <= 477218588, else LB_ERR_ARG)
  * with its shallow ring of row stages, 3 = staged kernel with its deep ring.
- * All compute the same update bit for bit.  LB_STORAGE_MOMENTS has one kernel
- * of its own (variant 4; 0 and 4 are accepted).  Invalidates the captured step
+ * All compute the same update bit for bit.  LB_STORAGE_MOMENTS,
+ * LB_STORAGE_MOMENTS_F16 and LB_STORAGE_F32_GELIM have one kernel of their own,
+ * the pull kernel over the reduced state (variant 4; 0 and 4 are accepted).  Invalidates the captured step
  * graph. */
 lb_status lb_set_kernel(lb_ctx *ctx, int variant);
 /* The kernel variant in use (1, 2, 3 or 4; automatic selection resolved). */
@@ -248,7 +264,9 @@ const char *lb_last_error(const lb_ctx *ctx);
 typedef struct lb_batch lb_batch;
 
 /* n lattices, each described as for lb_create (all binary, one common
- * storage), each set to the default initial state.  *out set only on LB_OK. */
+ * storage: LB_STORAGE_F64, LB_STORAGE_F32, LB_STORAGE_F16DEV or
+ * LB_STORAGE_MOMENTS), each set to the default initial state.  *out set only on
+ * LB_OK. */
 lb_status lb_batch_create(int n, const lb_grid *grids, const lb_walls *walls, const lb_params *params,
                           const lb_alloc *alloc, void *stream, lb_batch **out);
 void lb_batch_destroy(lb_batch *b);

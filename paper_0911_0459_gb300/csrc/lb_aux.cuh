@@ -37,7 +37,12 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
     if (is_solid(G, x, y)) {
       if constexpr (is_moments<S>::value) {
         const float z[M_PLANES] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        mom_store(B.f, N, n, z);
+        if constexpr (pull_kind<S>::value == 2) {
+          const float zf[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          sg_store(B.f, N, n, zf, 0.f);
+        } else {
+          pull_store_moments<S>(B.f, N, n, z);
+        }
       } else {
         // zero bits in every plane (with the FP16 offsets a stored 0 would not be),
         // the same as a fresh buffer: no step reads or writes a solid node
@@ -77,16 +82,41 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
       feq9<A>(rho, jx, jy, ux, uy, p0 - P.kappa * rho * rlap, P.kappa, rdx, rdy, rdx, rdy, P.lambda_scale * P.nu, fe);
     }
     if constexpr (is_moments<S>::value) {
-      A m[M_PLANES];
-      pops_to_moments(fe, ge, m);
-      m[M_RHO] = (A)(rho_in[nin] - 1.0);  // stored as rho - 1
-      mom_store(B.f, N, n, m);
+      if constexpr (pull_kind<S>::value == 2) {
+        // f as deviations from the rest weights (exact: f^eq_i and w_i are close), phi
+        float fd[9];
+        for (int i = 0; i < 9; ++i) fd[i] = fe[i] - (float)WREST(i);
+        sg_store(B.f, N, n, fd, (float)phi_in[nin]);
+      } else {
+        A m[M_PLANES];
+        pops_to_moments(fe, ge, m);
+        m[M_RHO] = (A)(rho_in[nin] - 1.0);  // stored as rho - 1
+        pull_store_moments<S>(B.f, N, n, m);
+      }
     } else {
       for (int i = 0; i < 9; ++i) {
         S::sf(B.f, N, n, i, fe[i], B.r);
         if (BIN) S::sg(B.g, B.g0, N, n, i, ge[i]);
       }
     }
+  }
+}
+
+// The six moments of node n of a pull-kernel storage in FP64 (rho as rho - 1):
+// read (SM32, SM16) or summed in FP64 from the f deviations (SG32).
+template <class S>
+__device__ __forceinline__ void pull_moments_f64(const void* base, size_t N, size_t n, double m[M_PLANES]) {
+  if constexpr (pull_kind<S>::value == 2) {
+    float fd[9], ph;
+    sg_load(base, N, n, fd, ph);
+    double f[9], g[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 9; ++i) f[i] = (double)fd[i];
+    g[0] = (double)ph;
+    pops_to_moments(f, g, m);
+  } else {
+    float mf[M_PLANES];
+    pull_load<S>(base, N, n, mf);
+    for (int k = 0; k < M_PLANES; ++k) m[k] = (double)mf[k];
   }
 }
 
@@ -118,13 +148,13 @@ __global__ void fields_kernel(Geom G, Buf<S> B, double* __restrict__ rho, double
       }
       bool sol[3][3], bnd;
       neighbour_solids(G, x, y, sol, bnd);
-      float m[M_PLANES];
-      mom_load(B.f, N, n, m);
-      const double r = 1.0 + (double)m[M_RHO];
+      double m[M_PLANES];
+      pull_moments_f64<S>(B.f, N, n, m);
+      const double r = 1.0 + m[M_RHO];
       rho[n] = r;
-      ux[n] = bnd ? 0.0 : (double)m[M_JX] / r;  // rest rule at boundary nodes
-      uy[n] = bnd ? 0.0 : (double)m[M_JY] / r;
-      phi[n] = (double)m[M_PHI];
+      ux[n] = bnd ? 0.0 : m[M_JX] / r;  // rest rule at boundary nodes
+      uy[n] = bnd ? 0.0 : m[M_JY] / r;
+      phi[n] = m[M_PHI];
     } else {
       A f[9], g[9];
       if (!node_state<MODEL, S>(G, B, N, x, y, true, f, g)) {
@@ -146,11 +176,31 @@ __global__ void pops_out_kernel(Geom G, Buf<S> B, int rested, double* __restrict
   const size_t N = (size_t)G.nx * G.ny;
   for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N; n += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
-    A f[9], g[9];
-    const bool fl = node_state<MODEL, S>(G, B, N, x, y, rested != 0, f, g);
-    for (int i = 0; i < 9; ++i) {
-      fo[i * N + n] = fl ? (double)f[i] : 0.0;
-      if (MODEL == MODEL_BINARY && go) go[i * N + n] = fl ? (double)g[i] : 0.0;
+    if constexpr (pull_kind<S>::value == 2) {
+      // the f populations (deviations plus the rest weights, in FP64); for g the
+      // populations (phi, 0, ..., 0), which carry the only moment of g a step uses
+      double f[9], g[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      const bool fl = !is_solid(G, x, y);
+      if (fl) {
+        float fd[9], ph;
+        sg_load(B.f, N, n, fd, ph);
+        for (int i = 0; i < 9; ++i) f[i] = (double)fd[i] + WREST(i);
+        g[0] = (double)ph;
+        bool sol[3][3], bnd;
+        neighbour_solids(G, x, y, sol, bnd);
+        if (rested && bnd) rest(f);
+      }
+      for (int i = 0; i < 9; ++i) {
+        fo[i * N + n] = fl ? f[i] : 0.0;
+        if (go) go[i * N + n] = fl ? g[i] : 0.0;
+      }
+    } else {
+      A f[9], g[9];
+      const bool fl = node_state<MODEL, S>(G, B, N, x, y, rested != 0, f, g);
+      for (int i = 0; i < 9; ++i) {
+        fo[i * N + n] = fl ? (double)f[i] : 0.0;
+        if (MODEL == MODEL_BINARY && go) go[i * N + n] = fl ? (double)g[i] : 0.0;
+      }
     }
   }
 }
@@ -163,17 +213,24 @@ __global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, 
     const int x = (int)(n % G.nx), y = (int)(n / G.nx);
     const bool sol = is_solid(G, x, y);
     if constexpr (is_moments<S>::value) {
-      // moments of the given populations, summed in FP64 and rounded once
+      // moments (or f deviations and phi) of the given populations, formed in
+      // FP64 and rounded once
       double f[9], g[9], m[M_PLANES];
       for (int i = 0; i < 9; ++i) {
         f[i] = fi[i * N + n];
         g[i] = MODEL == MODEL_BINARY ? gi[i * N + n] : 0.0;
       }
-      pops_to_moments(f, g, m);
-      m[M_RHO] -= 1.0;  // stored as rho - 1
-      float mf[M_PLANES];
-      for (int k = 0; k < M_PLANES; ++k) mf[k] = sol ? 0.f : (float)m[k];
-      mom_store(B.f, N, n, mf);
+      if constexpr (pull_kind<S>::value == 2) {
+        float fd[9];
+        for (int i = 0; i < 9; ++i) fd[i] = sol ? 0.f : (float)(f[i] - WREST(i));
+        sg_store(B.f, N, n, fd, sol ? 0.f : (float)sum9(g));
+      } else {
+        pops_to_moments(f, g, m);
+        m[M_RHO] -= 1.0;  // stored as rho - 1
+        float mf[M_PLANES];
+        for (int k = 0; k < M_PLANES; ++k) mf[k] = sol ? 0.f : (float)m[k];
+        pull_store_moments<S>(B.f, N, n, mf);
+      }
     } else {
       for (int i = 0; i < 9; ++i) {
         if (sol)
@@ -198,9 +255,7 @@ __global__ void moments_out_kernel(Geom G, Buf<S> B, double* __restrict__ out) {
     const bool sol = is_solid(G, x, y);
     double m[M_PLANES];
     if constexpr (is_moments<S>::value) {
-      float mf[M_PLANES];
-      mom_load(B.f, N, n, mf);
-      for (int k = 0; k < M_PLANES; ++k) m[k] = (double)mf[k];
+      pull_moments_f64<S>(B.f, N, n, m);
       m[M_RHO] += 1.0;
     } else {
       A fa[9], ga[9];
@@ -244,7 +299,7 @@ __device__ __forceinline__ void red_add_node(const Geom& G, const Buf<S>& B, siz
   using A = typename S::A;
   double r, p;
   if constexpr (is_moments<S>::value) {
-    const float2 v = __ldcg(reinterpret_cast<const float2*>(B.f) + MP_RP * N + n);
+    const float2 v = pull_rho_phi<S>(B.f, N, n);
     r = 1.0 + (double)v.x;
     p = (double)v.y;
   } else {
@@ -283,8 +338,7 @@ __device__ __forceinline__ double centre_value(const Geom& G, const Buf<S>& B, s
   const int x = wrapi(G.tube_x0 + k, G.nx);
   double va = 0.0, vb = 0.0;
   if constexpr (is_moments<S>::value) {
-    const float2* P = reinterpret_cast<const float2*>(B.f) + MP_RP * N;
-    const float2 a = __ldcg(P + (size_t)ya * G.nx + x), b = __ldcg(P + (size_t)yb * G.nx + x);
+    const float2 a = pull_rho_phi<S>(B.f, N, (size_t)ya * G.nx + x), b = pull_rho_phi<S>(B.f, N, (size_t)yb * G.nx + x);
     // binary: phi; liquid-gas: rho (stored as rho - 1)
     va = MODEL == MODEL_BINARY ? (double)a.y : 1.0 + (double)a.x;
     vb = MODEL == MODEL_BINARY ? (double)b.y : 1.0 + (double)b.x;

@@ -452,6 +452,8 @@ static void fill_caps(lb_batch* b, std::vector<CapDesc<A>>& caps) {
     c.off_g = b->off_g[i];
     c.off_g0 = b->off_g0[i];
     c.r = rest_offsets_binary(p.A);
+    c.Q = mom_phys(p.kappa, p.A, p.M, p.nu_l, p.nu_g, p.lambda_scale, w.wall_grad,
+                   p.nu_table >= 2 ? p.nu_table - 1 : 0);
     c.thr = 0.0;
     c.rho_l = p.rho_l;
     c.rho_g = p.rho_g;
@@ -609,6 +611,7 @@ void lb_batch_destroy(lb_batch* b) {
 }
 
 lb_status lb_batch_step(lb_batch* b, long n) {
+  NvtxRange range("lb_batch_step");
   if (!b) return LB_ERR_ARG;
   if (n < 0 || n > (1L << 30)) return berr(b, "step count out of range"), LB_ERR_ARG;
   if (b->poisoned) return berr(b, "batch holds a timed-out state"), LB_ERR_STATE;
@@ -650,6 +653,7 @@ lb_status lb_batch_load_state(lb_batch* b, const void* host, size_t bytes, long 
 }
 
 lb_status lb_batch_lengths(lb_batch* b, double* out) {
+  NvtxRange range("lb_batch_lengths");
   if (!b || !out) return LB_ERR_ARG;
   lb_status st = ensure_out(b, (size_t)b->n * 4);
   if (st) return st;
@@ -660,6 +664,7 @@ lb_status lb_batch_lengths(lb_batch* b, double* out) {
 }
 
 lb_status lb_batch_run_sampled(lb_batch* b, int nsamples, const long* at, double* out) {
+  NvtxRange range("lb_batch_run_sampled");
   if (!b || nsamples < 1 || !at || !out) return LB_ERR_ARG;
   if (b->poisoned) return berr(b, "batch holds a timed-out state"), LB_ERR_STATE;
   long prev = 0;
@@ -789,6 +794,7 @@ lb_status lb_batch_set_tile(lb_batch* b, int tile_x, int tile_y) {
 }
 
 lb_status lb_batch_autotune(lb_batch* b, int steps, int* tile_x, int* tile_y, double* ms_per_step) {
+  NvtxRange range("lb_batch_autotune");
   if (!b || steps < 1) return LB_ERR_ARG;
   if (b->poisoned) return LB_ERR_STATE;
   // tuning runs advance the state: run an even number of steps per candidate and

@@ -22,6 +22,7 @@ struct CapDesc {
   size_t off_g;     // offset of its g planes in the g arena
   size_t off_g0;    // offset of its g_0 plane (FP16 storage)
   Rest r;           // its FP16 deviation offsets
+  MomPhys Q;        // its moment-collision constants (moment storage)
   double thr, rho_l, rho_g;
 };
 
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : (NW == 4 ? 5 : 10)) bat
       const CapDesc<float>& c = a.caps[td.cap];
       const float* src = (fromA ? a.fa : a.fb) + c.off_f;
       float* dst = (fromA ? a.fb : a.fa) + c.off_f;
-      moment_strip<true>(c.G, c.P, src, dst, td.xb + warp * kMomCols, td.y0, td.y1, lane);
+      moment_strip<true, SM32>(c.G, c.Q, src, dst, td.xb + warp * kMomCols, td.y0, td.y1, lane);
     }
     if (!grid_barrier(a.bar, a.expected, a.limit_ns)) {
       if (threadIdx.x == 0) atomicExch(a.err, 1);

@@ -105,6 +105,8 @@ static OpsFn pick_ops(int model, int storage) {
     if (storage == LB_STORAGE_F32) return ops_bin_f32;
     if (storage == LB_STORAGE_F16DEV) return ops_bin_f16;
     if (storage == LB_STORAGE_MOMENTS) return ops_bin_m32;
+    if (storage == LB_STORAGE_MOMENTS_F16) return ops_bin_m16;
+    if (storage == LB_STORAGE_F32_GELIM) return ops_bin_g32;
   }
   return NULL;
 }
@@ -182,9 +184,16 @@ static lb_status build_graph(lb_ctx* c) {
   return LB_OK;
 }
 
+// Storages advanced by the pull kernel (the state is not the eighteen populations).
+static bool pull_storage(int storage) {
+  return storage == LB_STORAGE_MOMENTS || storage == LB_STORAGE_MOMENTS_F16 || storage == LB_STORAGE_F32_GELIM;
+}
+
 static size_t state_bytes(int model, int storage, size_t N, size_t* fb, size_t* gb, size_t* g0b) {
-  if (storage == LB_STORAGE_MOMENTS) {  // six FP32 planes in the f buffer
-    *fb = (size_t)M_PLANES * N * sizeof(float);
+  if (pull_storage(storage)) {  // everything in the f buffer
+    *fb = storage == LB_STORAGE_MOMENTS ? (size_t)M_PLANES * N * sizeof(float)
+        : storage == LB_STORAGE_MOMENTS_F16 ? m16_layout(N).total
+                                            : 10 * N * sizeof(float);
     *gb = 0;
     *g0b = 0;
     return *fb;
@@ -203,6 +212,8 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
   if (!pick_ops(p->model, p->storage)) return set_err(c, "unsupported model/storage pair"), LB_ERR_ARG;
   if (p->storage == LB_STORAGE_MOMENTS && (unsigned long long)M_PLANES * g->nx * g->ny >= (1ull << 32))
     return set_err(c, "the moment storage holds at most 715827882 nodes"), LB_ERR_ARG;
+  if (p->storage == LB_STORAGE_F32_GELIM && 10ull * g->nx * g->ny >= (1ull << 32))
+    return set_err(c, "the g-eliminated storage holds at most 429496729 nodes"), LB_ERR_ARG;
   if (w->tube_len < 0 || w->tube_len > g->nx) return set_err(c, "tube_len outside [0, nx]"), LB_ERR_ARG;
   if (w->tube_len > 0) {
     if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny)
@@ -377,6 +388,7 @@ lb_status lb_init_fields(lb_ctx* c, const double* rho, const double* ux, const d
 }
 
 lb_status lb_step(lb_ctx* c, long n) {
+  NvtxRange range("lb_step");
   if (!c) return LB_ERR_ARG;
   if (n < 0) return set_err(c, "negative step count"), LB_ERR_ARG;
   if (c->poisoned) return set_err(c, "context holds a non-finite or timed-out state"), LB_ERR_STATE;
@@ -436,6 +448,7 @@ lb_status lb_fields(lb_ctx* c, double* rho, double* ux, double* uy, double* phi)
 }
 
 lb_status lb_filled_length(lb_ctx* c, double* l_centre, double* l_vol, double* mass, double* phi_sum) {
+  NvtxRange range("lb_filled_length");
   if (!c) return LB_ERR_ARG;
   OpArgs a = base_args(c);
   a.src = c->buf[c->cur];
@@ -463,8 +476,8 @@ lb_status lb_filled_length(lb_ctx* c, double* l_centre, double* l_vol, double* m
 
 lb_status lb_get_populations(lb_ctx* c, double* f, double* g, int rested) {
   if (!c || !f) return c ? (set_err(c, "f is NULL"), LB_ERR_ARG) : LB_ERR_ARG;
-  if (c->prm.storage == LB_STORAGE_MOMENTS)
-    return set_err(c, "the moment storage keeps no populations (lb_get_moments)"), LB_ERR_ARG;
+  if (c->prm.storage == LB_STORAGE_MOMENTS || c->prm.storage == LB_STORAGE_MOMENTS_F16)
+    return set_err(c, "the moment storages keep no populations (lb_get_moments)"), LB_ERR_ARG;
   const size_t N = (size_t)c->grid.nx * c->grid.ny;
   const int bin = c->prm.model == LB_MODEL_BINARY;
   double* d = (double*)dev_alloc(c, (bin ? 18 : 9) * N * sizeof(double));
@@ -582,7 +595,7 @@ lb_status lb_sync(lb_ctx* c) {
 
 lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
   if (!c || !variant) return LB_ERR_ARG;
-  if (c->prm.storage == LB_STORAGE_MOMENTS) {
+  if (pull_storage(c->prm.storage)) {
     *variant = 4;
     return LB_OK;
   }
@@ -593,9 +606,9 @@ lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
 
 lb_status lb_set_kernel(lb_ctx* c, int variant) {
   if (!c) return LB_ERR_ARG;
-  if (c->prm.storage == LB_STORAGE_MOMENTS && variant != 0 && variant != 4)
-    return set_err(c, "the moment storage has one step kernel (variant 4)"), LB_ERR_ARG;
-  if (c->prm.storage == LB_STORAGE_MOMENTS) return LB_OK;
+  if (pull_storage(c->prm.storage) && variant != 0 && variant != 4)
+    return set_err(c, "this storage has one step kernel (variant 4)"), LB_ERR_ARG;
+  if (pull_storage(c->prm.storage)) return LB_OK;
   if (variant < 0 || variant > 3) return set_err(c, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
   if (variant >= 2 && c->grid.nx % 8 != 0)
     return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
@@ -637,6 +650,7 @@ lb_status lb_get_tile(const lb_ctx* c, int* tile_x, int* tile_y) {
 }
 
 lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) {
+  NvtxRange range("lb_autotune");
   if (!c) return LB_ERR_ARG;
   if (c->poisoned) return LB_ERR_STATE;
   const size_t N = (size_t)c->grid.nx * c->grid.ny;
@@ -654,7 +668,7 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   const int cand_x[3] = {64, 128, 256};
   // band heights: the moment kernel's time depends on how its warps fill the
   // GPU in waves, so it gets a finer set
-  const int moments = c->prm.storage == LB_STORAGE_MOMENTS;
+  const int moments = pull_storage(c->prm.storage);
   const std::vector<int> cand_y = moments ? std::vector<int>{4, 8, 12, 14, 16, 18, 20, 22, 24, 32, 48, 64}
                                           : std::vector<int>{1, 2, 4, 8, 16, 32, 64};
   const int saved_kernel = c->kernel, saved_deep = c->deep;

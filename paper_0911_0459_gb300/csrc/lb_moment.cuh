@@ -1,86 +1,129 @@
-// Moment representation of the binary-model state and its step kernel.
+// Reduced representations of the binary-model state and their step kernel.
 //
 // With the relaxation matrix of App. A every mode of f except the two stress
 // modes relaxes fully to equilibrium, and g relaxes fully to g^eq (Sec. 3.1).
 // The post-collision populations of a node therefore depend on its f only
 // through rho, jx, jy, pxx - pyy and pxy, and on its g only through phi (plus
-// the rho and phi stencils of Eq. (best)).  The state can thus be kept as six
-// numbers per node instead of eighteen populations: 48 bytes per lattice update
-// in FP32 (six read, six written) instead of 144.  The result is the population
-// scheme's in exact arithmetic; only the rounding differs.
+// the rho and phi stencils of Eq. (best)).  So the state need not hold all
+// eighteen populations.  Three storages use this, all advanced by the same pull
+// kernel:
+//   SM32  six FP32 moments per node (rho - 1, jx, jy, pxx - pyy, pxy, phi):
+//         48 bytes per lattice update (six read, six written) instead of 144;
+//   SM16  the same moments with rho - 1, j and the stresses in FP16 and phi in
+//         FP32: 28 bytes per update;
+//   SG32  the nine f populations in FP32 and phi in place of the nine g
+//         populations ("g eliminated"): 80 bytes per update.
+// The result is the population scheme's in exact arithmetic; only the rounding
+// differs (and, for SM16, the FP16 storage of five of the six moments).
 //
-// The stored moments are those of the post-streaming populations before the
-// boundary-node rest rule of Sec. 2.2, as in the population storages.  That rule
-// sets j to zero and leaves rho, pxx - pyy and pxy unchanged, so it is applied
-// when a boundary node is read.
+// The stored state is the post-streaming state before the boundary-node rest
+// rule of Sec. 2.2, as in the population storages.  That rule sets j to zero and
+// leaves rho, pxx - pyy and pxy unchanged, so it is applied when a boundary node
+// is read.
 //
 // The binary model keeps rho close to 1 (Sec. 3.1), so the density is stored
 // as rho - 1 and the populations are formed and streamed as deviations
 // f_i - w_i from the rest weights w = 4/9, 1/9, 1/36 (whose contributions to
 // every streamed moment cancel exactly: sum w_i = 1, sum w_i e_i = 0 and the
-// stress combinations of w vanish).  Rounding then acts on numbers of the size
-// of the flow, not on the populations themselves: in a nearly uniform phase
-// every node rounds almost the same population the same way, and at 1/9 that
-// fixed-sign error would accumulate into a drift of the interface.
+// stress combinations of w vanish); SG32 stores those deviations.  Rounding then
+// acts on numbers of the size of the flow, not on the populations themselves:
+// in a nearly uniform phase every node rounds almost the same population the
+// same way, and at 1/9 that fixed-sign error would accumulate into a drift of
+// the interface.
 //
-// Step (a pull): the new moments of node r are the moments of the populations
-// that arrive there, f_i(r) = f*_i(r - e_i), or f*_opp(i)(r) by bounce-back
-// where r - e_i is solid; likewise g_i(r) = g^eq_i(r - e_i).  A warp owns 32
+// Step (a pull): the new state of node r is made of the populations that
+// arrive there, f_i(r) = f*_i(r - e_i), or f*_opp(i)(r) by bounce-back where
+// r - e_i is solid; likewise g_i(r) = g^eq_i(r - e_i).  A warp owns 32
 // consecutive columns and every lane collides its own node; lanes 1..30 collect
 // the populations of their neighbours by warp shuffles, so a warp produces 30
 // columns and its two edge lanes only supply the halo.  The warp walks up a
 // band of rows: the populations of row k go to rows k - 1, k and k + 1, and row
 // k - 1 is complete (and stored) once row k has been distributed.  The rho/phi
 // rows of the stencil window are loaded two rows ahead of the collision, the
-// remaining moments one row ahead.
+// remaining values one row ahead.  Values of solid nodes are never loaded, and a
+// row whose whole window is wall under every column of the warp is skipped.
 #pragma once
+
+#include <cuda_fp16.h>
 
 #include "lb_device.cuh"
 
 namespace lbk {
 
-// Storage trait of the moment representation: six FP32 numbers per node, kept
-// as three planes of N float2, (rho - 1, phi), (jx, jy) and (pxx - pyy, pxy),
-// so that a node's moments take three 8-byte accesses.  M_RHO .. M_PHI name
-// the six moments in the order of the C interface.
-struct SM32 {
+// Storage traits of the pull kernel's representations.
+struct SM32 {  // six FP32 moments: three float2 planes (rho - 1, phi), (jx, jy), (pxx - pyy, pxy)
   using T = float;
   using A = float;
+  static constexpr int kind = 0;
+};
+struct SM16 {  // FP16 moments, FP32 phi: planes phi (float), rho - 1 (half), j (half2), stresses (half2)
+  using T = __half;
+  using A = float;
+  static constexpr int kind = 1;
+};
+struct SG32 {  // g eliminated: nine FP32 planes f_i - w_i, then a FP32 plane of phi
+  using T = float;
+  using A = float;
+  static constexpr int kind = 2;
 };
 enum { M_RHO = 0, M_JX = 1, M_JY = 2, M_XX = 3, M_XY = 4, M_PHI = 5, M_PLANES = 6 };
-enum { MP_RP = 0, MP_J = 1, MP_S = 2 };  // float2 planes
-
-// The six moments of node n (rho - 1 in m[M_RHO]).
-template <bool COHERENT = false>
-__device__ __forceinline__ void mom_load(const float* base, size_t N, size_t n, float m[M_PLANES]) {
-  const float2* P = reinterpret_cast<const float2*>(base);
-  const float2 a = COHERENT ? __ldcg(P + MP_RP * N + n) : P[MP_RP * N + n];
-  const float2 b = COHERENT ? __ldcg(P + MP_J * N + n) : P[MP_J * N + n];
-  const float2 c = COHERENT ? __ldcg(P + MP_S * N + n) : P[MP_S * N + n];
-  m[M_RHO] = a.x;
-  m[M_PHI] = a.y;
-  m[M_JX] = b.x;
-  m[M_JY] = b.y;
-  m[M_XX] = c.x;
-  m[M_XY] = c.y;
-}
-__device__ __forceinline__ void mom_store(float* base, size_t N, size_t n, const float m[M_PLANES]) {
-  float2* P = reinterpret_cast<float2*>(base);
-  P[MP_RP * N + n] = make_float2(m[M_RHO], m[M_PHI]);
-  P[MP_J * N + n] = make_float2(m[M_JX], m[M_JY]);
-  P[MP_S * N + n] = make_float2(m[M_XX], m[M_XY]);
-}
+enum { MP_RP = 0, MP_J = 1, MP_S = 2 };  // float2 planes of SM32
 
 template <class S>
-struct is_moments {
+struct is_moments {  // advanced by the pull kernel (populations are not all kept)
   static constexpr bool value = false;
 };
 template <>
 struct is_moments<SM32> {
   static constexpr bool value = true;
 };
+template <>
+struct is_moments<SM16> {
+  static constexpr bool value = true;
+};
+template <>
+struct is_moments<SG32> {
+  static constexpr bool value = true;
+};
 
-// The six stored moments of one node's populations.
+// Which pull storage a storage trait is (0 SM32, 1 SM16, 2 SG32), -1 for the
+// population storages.
+template <class S>
+struct pull_kind {
+  static constexpr int value = -1;
+};
+template <>
+struct pull_kind<SM32> {
+  static constexpr int value = 0;
+};
+template <>
+struct pull_kind<SM16> {
+  static constexpr int value = 1;
+};
+template <>
+struct pull_kind<SG32> {
+  static constexpr int value = 2;
+};
+
+// Byte offsets of the SM16 planes for N nodes (each plane 256-byte aligned).
+struct M16Layout {
+  size_t phi, r, j, m, total;
+};
+__host__ __device__ inline M16Layout m16_layout(size_t N) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  M16Layout L;
+  L.phi = 0;
+  L.j = up(4 * N);
+  L.m = L.j + up(4 * N);
+  L.r = L.m + up(4 * N);
+  L.total = L.r + up(2 * N);
+  return L;
+}
+
+// Rest weights of the deviations f_i - w_i.
+__host__ __device__ constexpr double WREST(int i) { return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+// The six stored moments of one node's populations (m[M_RHO] = sum f).
 template <typename A>
 __device__ __forceinline__ void pops_to_moments(const A f[9], const A g[9], A m[6]) {
   m[M_RHO] = sum9(f);
@@ -89,6 +132,95 @@ __device__ __forceinline__ void pops_to_moments(const A f[9], const A g[9], A m[
   m[M_XX] = (f[1] + f[2]) - (f[3] + f[4]);
   m[M_XY] = (f[5] + f[6]) - (f[7] + f[8]);
   m[M_PHI] = sum9(g);
+}
+
+// ------------------------------------------------------ per-node accessors
+//
+// Used by the initialisation, export, import and reduction kernels (one node
+// at a time).  Moments are those of the stored state, rho as rho - 1.
+
+template <bool COHERENT, class P>
+__device__ __forceinline__ P ldx(const P* p) {
+  if constexpr (COHERENT) return __ldcg(p);
+  return *p;
+}
+
+// The six moments of node n: SM32 and SM16 read them, SG32 sums its f
+// deviations (in FP32, in the order the step kernel sums them).
+template <class S, bool COHERENT = false>
+__device__ __forceinline__ void pull_load(const void* base, size_t N, size_t n, float m[M_PLANES]) {
+  if constexpr (S::kind == 0) {
+    const float2* P = static_cast<const float2*>(base);
+    const float2 a = ldx<COHERENT>(P + MP_RP * N + n), b = ldx<COHERENT>(P + MP_J * N + n);
+    const float2 c = ldx<COHERENT>(P + MP_S * N + n);
+    m[M_RHO] = a.x; m[M_PHI] = a.y; m[M_JX] = b.x; m[M_JY] = b.y; m[M_XX] = c.x; m[M_XY] = c.y;
+  } else if constexpr (S::kind == 1) {
+    const char* b = static_cast<const char*>(base);
+    const M16Layout L = m16_layout(N);
+    m[M_PHI] = ldx<COHERENT>(reinterpret_cast<const float*>(b + L.phi) + n);
+    m[M_RHO] = __half2float(ldx<COHERENT>(reinterpret_cast<const __half*>(b + L.r) + n));
+    const float2 j = __half22float2(ldx<COHERENT>(reinterpret_cast<const __half2*>(b + L.j) + n));
+    const float2 s = __half22float2(ldx<COHERENT>(reinterpret_cast<const __half2*>(b + L.m) + n));
+    m[M_JX] = j.x; m[M_JY] = j.y; m[M_XX] = s.x; m[M_XY] = s.y;
+  } else {
+    const float* F = static_cast<const float*>(base);
+    float f[9], g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = ldx<COHERENT>(F + i * N + n);
+    g[0] = ldx<COHERENT>(F + 9 * N + n);
+    pops_to_moments(f, g, m);
+  }
+}
+
+// Store the six moments of node n (SM32, SM16).
+template <class S>
+__device__ __forceinline__ void pull_store_moments(void* base, size_t N, size_t n, const float m[M_PLANES]) {
+  if constexpr (S::kind == 0) {
+    float2* P = static_cast<float2*>(base);
+    P[MP_RP * N + n] = make_float2(m[M_RHO], m[M_PHI]);
+    P[MP_J * N + n] = make_float2(m[M_JX], m[M_JY]);
+    P[MP_S * N + n] = make_float2(m[M_XX], m[M_XY]);
+  } else if constexpr (S::kind == 1) {
+    char* b = static_cast<char*>(base);
+    const M16Layout L = m16_layout(N);
+    reinterpret_cast<float*>(b + L.phi)[n] = m[M_PHI];
+    reinterpret_cast<__half*>(b + L.r)[n] = __float2half_rn(m[M_RHO]);
+    reinterpret_cast<__half2*>(b + L.j)[n] = __floats2half2_rn(m[M_JX], m[M_JY]);
+    reinterpret_cast<__half2*>(b + L.m)[n] = __floats2half2_rn(m[M_XX], m[M_XY]);
+  }
+}
+
+// SG32: the f deviations and phi of node n.
+__device__ __forceinline__ void sg_load(const void* base, size_t N, size_t n, float fd[9], float& phi) {
+  const float* F = static_cast<const float*>(base);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fd[i] = F[i * N + n];
+  phi = F[9 * N + n];
+}
+__device__ __forceinline__ void sg_store(void* base, size_t N, size_t n, const float fd[9], float phi) {
+  float* F = static_cast<float*>(base);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) F[i * N + n] = fd[i];
+  F[9 * N + n] = phi;
+}
+
+// (rho - 1, phi) of node n as the step kernel sees it, read through L2.
+template <class S>
+__device__ __forceinline__ float2 pull_rho_phi(const void* base, size_t N, size_t n) {
+  if constexpr (S::kind == 0) {
+    return __ldcg(static_cast<const float2*>(base) + MP_RP * N + n);
+  } else if constexpr (S::kind == 1) {
+    const char* b = static_cast<const char*>(base);
+    const M16Layout L = m16_layout(N);
+    return make_float2(__half2float(__ldcg(reinterpret_cast<const __half*>(b + L.r) + n)),
+                       __ldcg(reinterpret_cast<const float*>(b + L.phi) + n));
+  } else {
+    const float* F = static_cast<const float*>(base);
+    float f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = __ldcg(F + i * N + n);
+    return make_float2(sum9(f), __ldcg(F + 9 * N + n));
+  }
 }
 
 // Sign of population i in pxx - pyy and in pxy.
@@ -102,102 +234,165 @@ __device__ __forceinline__ float rcp_fast(float v) {
   return r;
 }
 
+// ---------------------------------------------------------------- collision
+
+// Constants of the collision, with the stencils' normalisations folded in: the
+// gradient stencils enter as 12 x the gradient and the Laplacian as 6 x the
+// Laplacian (see stencil_rows).
+struct MomPhys {
+  float A;          // phi^4 coefficient (Sec. 3.1)
+  float nkap6;      // -kappa / 6: -kappa lap = nkap6 (6 lap)
+  float kap144;     // kappa / 144: kappa (d phi)^2 = kap144 (12 d phi)^2
+  float lam12;      // lambda_scale / 12: lambda u . d rho = (lam12 nu) u . (12 d rho)
+  float nu_g, dnu;  // Eq. (nu): nu = nu_g + c (nu_l - nu_g)
+  float M3, M12;    // 2M/3 and 2M/12, g^eq's mobility terms (App. A)
+  float h;          // wall gradient d_n phi|_b
+  float lut, lut_inv;
+};
+
+inline MomPhys mom_phys(double kappa, double A, double M, double nu_l, double nu_g, double lambda_scale, double h,
+                        double lut) {
+  MomPhys q;
+  q.A = float(A);
+  q.nkap6 = float(-kappa / 6.0);
+  q.kap144 = float(kappa / 144.0);
+  q.lam12 = float(lambda_scale / 12.0);
+  q.nu_g = float(nu_g);
+  q.dnu = float(nu_l - nu_g);
+  q.M3 = float(2.0 * M / 3.0);
+  q.M12 = float(2.0 * M / 12.0);
+  q.h = float(h);
+  q.lut = float(lut);
+  q.lut_inv = lut > 0 ? float(1.0 / lut) : 0.f;
+  return q;
+}
+
 // Gradient and Laplacian stencils of Eq. (best) at one node, from per-row
 // summaries of the 3x3 neighbourhood: c (centre), s = right - left and
 // d = (left - c) + (right - c) of rows y-1 (0), y (1), y+1 (2), formed once per
 // row.  The sums of Eq. (best) regrouped into differences of neighbouring
-// values: dy = [(d2 - d0) + 6 (c2 - c0)] / 12 and
-// lap = [(d0 + d2 + 4 d1) + 6 ((c0 - c1) + (c2 - c1))] / 6.  Neighbouring values
-// are close, so those differences are exact in floating point and no large
-// partial sums cancel (in a nearly uniform phase the direct sums of about
-// twenty times the field value would leave a rounding error of fixed sign).
-__device__ __forceinline__ void stencil_rows(const float c[3], const float sv[3], const float d[3], float& dx,
-                                             float& dy, float& lap) {
-  dx = (fmaf(4.f, sv[1], sv[0]) + sv[2]) * (1.f / 12.f);
-  dy = fmaf(6.f, c[2] - c[0], d[2] - d[0]) * (1.f / 12.f);
-  lap = fmaf(6.f, (c[0] - c[1]) + (c[2] - c[1]), fmaf(4.f, d[1], d[0] + d[2])) * (1.f / 6.f);
+// values:
+//   12 dx = 4 s1 + s0 + s2,  12 dy = 6 (c2 - c0) + (d2 - d0),
+//   6 lap = 6 ((c0 - c1) + (c2 - c1)) + (4 d1 + d0 + d2).
+// Neighbouring values are close, so those differences are exact in floating
+// point and no large partial sums cancel (in a nearly uniform phase the direct
+// sums of about twenty times the field value would leave a rounding error of
+// fixed sign).  Returned unnormalised; the collision's constants carry the
+// factors 1/12 and 1/6.
+__device__ __forceinline__ void stencil_rows(const float c[3], const float sv[3], const float d[3], float& dx12,
+                                             float& dy12, float& lap6) {
+  dx12 = fmaf(4.f, sv[1], sv[0]) + sv[2];
+  dy12 = fmaf(6.f, c[2] - c[0], d[2] - d[0]);
+  lap6 = fmaf(6.f, (c[0] - c[1]) + (c[2] - c[1]), fmaf(4.f, d[1], d[0] + d[2]));
+}
+__device__ __forceinline__ void grad_rows(const float c[3], const float sv[3], const float d[3], float& dx12,
+                                          float& dy12) {
+  dx12 = fmaf(4.f, sv[1], sv[0]) + sv[2];
+  dy12 = fmaf(6.f, c[2] - c[0], d[2] - d[0]);
 }
 
-// Post-collision f and g (ge = g^eq) of one node from its moments and
-// stencils: Eq. (equilibrium) for f^eq with the binary pressure of Sec. 3.1,
-// g^eq of App. A, and the collision with every mode but pxx - pyy and pxy
-// relaxed fully.  The equilibrium stress moments enter in closed form,
-// (f^eq_1 + f^eq_2) - (f^eq_3 + f^eq_4) = (Txx - Tyy) + kappa (dx phi^2 - dy phi^2)
-// and (f^eq_5 + f^eq_6) - (f^eq_7 + f^eq_8) = Txy + kappa dx phi dy phi, and each
-// pair of opposite directions shares its even part.  drho = rho - 1; fs
-// receives f*_i - w_i.
-__device__ __forceinline__ void collide_moment_node(const Phys<float>& P, float drho, float jx, float jy, float mxx,
+// Eq. (best) on an explicit 3x3 neighbourhood (boundary nodes, after the wall
+// ghosts), unnormalised as above.
+__device__ __forceinline__ void stencil3_unnorm(const float v[3][3], float& dx12, float& dy12, float& lap6) {
+  dx12 = fmaf(4.f, v[1][2] - v[1][0], v[0][2] - v[0][0]) + (v[2][2] - v[2][0]);
+  dy12 = fmaf(4.f, v[2][1], v[2][0] + v[2][2]) - fmaf(4.f, v[0][1], v[0][0] + v[0][2]);
+  lap6 = fmaf(-20.f, v[1][1], fmaf(4.f, (v[0][1] + v[1][0]) + (v[1][2] + v[2][1]),
+                                   (v[0][0] + v[0][2]) + (v[2][0] + v[2][2])));
+}
+
+// Post-collision f (fs_i = f*_i - w_i) and g (ge = g^eq) of one node from its
+// moments and the unnormalised stencils: Eq. (equilibrium) for f^eq with the
+// binary pressure of Sec. 3.1, g^eq of App. A, and the collision with every
+// mode but pxx - pyy and pxy relaxed fully.
+//
+// With T = (Txx, Tyy, Txy) the second moment of f^eq beyond the pressure (the
+// rho u u and lambda terms of Eq. (equilibrium)) and G = kappa (dphi dphi) its
+// gradient terms, the even part of each pair of opposite directions, less w_i, is
+//   A1 = (P0 + Uxx - Uyy / 2) / 3 + dxx,   A3 = (P0 + Uyy - Uxx / 2) / 3 - dxx,
+//   A5 = (P0 + V + 3 (Txy + Gxy)) / 12 + dxy,  A7 = (P0 + V - 3 (Txy + Gxy)) / 12 - dxy,
+// with U = T + G, V = (Txx + Tyy) - (Gxx + Gyy) / 2, P0 the pressure less 1/3,
+// and dxx, dxy the stress non-equilibria relaxed at omega, (1 - omega)/4 times
+// (m - m^eq).  The odd parts are the momenta j/3 and j/12.
+__device__ __forceinline__ void collide_moment_node(const MomPhys& Q, float drho, float jx, float jy, float mxx,
                                                     float mxy, float phi, float rdx, float rdy, float pdx,
                                                     float pdy, float plap, float fs[9], float ge[9]) {
+  // Every product that feeds a sum is an explicit fused multiply-add and every
+  // other product an explicit __fmul_rn, so the compiler fuses nothing on its
+  // own and every kernel that inlines this function rounds a node alike.
   const float inv = rcp_fast(1.f + drho);
-  const float ux = jx * inv, uy = jy * inv;
-  const float phi2 = phi * phi;
-  const float mu = fmaf(-P.kappa, plap, P.Acoef * fmaf(phi2, phi, -phi));
-  float cl = __saturatef(fmaf(phi, 0.5f, 0.5f));  // liquid fraction (Eq. nu, clamped)
-  if (P.lut > 0.f) cl = rintf(cl * P.lut) * P.lut_inv;  // viscosity table of App. A
-  const float nu = fmaf(cl, P.nu_l - P.nu_g, P.nu_g);
-  const float omega = 2.f * rcp_fast(fmaf(6.f, nu, 1.f));
-  const float lam = P.lambda_scale * nu;
-  // P0 - 1/3: the pressure p0 = rho/3 + A(-phi^2/2 + 3 phi^4/4) less kappa phi lap phi
-  const float P0 = fmaf(-P.kappa * phi, plap, fmaf(drho, 1.f / 3.f, P.Acoef * phi2 * fmaf(0.75f, phi2, -0.5f)));
-  // second moment of f^eq beyond P0 (Eq. (equilibrium) with the lambda terms)
-  const float udr = fmaf(ux, rdx, uy * rdy);
-  const float Txx = fmaf(jx, ux, lam * fmaf(2.f * ux, rdx, udr));
-  const float Tyy = fmaf(jy, uy, lam * fmaf(2.f * uy, rdy, udr));
-  const float Txy = fmaf(jx, uy, lam * fmaf(ux, rdy, uy * rdx));
-  const float tr3 = (Txx + Tyy) * (1.f / 3.f);
-  const float ax = 1.5f * (Txx - tr3), ay = 1.5f * (Tyy - tr3);
-  const float dp = 1.5f * (fmaf(2.f, Txy, Txx + Tyy) - tr3), dm = 1.5f * (fmaf(-2.f, Txy, Txx + Tyy) - tr3);
-  const float Gxx = P.kappa * pdx * pdx, Gyy = P.kappa * pdy * pdy, Gxy = P.kappa * pdx * pdy;
-  const float k13 = fmaf(Gxx, 1.f / 3.f, Gyy * (-1.f / 6.f));
-  const float k24 = fmaf(Gyy, 1.f / 3.f, Gxx * (-1.f / 6.f));
-  const float kd = (Gxx + Gyy) * (-1.f / 24.f);
-  const float kxy = Gxy * 0.25f;
-  // non-equilibrium of the two stress modes, relaxed at omega
-  const float c = (1.f - omega) * 0.25f;
-  const float dxx = c * (mxx - (Txx - Tyy) - (Gxx - Gyy));
-  const float dxy = c * (mxy - Txy - Gxy);
-  // even parts of the four direction pairs, less w_i
-  const float A1 = fmaf(P0 + ax, 1.f / 3.f, k13 + dxx);
-  const float A3 = fmaf(P0 + ay, 1.f / 3.f, k24 - dxx);
-  const float A5 = fmaf(P0 + dp, 1.f / 12.f, kd + kxy + dxy);
-  const float A7 = fmaf(P0 + dm, 1.f / 12.f, kd - kxy - dxy);
-  const float bx = jx * (1.f / 3.f), by = jy * (1.f / 3.f);
-  const float bp = (jx + jy) * (1.f / 12.f), bm = (jy - jx) * (1.f / 12.f);
-  fs[1] = A1 + bx; fs[2] = A1 - bx;
-  fs[3] = A3 + by; fs[4] = A3 - by;
-  fs[5] = A5 + bp; fs[6] = A5 - bp;
-  fs[7] = A7 + bm; fs[8] = A7 - bm;
+  const float ux = __fmul_rn(jx, inv), uy = __fmul_rn(jy, inv);
+  const float phi2 = __fmul_rn(phi, phi);
+  // chemical potential (Eq. chempot): A (phi^3 - phi) - kappa lap phi
+  const float mu = fmaf(Q.nkap6, plap, __fmul_rn(Q.A, fmaf(phi2, phi, -phi)));
+  // viscosity (Eq. nu, the liquid fraction clamped) and c = (1 - omega) / 4
+  float cl = __saturatef(fmaf(phi, 0.5f, 0.5f));
+  if (Q.lut > 0.f) cl = __fmul_rn(rintf(__fmul_rn(cl, Q.lut)), Q.lut_inv);  // viscosity table of App. A
+  const float nu = fmaf(cl, Q.dnu, Q.nu_g);
+  const float r = rcp_fast(fmaf(6.f, nu, 1.f));  // omega / 2
+  const float c = fmaf(-0.5f, r, 0.25f);
+  const float lam = __fmul_rn(Q.lam12, nu);
+  // P0 - 1/3: p0 = rho/3 + A (-phi^2/2 + 3 phi^4/4) less kappa phi lap phi
+  const float P0 = fmaf(__fmul_rn(Q.nkap6, phi), plap,
+                        fmaf(drho, 1.f / 3.f, __fmul_rn(__fmul_rn(Q.A, phi2), fmaf(0.75f, phi2, -0.5f))));
+  // second moment of f^eq beyond P0: T (rho u u and the lambda terms) and the
+  // gradient terms G = kappa (dphi dphi), with U = T + G
+  const float ax = __fmul_rn(ux, rdx), ay = __fmul_rn(uy, rdy);
+  const float udr = ax + ay;
+  const float Txx = fmaf(jx, ux, __fmul_rn(lam, fmaf(2.f, ax, udr)));
+  const float Tyy = fmaf(jy, uy, __fmul_rn(lam, fmaf(2.f, ay, udr)));
+  const float Txy = fmaf(jx, uy, __fmul_rn(lam, fmaf(ux, rdy, __fmul_rn(uy, rdx))));
+  const float kx = __fmul_rn(Q.kap144, pdx), ky = __fmul_rn(Q.kap144, pdy);
+  const float Uxx = fmaf(kx, pdx, Txx), Uyy = fmaf(ky, pdy, Tyy);
+  const float GS = fmaf(kx, pdx, __fmul_rn(ky, pdy));   // Gxx + Gyy
+  const float V = fmaf(-0.5f, GS, Txx + Tyy);
+  const float TG = fmaf(kx, pdy, Txy);                  // Txy + Gxy
+  const float dxx = __fmul_rn(c, mxx - (Uxx - Uyy));
+  const float dxy = __fmul_rn(c, mxy - TG);
+  const float A1 = fmaf(P0 + fmaf(-0.5f, Uyy, Uxx), 1.f / 3.f, dxx);
+  const float A3 = fmaf(P0 + fmaf(-0.5f, Uxx, Uyy), 1.f / 3.f, -dxx);
+  const float W3 = __fmul_rn(3.f, TG);
+  const float A5 = fmaf(P0 + (V + W3), 1.f / 12.f, dxy);
+  const float A7 = fmaf(P0 + (V - W3), 1.f / 12.f, -dxy);
+  const float jp = jx + jy, jm = jy - jx;
+  fs[1] = fmaf(jx, 1.f / 3.f, A1); fs[2] = fmaf(jx, -1.f / 3.f, A1);
+  fs[3] = fmaf(jy, 1.f / 3.f, A3); fs[4] = fmaf(jy, -1.f / 3.f, A3);
+  fs[5] = fmaf(jp, 1.f / 12.f, A5); fs[6] = fmaf(jp, -1.f / 12.f, A5);
+  fs[7] = fmaf(jm, 1.f / 12.f, A7); fs[8] = fmaf(jm, -1.f / 12.f, A7);
   fs[0] = fmaf(-2.f, (A1 + A3) + (A5 + A7), drho);
   // g^eq (App. A, dt = 1)
-  const float Q = 2.f * P.M * mu;
-  const float u2 = fmaf(ux, ux, uy * uy) * (1.f / 3.f);
-  const float h15 = 1.5f * phi;
+  const float Q3 = __fmul_rn(Q.M3, mu), Q12 = __fmul_rn(Q.M12, mu);
+  const float nu2 = __fmul_rn(fmaf(ux, ux, __fmul_rn(uy, uy)), -1.f / 3.f);  // -u.u / 3
+  const float hp = __fmul_rn(0.5f, phi), hq = __fmul_rn(0.125f, phi);
   const float upp = ux + uy, ump = ux - uy;
-  const float B1 = fmaf(h15, fmaf(ux, ux, -u2), Q) * (1.f / 3.f);
-  const float B3 = fmaf(h15, fmaf(uy, uy, -u2), Q) * (1.f / 3.f);
-  const float B5 = fmaf(h15, fmaf(upp, upp, -u2), Q) * (1.f / 12.f);
-  const float B7 = fmaf(h15, fmaf(ump, ump, -u2), Q) * (1.f / 12.f);
-  const float px = phi * ux * (1.f / 3.f), py = phi * uy * (1.f / 3.f);
-  const float pp = phi * upp * (1.f / 12.f), pm = phi * (uy - ux) * (1.f / 12.f);
-  ge[1] = B1 + px; ge[2] = B1 - px;
-  ge[3] = B3 + py; ge[4] = B3 - py;
-  ge[5] = B5 + pp; ge[6] = B5 - pp;
-  ge[7] = B7 + pm; ge[8] = B7 - pm;
+  const float B1 = fmaf(hp, fmaf(ux, ux, nu2), Q3);
+  const float B3 = fmaf(hp, fmaf(uy, uy, nu2), Q3);
+  const float B5 = fmaf(hq, fmaf(upp, upp, nu2), Q12);
+  const float B7 = fmaf(hq, fmaf(ump, ump, nu2), Q12);
+  const float p3 = __fmul_rn(phi, 1.f / 3.f), p12 = __fmul_rn(phi, 1.f / 12.f);
+  ge[1] = fmaf(p3, ux, B1); ge[2] = fmaf(-p3, ux, B1);
+  ge[3] = fmaf(p3, uy, B3); ge[4] = fmaf(-p3, uy, B3);
+  ge[5] = fmaf(p12, upp, B5); ge[6] = fmaf(-p12, upp, B5);
+  ge[7] = fmaf(-p12, ump, B7); ge[8] = fmaf(p12, ump, B7);
   ge[0] = fmaf(-2.f, (B1 + B3) + (B5 + B7), phi);
 }
 
 struct MomArgs {
   Geom G;
-  Phys<float> P;
-  const float* src;  // three float2 planes of N nodes (6 N < 2^32)
-  float* dst;
-  int yc;            // rows per band
+  MomPhys Q;
+  const void* src;  // the state in the storage's layout (element offsets below 2^32)
+  void* dst;
+  int yc;           // rows per band
 };
 
-// Moments of a destination node as they accumulate.
-struct MAcc {
+// What a destination node has received so far: its moments (SM32, SM16), or
+// its f populations (as deviations) and phi (SG32).
+template <class S>
+struct PullAcc {
   float r, jx, jy, xx, xy, p;
+};
+template <>
+struct PullAcc<SG32> {
+  float f[9], p;
 };
 
 // Columns produced per warp.
@@ -207,10 +402,11 @@ constexpr int kMomCols = 30;
 // one step (every lane of the warp calls it, with the same arguments).
 // COHERENT: read src through L2 (a persistent launch whose other CTAs wrote
 // src earlier in the same launch).
-template <bool COHERENT>
-__device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P, const float* src_f, float* dst_f,
-                                             int xo, int y0, int y1, int lane) {
+template <bool COHERENT, class S>
+__device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, const void* src_v, void* dst_v, int xo,
+                                             int y0, int y1, int lane) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int K = S::kind;
   const int nx = G.nx, ny = G.ny;
   const unsigned N = (unsigned)nx * (unsigned)ny;
   if (xo >= nx) return;                                // whole warp
@@ -225,10 +421,17 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P
   const bool tc0 = tubed && col_in_tube(G, xm);
   const bool tc1 = tubed && col_in_tube(G, x);
   const bool tc2 = tubed && col_in_tube(G, xp);
+  const bool tce = lane == 0 ? tc0 : tc2;              // the edge column lies in the tube
   const bool warp_tube = __any_sync(FULL, tc0 || tc1 || tc2);
-  const float2* __restrict__ src = reinterpret_cast<const float2*>(src_f);
-  float2* __restrict__ dst = reinterpret_cast<float2*>(dst_f);
-  auto ld2 = [&](unsigned i) { return COHERENT ? __ldcg(src + i) : __ldg(src + i); };
+  const bool warp_all_tube = __all_sync(FULL, tc0 && tc1 && tc2);
+  // the storage's planes
+  const char* __restrict__ sb = static_cast<const char*>(src_v);
+  char* __restrict__ db = static_cast<char*>(dst_v);
+  [[maybe_unused]] const M16Layout L16 = m16_layout(N);
+  auto ldf = [&](const float* p) { return COHERENT ? __ldcg(p) : __ldg(p); };
+  auto ldf2 = [&](const float2* p) { return COHERENT ? __ldcg(p) : __ldg(p); };
+  auto ldh = [&](const __half* p) { return COHERENT ? __ldcg(p) : __ldg(p); };
+  auto ldh2 = [&](const __half2* p) { return COHERENT ? __ldcg(p) : __ldg(p); };
 
   // one row of the stencil window: centre c, s = right - left and
   // d = (left - c) + (right - c) of rho and phi at this lane's column.  The
@@ -273,26 +476,65 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P
     w.ph = (pl - p) + (pr - p);
     return w;
   };
-  auto load_rp = [&](unsigned rowb, float& rv, float& pv, float& re, float& pe) {
-    const float2 v = ld2(MP_RP * N + rowb + x);
-    rv = v.x;
-    pv = v.y;
-    re = 0.f;
-    pe = 0.f;
-    if (edge) {
-      const float2 e = ld2(MP_RP * N + rowb + xe);
-      re = e.x;
-      pe = e.y;
+  // j and the stresses of a node
+  struct JM {
+    float jx, jy, mx, my;
+  };
+  // rho - 1 and phi of node o; SG32 also gives the node's j and stresses, from
+  // the same f (the step keeps them until the row's collision)
+  auto load_node_rp = [&](unsigned o, float& rv, float& pv, JM& m) {
+    if constexpr (K == 0) {
+      const float2 v = ldf2(reinterpret_cast<const float2*>(sb) + MP_RP * N + o);
+      rv = v.x;
+      pv = v.y;
+    } else if constexpr (K == 1) {
+      pv = ldf(reinterpret_cast<const float*>(sb + L16.phi) + o);
+      rv = __half2float(ldh(reinterpret_cast<const __half*>(sb + L16.r) + o));
+    } else {
+      const float* F = reinterpret_cast<const float*>(sb);
+      float f[9], mm[6], g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = ldf(F + i * N + o);
+      pops_to_moments(f, g, mm);
+      rv = mm[M_RHO];
+      pv = ldf(F + 9 * N + o);
+      m = JM{mm[M_JX], mm[M_JY], mm[M_XX], mm[M_XY]};
     }
   };
-  auto load_jm = [&](unsigned rowb, float& jx, float& jy, float& mx, float& my) {
-    const unsigned o = rowb + x;
-    const float2 j = ld2(MP_J * N + o);
-    const float2 m = ld2(MP_S * N + o);
-    jx = j.x;
-    jy = j.y;
-    mx = m.x;
-    my = m.y;
+  // row rowb: this lane's rho - 1, phi (and SG32 moments) and the edge column's
+  // rho - 1, phi.  Solid nodes hold zeros; SG32 does not read them (ten values
+  // a node), the moment storages read them rather than test for them.
+  auto load_rp = [&](unsigned rowb, bool in_band, float& rv, float& pv, float& re, float& pe, JM& m) {
+    re = pe = 0.f;
+    if constexpr (K == 2) {
+      rv = pv = 0.f;
+      m = JM{0.f, 0.f, 0.f, 0.f};
+      if (!(tc1 && !in_band)) load_node_rp(rowb + x, rv, pv, m);
+      if (edge && !(tce && !in_band)) {
+        JM unused;
+        load_node_rp(rowb + xe, re, pe, unused);
+      }
+    } else {
+      load_node_rp(rowb + x, rv, pv, m);
+      if (edge) {
+        JM unused;
+        load_node_rp(rowb + xe, re, pe, unused);
+      }
+    }
+  };
+  auto load_jm = [&](unsigned rowb, bool in_band, JM& m) {
+    if constexpr (K == 0 || K == 1) {
+      const unsigned o = rowb + x;
+      if constexpr (K == 0) {
+        const float2 j = ldf2(reinterpret_cast<const float2*>(sb) + MP_J * N + o);
+        const float2 s = ldf2(reinterpret_cast<const float2*>(sb) + MP_S * N + o);
+        m = JM{j.x, j.y, s.x, s.y};
+      } else {
+        const float2 j = __half22float2(ldh2(reinterpret_cast<const __half2*>(sb + L16.j) + o));
+        const float2 s = __half22float2(ldh2(reinterpret_cast<const __half2*>(sb + L16.m) + o));
+        m = JM{j.x, j.y, s.x, s.y};
+      }
+    }
   };
   auto next_row = [&](int yy) { return yy + 1 == ny ? 0 : yy + 1; };
 
@@ -313,160 +555,222 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P
   S0.rb = row_in_band(G, S0.y);
   S1.rb = row_in_band(G, S1.y);
   S2.rb = row_in_band(G, S2.y);
-  float jx, jy, mx, my;  // moments of the collision row
+  JM cm;     // j and stresses of the collision row
+  JM stash;  // SG32: those of the row after it, taken from its f two rows ahead
   {
     float r, p, re, pe;
-    load_rp((unsigned)S0.y * nx, r, p, re, pe);
+    JM m;
+    load_rp((unsigned)S0.y * nx, S0.rb, r, p, re, pe, m);
     S0.w = make_row(r, p, re, pe, S0.rb);
-    load_rp((unsigned)S1.y * nx, r, p, re, pe);
+    load_rp((unsigned)S1.y * nx, S1.rb, r, p, re, pe, m);
     S1.w = make_row(r, p, re, pe, S1.rb);
-    load_rp((unsigned)S2.y * nx, r, p, re, pe);
+    cm = m;
+    load_rp((unsigned)S2.y * nx, S2.rb, r, p, re, pe, m);
     S2.w = make_row(r, p, re, pe, S2.rb);
-    load_jm((unsigned)S1.y * nx, jx, jy, mx, my);
+    stash = m;
+    if constexpr (K != 2) load_jm((unsigned)S1.y * nx, S1.rb, cm);
   }
-  MAcc A0 = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, A1 = A0, A2 = A0;
+  PullAcc<S> A0, A1, A2;
+  if constexpr (K == 2) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A0.f[i] = 0.f;
+    A0.p = 0.f;
+  } else {
+    A0 = PullAcc<S>{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  }
+  A1 = A0;
+  A2 = A0;
+  const PullAcc<S> zero = A0;
 
   // collision row k: slots lo/mid/hi hold rows k - 1, k, k + 1; accumulators
   // a0 (row k - 1, stored here), a1 (row k) and a2 (row k + 1, started here)
-  auto step = [&](Slot& lo, Slot& mid, Slot& hi, MAcc& a0, MAcc& a1, MAcc& a2, int k) {
+  auto step = [&](Slot& lo, Slot& mid, Slot& hi, PullAcc<S>& a0, PullAcc<S>& a1, PullAcc<S>& a2, int k) {
     // next rows in flight while this one collides
     const int yq = next_row(hi.y);  // row k + 2
-    float nr = 0.f, np = 0.f, ner = 0.f, nep = 0.f, njx = 0.f, njy = 0.f, nmx = 0.f, nmy = 0.f;
+    const bool qb = row_in_band(G, yq);
+    float nr = 0.f, np = 0.f, ner = 0.f, nep = 0.f;
+    JM njm = JM{0.f, 0.f, 0.f, 0.f}, qjm = JM{0.f, 0.f, 0.f, 0.f};
     if (k < y1) {
-      load_rp((unsigned)yq * nx, nr, np, ner, nep);
-      load_jm((unsigned)hi.y * nx, njx, njy, nmx, nmy);
-    }
-    // walls can touch this warp only if it has tube columns and a row leaves the
-    // band (warp-uniform); otherwise every node is fluid with fluid neighbours
-    const bool walls = warp_tube && !(lo.rb && mid.rb && hi.rb);
-    float fs[9], ge[9];
-    if (!walls) {
-      float rdx, rdy, rlap, pdx, pdy, plap;
-      const float rc[3] = {lo.w.rc, mid.w.rc, hi.w.rc}, rs[3] = {lo.w.rs, mid.w.rs, hi.w.rs};
-      const float rh[3] = {lo.w.rh, mid.w.rh, hi.w.rh};
-      const float pc[3] = {lo.w.pc, mid.w.pc, hi.w.pc}, ps[3] = {lo.w.ps, mid.w.ps, hi.w.ps};
-      const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
-      stencil_rows(rc, rs, rh, rdx, rdy, rlap);
-      stencil_rows(pc, ps, ph, pdx, pdy, plap);
-      collide_moment_node(P, mid.w.rc, jx, jy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
-      a1.r += fs[0];
-      a1.p += ge[0];
-    } else {
-      const bool fluid = !(tc1 && !mid.rb);
-      bool sol[3][3];
-      bool bnd = false;
-      {
-        const bool tc[3] = {tc0, tc1, tc2};
-        const bool rb[3] = {lo.rb, mid.rb, hi.rb};
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            sol[j][i] = tc[i] && !rb[j];
-            bnd = bnd || sol[j][i];
-          }
+      if constexpr (K == 2) {
+        njm = stash;
+      } else {
+        load_jm((unsigned)hi.y * nx, hi.rb, njm);
       }
-      if (fluid) {
-        float rdx, rdy, rlap, pdx, pdy, plap;
-        float cjx = jx, cjy = jy;
-        if (!bnd) {
-          const float rc[3] = {lo.w.rc, mid.w.rc, hi.w.rc}, rs[3] = {lo.w.rs, mid.w.rs, hi.w.rs};
-          const float rh[3] = {lo.w.rh, mid.w.rh, hi.w.rh};
-          const float pc[3] = {lo.w.pc, mid.w.pc, hi.w.pc}, ps[3] = {lo.w.ps, mid.w.ps, hi.w.ps};
-          const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
-          stencil_rows(rc, rs, rh, rdx, rdy, rlap);
-          stencil_rows(pc, ps, ph, pdx, pdy, plap);
-        } else {
-          // boundary node: wall ghosts on the full neighbourhood, and the rest rule
-          const Row* wr[3] = {&lo.w, &mid.w, &hi.w};
-          float vr[3][3], vp[3][3];
+      load_rp((unsigned)yq * nx, qb, nr, np, ner, nep, qjm);
+    }
+    // a row whose whole window is wall under every column sends and stores nothing
+    const bool all_wall = warp_all_tube && !lo.rb && !mid.rb && !hi.rb;
+    if (!all_wall) {
+      // walls can touch this warp only if it has tube columns and a row leaves the
+      // band (warp-uniform); otherwise every node is fluid with fluid neighbours
+      const bool walls = warp_tube && !(lo.rb && mid.rb && hi.rb);
+      float fs[9], ge[9];
+      // populations the own node sent into a wall, returned to it (bounce-back)
+      bool bounce[9] = {false, false, false, false, false, false, false, false, false};
+      if (!walls) {
+        float rdx, rdy, pdx, pdy, plap;
+        const float rc[3] = {lo.w.rc, mid.w.rc, hi.w.rc}, rs[3] = {lo.w.rs, mid.w.rs, hi.w.rs};
+        const float rh[3] = {lo.w.rh, mid.w.rh, hi.w.rh};
+        const float pc[3] = {lo.w.pc, mid.w.pc, hi.w.pc}, ps[3] = {lo.w.ps, mid.w.ps, hi.w.ps};
+        const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
+        grad_rows(rc, rs, rh, rdx, rdy);
+        stencil_rows(pc, ps, ph, pdx, pdy, plap);
+        collide_moment_node(Q, mid.w.rc, cm.jx, cm.jy, cm.mx, cm.my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+      } else {
+        const bool fluid = !(tc1 && !mid.rb);
+        bool sol[3][3];
+        bool bnd = false;
+        {
+          const bool tc[3] = {tc0, tc1, tc2};
+          const bool rb[3] = {lo.rb, mid.rb, hi.rb};
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            vr[j][0] = fmaf(0.5f, wr[j]->rh - wr[j]->rs, wr[j]->rc);
-            vr[j][1] = wr[j]->rc;
-            vr[j][2] = fmaf(0.5f, wr[j]->rh + wr[j]->rs, wr[j]->rc);
-            vp[j][0] = fmaf(0.5f, wr[j]->ph - wr[j]->ps, wr[j]->pc);
-            vp[j][1] = wr[j]->pc;
-            vp[j][2] = fmaf(0.5f, wr[j]->ph + wr[j]->ps, wr[j]->pc);
-          }
-          apply_ghosts(vr, sol, 0.f);
-          apply_ghosts(vp, sol, P.h);
-          stencil3(vr, rdx, rdy, rlap);
-          stencil3(vp, pdx, pdy, plap);
-          cjx = 0.f;
-          cjy = 0.f;
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              sol[j][i] = tc[i] && !rb[j];
+              bnd = bnd || sol[j][i];
+            }
         }
-        collide_moment_node(P, mid.w.rc, cjx, cjy, mx, my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
-        // own node: the rest population, and bounce-back of what was sent into a
-        // wall (all populations as deviations from w_i, which add up to 1, 0, 0, 0, 0)
-        a1.r += fs[0];
-        a1.p += ge[0];
-        if (bnd) {
+        if (fluid) {
+          float rdx, rdy, rlap, pdx, pdy, plap;
+          float cjx = cm.jx, cjy = cm.jy;
+          if (!bnd) {
+            const float rc[3] = {lo.w.rc, mid.w.rc, hi.w.rc}, rs[3] = {lo.w.rs, mid.w.rs, hi.w.rs};
+            const float rh[3] = {lo.w.rh, mid.w.rh, hi.w.rh};
+            const float pc[3] = {lo.w.pc, mid.w.pc, hi.w.pc}, ps[3] = {lo.w.ps, mid.w.ps, hi.w.ps};
+            const float ph[3] = {lo.w.ph, mid.w.ph, hi.w.ph};
+            grad_rows(rc, rs, rh, rdx, rdy);
+            stencil_rows(pc, ps, ph, pdx, pdy, plap);
+          } else {
+            // boundary node: wall ghosts on the full neighbourhood, and the rest rule
+            const Row* wr[3] = {&lo.w, &mid.w, &hi.w};
+            float vr[3][3], vp[3][3];
 #pragma unroll
-          for (int i = 1; i < 9; ++i)
-            if (sol[1 + EYd(i)][1 + EXd(i)]) {
-              const float v = fs[i];
+            for (int j = 0; j < 3; ++j) {
+              vr[j][0] = fmaf(0.5f, wr[j]->rh - wr[j]->rs, wr[j]->rc);
+              vr[j][1] = wr[j]->rc;
+              vr[j][2] = fmaf(0.5f, wr[j]->rh + wr[j]->rs, wr[j]->rc);
+              vp[j][0] = fmaf(0.5f, wr[j]->ph - wr[j]->ps, wr[j]->pc);
+              vp[j][1] = wr[j]->pc;
+              vp[j][2] = fmaf(0.5f, wr[j]->ph + wr[j]->ps, wr[j]->pc);
+            }
+            apply_ghosts(vr, sol, 0.f);
+            apply_ghosts(vp, sol, Q.h);
+            stencil3_unnorm(vr, rdx, rdy, rlap);
+            stencil3_unnorm(vp, pdx, pdy, plap);
+            cjx = 0.f;
+            cjy = 0.f;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) bounce[i] = sol[1 + EYd(i)][1 + EXd(i)];
+          }
+          collide_moment_node(Q, mid.w.rc, cjx, cjy, cm.mx, cm.my, mid.w.pc, rdx, rdy, pdx, pdy, plap, fs, ge);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            fs[i] = 0.f;  // a solid node sends nothing
+            ge[i] = 0.f;
+          }
+        }
+      }
+      // own node: the rest population, and bounce-back of what was sent into a
+      // wall (all populations as deviations from w_i, which add up to 1, 0, 0, 0, 0)
+      if constexpr (K == 2) {
+        a1.f[0] += fs[0];
+      } else {
+        a1.r += fs[0];
+      }
+      a1.p += ge[0];
+      if (walls) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          if (bounce[i]) {
+            const float v = fs[i];
+            if constexpr (K == 2) {
+              a1.f[OPPd(i)] += v;
+            } else {
               a1.r += v;
               a1.jx -= float(EXd(i)) * v;
               a1.jy -= float(EYd(i)) * v;
               a1.xx += float(SXXd(i)) * v;
               a1.xy += float(SXYd(i)) * v;
-              a1.p += ge[i];
             }
-        }
-      } else {
+            a1.p += ge[i];
+          }
+      }
+      // populations moving in +x come from lane - 1, in -x from lane + 1
+      const float f1 = __shfl_up_sync(FULL, fs[1], 1), f5 = __shfl_up_sync(FULL, fs[5], 1);
+      const float f8 = __shfl_up_sync(FULL, fs[8], 1);
+      const float f2 = __shfl_down_sync(FULL, fs[2], 1), f6 = __shfl_down_sync(FULL, fs[6], 1);
+      const float f7 = __shfl_down_sync(FULL, fs[7], 1);
+      const float g1 = __shfl_up_sync(FULL, ge[1], 1), g5 = __shfl_up_sync(FULL, ge[5], 1);
+      const float g8 = __shfl_up_sync(FULL, ge[8], 1);
+      const float g2 = __shfl_down_sync(FULL, ge[2], 1), g6 = __shfl_down_sync(FULL, ge[6], 1);
+      const float g7 = __shfl_down_sync(FULL, ge[7], 1);
+      a1.p += g1 + g2;
+      a2.p = ge[3] + (g5 + g7);
+      a0.p += ge[4] + (g6 + g8);
+      if constexpr (K == 2) {
+        // row k: 1 from x - 1, 2 from x + 1; row k + 1: 3 from here, 5 from x - 1,
+        // 7 from x + 1; row k - 1: 4 from here, 8 from x - 1, 6 from x + 1
+        a1.f[1] += f1;
+        a1.f[2] += f2;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          fs[i] = 0.f;  // a solid node sends nothing
-          ge[i] = 0.f;
+        for (int i = 0; i < 9; ++i) a2.f[i] = 0.f;
+        a2.f[3] = fs[3];
+        a2.f[5] = f5;
+        a2.f[7] = f7;
+        a0.f[4] += fs[4];
+        a0.f[8] += f8;
+        a0.f[6] += f6;
+      } else {
+        // row k: e = (+-1, 0)
+        a1.r += f1 + f2;
+        a1.jx += f1 - f2;
+        a1.xx += f1 + f2;
+        // row k + 1: e_y = +1 (3 from here, 5 from x - 1, 7 from x + 1)
+        a2.r = fs[3] + (f5 + f7);
+        a2.jx = f5 - f7;
+        a2.jy = a2.r;
+        a2.xx = -fs[3];
+        a2.xy = f5 - f7;
+        // row k - 1: e_y = -1 (4 from here, 8 from x - 1, 6 from x + 1)
+        const float s4 = fs[4] + (f6 + f8);
+        a0.r += s4;
+        a0.jx += f8 - f6;
+        a0.jy -= s4;
+        a0.xx -= fs[4];
+        a0.xy += f6 - f8;
+      }
+      // row k - 1 has received everything
+      if (k > y0 && store_lane && !(tc1 && !lo.rb)) {
+        const unsigned o = (unsigned)lo.y * nx + x;
+        if constexpr (K == 0) {
+          float2* P = reinterpret_cast<float2*>(db);
+          P[MP_RP * N + o] = make_float2(a0.r, a0.p);
+          P[MP_J * N + o] = make_float2(a0.jx, a0.jy);
+          P[MP_S * N + o] = make_float2(a0.xx, a0.xy);
+        } else if constexpr (K == 1) {
+          reinterpret_cast<float*>(db + L16.phi)[o] = a0.p;
+          reinterpret_cast<__half*>(db + L16.r)[o] = __float2half_rn(a0.r);
+          reinterpret_cast<__half2*>(db + L16.j)[o] = __floats2half2_rn(a0.jx, a0.jy);
+          reinterpret_cast<__half2*>(db + L16.m)[o] = __floats2half2_rn(a0.xx, a0.xy);
+        } else {
+          float* F = reinterpret_cast<float*>(db);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) F[i * N + o] = a0.f[i];
+          F[9 * N + o] = a0.p;
         }
       }
-    }
-    // populations moving in +x come from lane - 1, in -x from lane + 1
-    const float f1 = __shfl_up_sync(FULL, fs[1], 1), f5 = __shfl_up_sync(FULL, fs[5], 1);
-    const float f8 = __shfl_up_sync(FULL, fs[8], 1);
-    const float f2 = __shfl_down_sync(FULL, fs[2], 1), f6 = __shfl_down_sync(FULL, fs[6], 1);
-    const float f7 = __shfl_down_sync(FULL, fs[7], 1);
-    const float g1 = __shfl_up_sync(FULL, ge[1], 1), g5 = __shfl_up_sync(FULL, ge[5], 1);
-    const float g8 = __shfl_up_sync(FULL, ge[8], 1);
-    const float g2 = __shfl_down_sync(FULL, ge[2], 1), g6 = __shfl_down_sync(FULL, ge[6], 1);
-    const float g7 = __shfl_down_sync(FULL, ge[7], 1);
-    // row k: e = (+-1, 0)
-    a1.r += f1 + f2;
-    a1.jx += f1 - f2;
-    a1.xx += f1 + f2;
-    a1.p += g1 + g2;
-    // row k + 1: e_y = +1 (3 from here, 5 from x - 1, 7 from x + 1)
-    a2.r = fs[3] + (f5 + f7);
-    a2.jx = f5 - f7;
-    a2.jy = a2.r;
-    a2.xx = -fs[3];
-    a2.xy = f5 - f7;
-    a2.p = ge[3] + (g5 + g7);
-    // row k - 1: e_y = -1 (4 from here, 8 from x - 1, 6 from x + 1)
-    const float s4 = fs[4] + (f6 + f8);
-    a0.r += s4;
-    a0.jx += f8 - f6;
-    a0.jy -= s4;
-    a0.xx -= fs[4];
-    a0.xy += f6 - f8;
-    a0.p += ge[4] + (g6 + g8);
-    // row k - 1 has received everything
-    if (k > y0 && store_lane && !(tc1 && !lo.rb)) {
-      const unsigned o = (unsigned)lo.y * nx + x;
-      dst[MP_RP * N + o] = make_float2(a0.r, a0.p);
-      dst[MP_J * N + o] = make_float2(a0.jx, a0.jy);
-      dst[MP_S * N + o] = make_float2(a0.xx, a0.xy);
+    } else {
+      a2 = zero;
     }
     if (k < y1) {
       // row k + 2 takes the slot of row k - 1
       lo.y = yq;
-      lo.rb = row_in_band(G, yq);
-      lo.w = make_row(nr, np, ner, nep, lo.rb);
-      jx = njx;
-      jy = njy;
-      mx = nmx;
-      my = nmy;
+      lo.rb = qb;
+      lo.w = make_row(nr, np, ner, nep, qb);
+      cm = njm;
+      if constexpr (K == 2) stash = qjm;
     }
   };
 
@@ -482,13 +786,13 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const Phys<float>& P
   }
 }
 
-template <int NW>
+template <int NW, class S>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 3 : (NW == 4 ? 7 : 14)) moment_step_kernel(MomArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int cb, band;
   tile_of_block((a.G.nx + NW * kMomCols - 1) / (NW * kMomCols), cb, band);
   const int y0 = band * a.yc;
-  moment_strip<false>(a.G, a.P, a.src, a.dst, (cb * NW + warp) * kMomCols, y0, min(y0 + a.yc, a.G.ny), lane);
+  moment_strip<false, S>(a.G, a.Q, a.src, a.dst, (cb * NW + warp) * kMomCols, y0, min(y0 + a.yc, a.G.ny), lane);
 }
 
 }  // namespace lbk

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 
 namespace lbk {
@@ -26,6 +27,15 @@ inline int device_sm_count() {
   }
   return cache[dev];
 }
+
+// An NVTX range around a host call (named in timelines of profilers; a no-op
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL, OP_MOMENTS_OUT };
 
@@ -67,5 +77,7 @@ cudaError_t ops_bin_f64(OpKind, const OpArgs&, cudaStream_t);
 cudaError_t ops_bin_f32(OpKind, const OpArgs&, cudaStream_t);
 cudaError_t ops_bin_f16(OpKind, const OpArgs&, cudaStream_t);
 cudaError_t ops_bin_m32(OpKind, const OpArgs&, cudaStream_t);  // moment storage
+cudaError_t ops_bin_m16(OpKind, const OpArgs&, cudaStream_t);  // FP16 moments, FP32 phi
+cudaError_t ops_bin_g32(OpKind, const OpArgs&, cudaStream_t);  // f and phi (g eliminated)
 
 }  // namespace lbk

@@ -76,16 +76,16 @@ static cudaError_t launch_staged(const OpArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NW>
+template <int NW, class S>
 static cudaError_t launch_moment(const OpArgs& a, cudaStream_t s) {
   MomArgs k;
   k.G = to_geom(a);
-  k.P = to_phys<float>(a);
-  k.src = (const float*)a.src.f;
-  k.dst = (float*)a.dst.f;
+  k.Q = mom_phys(a.kappa, a.Acoef, a.M, a.nu_l, a.nu_g, a.lambda_scale, a.h, a.lut);
+  k.src = a.src.f;
+  k.dst = a.dst.f;
   k.yc = a.yc;
   const unsigned grid = tiles_1d((a.nx + NW * kMomCols - 1) / (NW * kMomCols), a.ny, a.yc);
-  moment_step_kernel<NW><<<grid, NW * 32, 0, s>>>(k);
+  moment_step_kernel<NW, S><<<grid, NW * 32, 0, s>>>(k);
   return cudaGetLastError();
 }
 
@@ -97,12 +97,13 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
   if constexpr (is_moments<S>::value) {
     static_assert(MODEL == MODEL_BINARY, "the moment storage holds the binary model");
     if (op == OP_STEP) {
-      if (a.bx == 64) return launch_moment<2>(a, s);
-      if (a.bx == 128) return launch_moment<4>(a, s);
-      if (a.bx == 256) return launch_moment<8>(a, s);
+      if (a.bx == 64) return launch_moment<2, S>(a, s);
+      if (a.bx == 128) return launch_moment<4, S>(a, s);
+      if (a.bx == 256) return launch_moment<8, S>(a, s);
       return cudaErrorInvalidValue;
     }
-    if (op == OP_POPS_OUT) return cudaErrorNotSupported;  // populations are not kept
+    // the moment storages keep no populations (g eliminated keeps f and phi)
+    if (op == OP_POPS_OUT && pull_kind<S>::value != 2) return cudaErrorNotSupported;
   }
   switch (op) {
     case OP_STEP:
@@ -127,7 +128,7 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
       fields_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src, a), a.out0, a.out1, a.out2, a.out3);
       return cudaGetLastError();
     case OP_POPS_OUT:
-      if constexpr (!is_moments<S>::value)
+      if constexpr (!is_moments<S>::value || pull_kind<S>::value == 2)
         pops_out_kernel<MODEL, S><<<grid_for(N, 256), 256, 0, s>>>(G, to_buf<S>(a.src, a), a.flag, a.out0, a.out1);
       return cudaGetLastError();
     case OP_MOMENTS_OUT:

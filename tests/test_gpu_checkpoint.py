@@ -16,8 +16,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STORAGE_MOMENTS, Batch,  # noqa: E402
-                                   Lattice, LbError)
+from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_GELIM, STORAGE_F64,  # noqa: E402
+                                   STORAGE_MOMENTS, STORAGE_MOMENTS_F16, Batch, Lattice, LbError)
 
 
 def capillary(storage):
@@ -25,7 +25,8 @@ def capillary(storage):
                        W.binary_params(nu_l=0.8, nu_g=0.08, storage=storage), theta_deg=50.0)
 
 
-@pytest.mark.parametrize("storage", [STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS])
+@pytest.mark.parametrize("storage", [STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS,
+                                     STORAGE_MOMENTS_F16, STORAGE_F32_GELIM])
 def test_lattice_checkpoint_resumes_bit_for_bit(storage, tmp_path):
     cap = capillary(storage)
     a = Lattice.from_workload(cap)
@@ -41,7 +42,7 @@ def test_lattice_checkpoint_resumes_bit_for_bit(storage, tmp_path):
     got, tb = b.save_state()
     assert tb == t == 138 and np.array_equal(got, ref)
     # a poisoned context takes a checkpoint and runs on
-    f, g = b.populations(False) if storage != STORAGE_MOMENTS else (None, None)
+    f, g = b.populations(False) if storage not in (STORAGE_MOMENTS, STORAGE_MOMENTS_F16) else (None, None)
     if f is not None:
         f[0, 10, 70] = np.nan
         b.set_populations(f, g)
