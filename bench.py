@@ -132,7 +132,7 @@ def step_kernel_label(variant, tx, ty, storage="FP32"):
         return (f"step_tma_kernel<binary, {storage}, BX={tx}, NS={STAGED_NS[variant][tx]}> "
                 f"(variant {variant}, tile {tx}x{ty})")
     if variant == 4:
-        return f"moment_step_kernel (tile {tx}x{ty})"
+        return f"moment_step_kernel<{storage}> (tile {tx}x{ty})"
     return f"step_kernel<binary, {storage}, BX={tx}> (variant {variant}, tile {tx}x{ty})"
 
 
@@ -159,10 +159,16 @@ def fluid_nodes_of(cap):
     return cap.nx * cap.ny - solid
 
 
-def bench_config(cap, world):
+# algorithmic bytes per fluid-node update and the name of each storage
+STORAGES = {"f32": (144.0, "FP32 storage", "FP32"), "f16dev": (76.0, "FP16-deviation storage", "FP16dev"),
+            "moments": (48.0, "FP32 moment storage", "SM32"), "moments_f16": (28.0, "FP16 moment storage", "SM16"),
+            "gelim": (80.0, "FP32 f + phi storage (g eliminated)", "SG32")}
+
+
+def bench_config(cap, world, storage="f32"):
     """The `config` object of both arms' JSON lines (the same workload)."""
     return {"workload": "binary_16384x256: H=200 tube over x in [512, 16384), gas 128 cols, "
-                        "viscosity ratio 50 (0.83/0.0166), theta 45 deg, FP32 storage",
+                        f"viscosity ratio 50 (0.83/0.0166), theta 45 deg, {STORAGES[storage][1]}",
             "nodes": cap.nx * cap.ny, "fluid_nodes": fluid_nodes_of(cap), "reductions_every": RED_EVERY,
             "l2": "no flush: state 2 x 302 MB > 129 MB L2", "parallelism": f"replicas x{world}"}
 
@@ -455,7 +461,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="BX,YC: fixed step-kernel tile instead of autotuning")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "moments"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "moments", "moments_f16", "gelim"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep secondary metric")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate secondary metric")
@@ -470,7 +476,8 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_0911_0459_gb300 import STORAGE_F16DEV, STORAGE_F32, STORAGE_MOMENTS, Lattice
+    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_GELIM, STORAGE_MOMENTS,
+                                       STORAGE_MOMENTS_F16, Lattice)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -480,8 +487,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    cap = W.config_binary_16384x256({"f32": STORAGE_F32, "f16dev": STORAGE_F16DEV,
-                                     "moments": STORAGE_MOMENTS}[args.storage])
+    cap = W.config_binary_16384x256({"f32": STORAGE_F32, "f16dev": STORAGE_F16DEV, "moments": STORAGE_MOMENTS,
+                                     "moments_f16": STORAGE_MOMENTS_F16, "gelim": STORAGE_F32_GELIM}[args.storage])
     lat = Lattice.from_workload(cap)
     if args.tile:
         tx, ty = (int(v) for v in args.tile.split(","))
@@ -514,8 +521,9 @@ def main():
     value = world * fluid * args.steps / (total_max * 1e-3) / 1e6
     l_end = lat.filled_length()
 
-    # roofline of the step kernel: algorithmic bytes = fluid nodes x 18 planes x 4 B x (read + write)
-    bytes_per_lu = 144.0
+    # roofline of the step kernel: algorithmic bytes = fluid nodes x the storage's bytes per update
+    # (FP32: 18 planes x 4 B x (read + write))
+    bytes_per_lu = STORAGES[args.storage][0]
     per_launch_ms = step_ms / args.steps
     achieved = fluid * bytes_per_lu / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
@@ -640,10 +648,11 @@ def main():
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": bench_config(cap, world),
+            "config": bench_config(cap, world, args.storage),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": step_kernel_label(kernel_variant, tx, ty), "bytes_per_lu": bytes_per_lu,
+                         "kernel": step_kernel_label(kernel_variant, tx, ty, STORAGES[args.storage][2]),
+                         "bytes_per_lu": bytes_per_lu,
                          "peak_source": f"{peak_kind} copy bandwidth (HBM, burst)",
                          "us_per_launch": 1e3 * per_launch_ms,
                          "kernel_mlups": kernel_mlups,
