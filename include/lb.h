@@ -207,6 +207,18 @@ size_t lb_state_bytes(const lb_ctx *ctx);
 lb_status lb_save_state(lb_ctx *ctx, void *host, size_t bytes);
 lb_status lb_load_state(lb_ctx *ctx, const void *host, size_t bytes, long time);
 
+/* Bounds-checked debug build of the library (compiled with -DLB_CHECK): every
+ * global load and store of the step kernels checks its index against its
+ * buffer; an index outside is counted, the first one recorded and the access
+ * skipped (a load reads 0), with no trap.  This call returns the count of such
+ * accesses and the first offending element index + 1 since the last call (the
+ * counters are then cleared), with *enabled = 1.  The counters belong to the
+ * kernels of the context's model and storage and count every lattice of that
+ * model and storage in the process.  In the normal build *enabled, *bad and
+ * *first_bad are 0.  Any pointer may be NULL.  Waits for the device. */
+lb_status lb_check_report(lb_ctx *ctx, int *enabled, unsigned long long *bad,
+                          unsigned long long *first_bad);
+
 /* Wait for all work issued on the context's stream; LB_ERR_TIMEOUT if a
  * device-side wait of the step kernel gave up since the state was set. */
 lb_status lb_sync(lb_ctx *ctx);
@@ -322,6 +334,11 @@ lb_status lb_batch_get_kernel(const lb_batch *b, int *variant);
  * state is unreliable and the next waiting call returns LB_ERR_TIMEOUT.  The
  * staged body's shared-memory waits use a fixed 2 s limit. */
 lb_status lb_batch_set_barrier(lb_batch *b, unsigned int absent_blocks, double limit_seconds);
+
+/* As lb_check_report, for the persistent batch kernels (every batch in the
+ * process). */
+lb_status lb_batch_check_report(lb_batch *b, int *enabled, unsigned long long *bad,
+                                unsigned long long *first_bad);
 
 long lb_batch_time(const lb_batch *b);
 /* Fluid nodes of lattice i, or of the whole batch for i < 0. */

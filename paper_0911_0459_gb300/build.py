@@ -42,8 +42,17 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), variant: str = "") -> str:
+    """Compile and link the library; variant="check" builds the bounds-checked debug
+    library (-DLB_CHECK) into _lib/check/ instead."""
+    out_dir, lib = OUT, LIB
+    if variant == "check":
+        out_dir = os.path.join(OUT, "check")
+        lib = os.path.join(out_dir, "liblbgb300.so")
+        extra = ("-DLB_CHECK", *extra)
+    elif variant:
+        raise ValueError(f"unknown variant {variant!r}")
+    os.makedirs(out_dir, exist_ok=True)
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     flags = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -51,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([nvcc(), *flags, "-c", src, "-o", obj])
@@ -63,19 +72,20 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or not os.path.exists(LIB):
+    if force or jobs or not os.path.exists(lib):
         libdir = cuda_libdir()
-        cmd = [nvcc(), "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-cudart", "shared",
+        cmd = [nvcc(), "-shared", *ARCH, "-o", lib + ".tmp", *objs, "-cudart", "shared",
                "-L", libdir, "-Xlinker", "-rpath=" + libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(force="--force" in sys.argv, verbose=v or bool(extra), extra=extra))
+    print(build(force="--force" in sys.argv, verbose=v or bool(extra), extra=extra,
+                variant="check" if "--check" in sys.argv else ""))

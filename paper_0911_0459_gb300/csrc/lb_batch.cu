@@ -897,6 +897,17 @@ lb_status lb_batch_get_kernel(const lb_batch* b, int* variant) {
   return LB_OK;
 }
 
+lb_status lb_batch_check_report(lb_batch* b, int* enabled, unsigned long long* bad, unsigned long long* first_bad) {
+  if (!b) return LB_ERR_ARG;
+  BCK(cudaStreamSynchronize(b->stream));
+  unsigned long long h[3] = {0, 0, 0};
+  BCK(read_check_counters(h));
+  if (enabled) *enabled = (int)h[0];
+  if (bad) *bad = h[1];
+  if (first_bad) *first_bad = h[2];
+  return LB_OK;
+}
+
 long lb_batch_time(const lb_batch* b) { return b ? b->t : -1; }
 
 long lb_batch_fluid_nodes(const lb_batch* b, int i) {

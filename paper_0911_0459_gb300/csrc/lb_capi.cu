@@ -587,6 +587,19 @@ lb_status lb_inject_wait_timeout(lb_ctx* c) {
   return LB_OK;
 }
 
+lb_status lb_check_report(lb_ctx* c, int* enabled, unsigned long long* bad, unsigned long long* first_bad) {
+  if (!c) return LB_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned long long h[3] = {0, 0, 0};
+  OpArgs a = base_args(c);
+  a.check_out = h;
+  CK(c->ops(OP_CHECK, a, c->stream));
+  if (enabled) *enabled = (int)h[0];
+  if (bad) *bad = h[1];
+  if (first_bad) *first_bad = h[2];
+  return LB_OK;
+}
+
 lb_status lb_sync(lb_ctx* c) {
   if (!c) return LB_ERR_ARG;
   CK(cudaStreamSynchronize(c->stream));

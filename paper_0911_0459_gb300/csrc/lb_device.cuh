@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace lbk {
@@ -41,6 +42,52 @@ struct Phys {
   A h;                 // wall gradient of the wetted field
   A lut, lut_inv;      // viscosity table of App. A: K - 1 steps (0: exact nu) and 1 / (K - 1)
 };
+
+// ---------------------------------------------------------- bounds checks
+//
+// Debug build (-DLB_CHECK): every global load and store of the step kernels
+// checks its element index against its buffer.  An index outside records
+// itself in two device words of the translation unit (a count and the first
+// offending index + 1) and the access is skipped (a load gives 0); nothing
+// traps.  In the normal build the checks compile to nothing.
+#ifdef LB_CHECK
+static __device__ unsigned long long lb_check_hits;
+static __device__ unsigned long long lb_check_first;
+__device__ __forceinline__ bool lb_in(unsigned long long idx, unsigned long long lim) {
+  if (idx < lim) return true;
+  atomicAdd(&lb_check_hits, 1ull);
+  atomicCAS(&lb_check_first, 0ull, idx + 1);
+  return false;
+}
+#define LB_GUARD(idx, lim, ret)                                                       \
+  do {                                                                                \
+    if (!::lbk::lb_in((unsigned long long)(idx), (unsigned long long)(lim))) return ret; \
+  } while (0)
+#else
+#define LB_GUARD(idx, lim, ret) \
+  do {                          \
+  } while (0)
+#endif
+
+// Host side: read and clear this translation unit's counters into
+// out = {enabled, bad accesses, first bad index + 1}.
+inline cudaError_t read_check_counters(unsigned long long* out) {
+#ifdef LB_CHECK
+  unsigned long long h = 0, f = 0, z = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&h, lb_check_hits, sizeof h);
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&f, lb_check_first, sizeof f);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(lb_check_hits, &z, sizeof z);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(lb_check_first, &z, sizeof z);
+  out[0] = 1;
+  out[1] = h;
+  out[2] = f;
+  return e;
+#else
+  out[0] = out[1] = out[2] = 0;
+  return cudaSuccess;
+#endif
+}
 
 // ------------------------------------------------------------------ storage
 
@@ -65,21 +112,37 @@ struct SF64 {
   __device__ static A pf(const T* f, int W, int c, int i, const Rest&) { return f[i * W + c]; }
   __device__ static A pg(const T* g, const float*, int W, int c, int i) { return g[i * W + c]; }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
     return __ldg(f + i * N + n);
   }
-  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) { f[i * N + n] = v; }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) {
+    LB_GUARD(i * N + n, 9 * N, );
+    f[i * N + n] = v;
+  }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
     return __ldg(g + i * N + n);
   }
-  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) {
+    LB_GUARD(i * N + n, 9 * N, );
+    g[i * N + n] = v;
+  }
   // L2-coherent loads, for buffers written earlier in the same launch
-  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) { return __ldcg(f + i * N + n); }
-  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
+    return __ldcg(f + i * N + n);
+  }
+  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
+    return __ldcg(g + i * N + n);
+  }
   // stores at 32-bit element offsets (node n of plane i at i * N + n; needs 9N < 2^32)
   __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
+    LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     f[i * N + n] = v;
   }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
+    LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     g[i * N + n] = v;
   }
 };
@@ -90,19 +153,35 @@ struct SF32 {
   __device__ static A pf(const T* f, int W, int c, int i, const Rest&) { return f[i * W + c]; }
   __device__ static A pg(const T* g, const float*, int W, int c, int i) { return g[i * W + c]; }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
     return __ldg(f + i * N + n);
   }
-  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) { f[i * N + n] = v; }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) {
+    LB_GUARD(i * N + n, 9 * N, );
+    f[i * N + n] = v;
+  }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
     return __ldg(g + i * N + n);
   }
-  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) { g[i * N + n] = v; }
-  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) { return __ldcg(f + i * N + n); }
-  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) { return __ldcg(g + i * N + n); }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) {
+    LB_GUARD(i * N + n, 9 * N, );
+    g[i * N + n] = v;
+  }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
+    return __ldcg(f + i * N + n);
+  }
+  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
+    return __ldcg(g + i * N + n);
+  }
   __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
+    LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     f[i * N + n] = v;
   }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
+    LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     g[i * N + n] = v;
   }
 };
@@ -118,31 +197,39 @@ struct SF16 {
     return i == 0 ? g0[c] : __half2float(g[(i - 1) * W + c]);
   }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest& r) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
     return __half2float(__ldg(f + i * N + n)) + rest_w(r, i);
   }
   __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest& r) {
+    LB_GUARD(i * N + n, 9 * N, );
     f[i * N + n] = __float2half_rn(v - rest_w(r, i));
   }
   __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest& r) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
     return __half2float(__ldcg(f + i * N + n)) + rest_w(r, i);
   }
   __device__ static A lgc(const T* g, const float* g0, size_t N, size_t n, int i) {
+    LB_GUARD(i == 0 ? n : (i - 1) * N + n, i == 0 ? N : 8 * N, A(0));
     return i == 0 ? __ldcg(g0 + n) : __half2float(__ldcg(g + (i - 1) * N + n));
   }
   // g_1..g_8 in FP16 planes 0..7; g_0 (which carries phi) in an FP32 plane.
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__ g0, size_t N, size_t n, int i) {
+    LB_GUARD(i == 0 ? n : (i - 1) * N + n, i == 0 ? N : 8 * N, A(0));
     return i == 0 ? __ldg(g0 + n) : __half2float(__ldg(g + (i - 1) * N + n));
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__ g0, size_t N, size_t n, int i, A v) {
+    LB_GUARD(i == 0 ? n : (i - 1) * N + n, i == 0 ? N : 8 * N, );
     if (i == 0)
       g0[n] = v;
     else
       g[(i - 1) * N + n] = __float2half_rn(v);
   }
   __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest& r) {
+    LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     f[i * N + n] = __float2half_rn(v - rest_w(r, i));
   }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__ g0, uint32_t N, uint32_t n, int i, A v) {
+    LB_GUARD(i == 0 ? (unsigned long long)n : (unsigned long long)(i - 1) * N + n, i == 0 ? N : 8ull * N, );
     if (i == 0)
       g0[n] = v;
     else

@@ -483,6 +483,13 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
   // rho - 1 and phi of node o; SG32 also gives the node's j and stresses, from
   // the same f (the step keeps them until the row's collision)
   auto load_node_rp = [&](unsigned o, float& rv, float& pv, JM& m) {
+#ifdef LB_CHECK
+    if (!lb_in(o, N)) {  // every plane holds N nodes
+      rv = pv = 0.f;
+      m = JM{0.f, 0.f, 0.f, 0.f};
+      return;
+    }
+#endif
     if constexpr (K == 0) {
       const float2 v = ldf2(reinterpret_cast<const float2*>(sb) + MP_RP * N + o);
       rv = v.x;
@@ -525,6 +532,12 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
   auto load_jm = [&](unsigned rowb, bool in_band, JM& m) {
     if constexpr (K == 0 || K == 1) {
       const unsigned o = rowb + x;
+#ifdef LB_CHECK
+      if (!lb_in(o, N)) {
+        m = JM{0.f, 0.f, 0.f, 0.f};
+        return;
+      }
+#endif
       if constexpr (K == 0) {
         const float2 j = ldf2(reinterpret_cast<const float2*>(sb) + MP_J * N + o);
         const float2 s = ldf2(reinterpret_cast<const float2*>(sb) + MP_S * N + o);
@@ -744,6 +757,9 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
       // row k - 1 has received everything
       if (k > y0 && store_lane && !(tc1 && !lo.rb)) {
         const unsigned o = (unsigned)lo.y * nx + x;
+#ifdef LB_CHECK
+        if (lb_in(o, N))
+#endif
         if constexpr (K == 0) {
           float2* P = reinterpret_cast<float2*>(db);
           P[MP_RP * N + o] = make_float2(a0.r, a0.p);

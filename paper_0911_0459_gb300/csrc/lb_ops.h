@@ -37,7 +37,8 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
-enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL, OP_MOMENTS_OUT };
+enum OpKind { OP_STEP, OP_INIT, OP_FIELDS, OP_POPS_OUT, OP_POPS_IN, OP_RED_PARTIALS, OP_RED_FINAL, OP_MOMENTS_OUT,
+              OP_CHECK };
 
 struct OpBufs {
   void* f;
@@ -67,6 +68,7 @@ struct OpArgs {
   int nparts;    // reduction partial blocks
   double* partials;
   double* red_out;
+  unsigned long long* check_out;  // OP_CHECK: host array {enabled, bad accesses, first bad index + 1}
 };
 
 typedef cudaError_t (*OpsFn)(OpKind, const OpArgs&, cudaStream_t);

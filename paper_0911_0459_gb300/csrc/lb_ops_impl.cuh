@@ -141,6 +141,8 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
       reduce_partials_kernel<MODEL, S><<<a.nparts, RED_THREADS, 0, s>>>(G, to_buf<S>(a.src, a), a.rho_l, a.rho_g, a.thr,
                                                                         a.partials);
       return cudaGetLastError();
+    case OP_CHECK:
+      return read_check_counters(a.check_out);
     case OP_RED_FINAL:
       reduce_final_kernel<MODEL, S><<<1, 32, 0, s>>>(G, to_buf<S>(a.src, a), a.thr, a.nparts, a.partials, a.red_out);
       return cudaGetLastError();

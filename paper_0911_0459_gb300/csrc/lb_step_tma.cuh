@@ -92,6 +92,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Source of a bulk copy of cnt elements at element offset off of a buffer of
+// lim elements.  In the bounds-checked build a range that leaves the buffer is
+// recorded and the copy reads the buffer's start instead (same size, so the
+// barrier's byte count still completes).
+template <class T>
+__device__ __forceinline__ const T* copy_src(const T* base, size_t off, size_t cnt, size_t lim) {
+#ifdef LB_CHECK
+  if (!lb_in(off + cnt - 1, lim)) return base;
+#endif
+  return base + off;
+}
+
 template <class S>
 struct NGPlanes {
   static constexpr int value = 9;
@@ -187,12 +199,13 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const uint32_t ecols = (uint32_t)(ncols + (wl ? 8 : 0) + (wr ? 8 : 0));
   const uint32_t total = ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
   auto planes = [&](const T* base, int nplanes, T* dst0, size_t rowoff, uint64_t* bar) {
+    const size_t lim = (size_t)nplanes * N;
     for (int i = 0; i < nplanes; ++i) {
-      const T* sp = base + (size_t)i * N + rowoff;
+      const size_t po = (size_t)i * N + rowoff;
       T* d = dst0 + i * W;
-      bulk_g2s(d + so, sp + lo, (uint32_t)ncols * sizeof(T), bar);
-      if (wl) bulk_g2s(d, sp + (nx - 8), 8 * sizeof(T), bar);
-      if (wr) bulk_g2s(d + sr, sp, 8 * sizeof(T), bar);
+      bulk_g2s(d + so, copy_src(base, po + lo, (size_t)ncols, lim), (uint32_t)ncols * sizeof(T), bar);
+      if (wl) bulk_g2s(d, copy_src(base, po + (nx - 8), 8, lim), 8 * sizeof(T), bar);
+      if (wr) bulk_g2s(d + sr, copy_src(base, po, 8, lim), 8 * sizeof(T), bar);
     }
   };
   // every staged column inside the tube: rows outside the band are all solid and
@@ -215,11 +228,10 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     planes(src.f, L::NF, R.f(s), rowoff, &R.full[s]);
     if (BIN) planes(src.g, L::NG, R.g(s), rowoff, &R.full[s]);
     if (L::NG0) {
-      const float* sp = src.g0 + rowoff;
       float* d = R.g0(s);
-      bulk_g2s(d + so, sp + lo, (uint32_t)ncols * 4u, &R.full[s]);
-      if (wl) bulk_g2s(d, sp + (nx - 8), 32u, &R.full[s]);
-      if (wr) bulk_g2s(d + sr, sp, 32u, &R.full[s]);
+      bulk_g2s(d + so, copy_src(src.g0, rowoff + lo, (size_t)ncols, N), (uint32_t)ncols * 4u, &R.full[s]);
+      if (wl) bulk_g2s(d, copy_src(src.g0, rowoff + (nx - 8), 8, N), 32u, &R.full[s]);
+      if (wr) bulk_g2s(d + sr, copy_src(src.g0, rowoff, 8, N), 32u, &R.full[s]);
     }
     issued = k + 1;
   }

@@ -15,7 +15,8 @@ from typing import Optional
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblbgb300.so")
+# LB_GB300_LIBRARY selects another build of the same library (the bounds-checked one)
+LIB_PATH = os.environ.get("LB_GB300_LIBRARY") or os.path.join(_PKG, "_lib", "liblbgb300.so")
 
 LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_TIMEOUT, LB_ERR_STATE, LB_ERR_NOMEM = range(7)
 STATUS_NAMES = ["LB_OK", "LB_ERR_ARG", "LB_ERR_CUDA", "LB_ERR_NONFINITE", "LB_ERR_TIMEOUT",
@@ -82,6 +83,9 @@ def library():
         "lb_set_populations": (C.c_int, [vp, dp, dp]),
         "lb_sync": (C.c_int, [vp]),
         "lb_inject_wait_timeout": (C.c_int, [vp]),
+        "lb_check_report": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)]),
+        "lb_batch_check_report": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_ulonglong),
+                                            C.POINTER(C.c_ulonglong)]),
         "lb_state_bytes": (C.c_size_t, [vp]),
         "lb_save_state": (C.c_int, [vp, vp, C.c_size_t]),
         "lb_load_state": (C.c_int, [vp, vp, C.c_size_t, C.c_long]),
@@ -124,7 +128,8 @@ def library():
 
 def exported_symbols():
     return ["lb_create", "lb_destroy", "lb_init_fields", "lb_step", "lb_fields", "lb_filled_length",
-            "lb_get_populations", "lb_set_populations", "lb_get_moments", "lb_sync", "lb_inject_wait_timeout", "lb_time", "lb_fluid_nodes",
+            "lb_get_populations", "lb_set_populations", "lb_get_moments", "lb_sync", "lb_inject_wait_timeout",
+            "lb_check_report", "lb_batch_check_report", "lb_time", "lb_fluid_nodes",
             "lb_set_tile", "lb_get_tile", "lb_autotune", "lb_last_error", "lb_set_kernel", "lb_get_kernel",
             "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_lengths", "lb_batch_run_sampled",
             "lb_batch_populations", "lb_batch_moments", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
@@ -240,6 +245,12 @@ class Lattice:
     def step(self, n=1):
         _check(library().lb_step(self.h, int(n)), self.h)
         return self
+
+    def check_report(self):
+        """Bounds-checked build: (enabled, bad accesses, first bad index + 1) since the last call."""
+        e, b, f = C.c_int(), C.c_ulonglong(), C.c_ulonglong()
+        _check(library().lb_check_report(self.h, C.byref(e), C.byref(b), C.byref(f)), self.h)
+        return e.value, b.value, f.value
 
     def inject_wait_timeout(self):
         """Failure injection for tests: mark the device error word as a timed-out wait does."""
@@ -381,6 +392,15 @@ class Batch:
     @property
     def stream(self):
         return self._torch_stream
+
+    def check_report(self):
+        """Bounds-checked build: (enabled, bad accesses, first bad index + 1) of the batch kernels."""
+        e, b, f = C.c_int(), C.c_ulonglong(), C.c_ulonglong()
+        L = library()
+        st = L.lb_batch_check_report(self.h, C.byref(e), C.byref(b), C.byref(f))
+        if st != LB_OK:
+            raise LbError(st, L.lb_batch_last_error(self.h).decode(errors="replace"))
+        return e.value, b.value, f.value
 
     def close(self):
         if getattr(self, "h", None) is not None:
