@@ -46,6 +46,8 @@
 
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lb_device.cuh"
 
 namespace lbk {
@@ -442,7 +444,9 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
   struct Row {
     float rc, rs, rh, pc, ps, ph;  // rh, ph hold d
   };
-  auto make_row = [&](float r, float p, float re, float pe, bool in_band) {
+  // WALL: the row may hold solid nodes under this warp's columns (else the
+  // solid handling is compiled out)
+  auto make_row = [&](float r, float p, float re, float pe, bool in_band, auto WALL) {
     Row w;
     float rl = __shfl_up_sync(FULL, r, 1), rr = __shfl_down_sync(FULL, r, 1);
     float pl = __shfl_up_sync(FULL, p, 1), pr = __shfl_down_sync(FULL, p, 1);
@@ -454,7 +458,7 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
       rr = re;
       pr = pe;
     }
-    if (warp_tube && !in_band) {
+    if (decltype(WALL)::value && warp_tube && !in_band) {
       if (tc1) {
         r = 0.f;
         p = 0.f;
@@ -574,12 +578,12 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
     float r, p, re, pe;
     JM m;
     load_rp((unsigned)S0.y * nx, S0.rb, r, p, re, pe, m);
-    S0.w = make_row(r, p, re, pe, S0.rb);
+    S0.w = make_row(r, p, re, pe, S0.rb, std::true_type{});
     load_rp((unsigned)S1.y * nx, S1.rb, r, p, re, pe, m);
-    S1.w = make_row(r, p, re, pe, S1.rb);
+    S1.w = make_row(r, p, re, pe, S1.rb, std::true_type{});
     cm = m;
     load_rp((unsigned)S2.y * nx, S2.rb, r, p, re, pe, m);
-    S2.w = make_row(r, p, re, pe, S2.rb);
+    S2.w = make_row(r, p, re, pe, S2.rb, std::true_type{});
     stash = m;
     if constexpr (K != 2) load_jm((unsigned)S1.y * nx, S1.rb, cm);
   }
@@ -597,7 +601,10 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
 
   // collision row k: slots lo/mid/hi hold rows k - 1, k, k + 1; accumulators
   // a0 (row k - 1, stored here), a1 (row k) and a2 (row k + 1, started here)
-  auto step = [&](Slot& lo, Slot& mid, Slot& hi, PullAcc<S>& a0, PullAcc<S>& a1, PullAcc<S>& a2, int k) {
+  // WALL (std::true_type / std::false_type): whether walls can touch this strip's
+  // rows; without, the step is compiled with no wall code at all
+  auto step = [&](Slot& lo, Slot& mid, Slot& hi, PullAcc<S>& a0, PullAcc<S>& a1, PullAcc<S>& a2, int k, auto WALL) {
+    constexpr bool CW = decltype(WALL)::value;
     // next rows in flight while this one collides
     const int yq = next_row(hi.y);  // row k + 2
     const bool qb = row_in_band(G, yq);
@@ -612,11 +619,11 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
       load_rp((unsigned)yq * nx, qb, nr, np, ner, nep, qjm);
     }
     // a row whose whole window is wall under every column sends and stores nothing
-    const bool all_wall = warp_all_tube && !lo.rb && !mid.rb && !hi.rb;
+    const bool all_wall = CW && warp_all_tube && !lo.rb && !mid.rb && !hi.rb;
     if (!all_wall) {
       // walls can touch this warp only if it has tube columns and a row leaves the
       // band (warp-uniform); otherwise every node is fluid with fluid neighbours
-      const bool walls = warp_tube && !(lo.rb && mid.rb && hi.rb);
+      const bool walls = CW && warp_tube && !(lo.rb && mid.rb && hi.rb);
       float fs[9], ge[9];
       // populations the own node sent into a wall, returned to it (bounce-back)
       bool bounce[9] = {false, false, false, false, false, false, false, false, false};
@@ -784,22 +791,36 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
       // row k + 2 takes the slot of row k - 1
       lo.y = yq;
       lo.rb = qb;
-      lo.w = make_row(nr, np, ner, nep, qb);
+      lo.w = make_row(nr, np, ner, nep, qb, WALL);
       cm = njm;
       if constexpr (K == 2) stash = qjm;
     }
   };
 
-  int k = y0 - 1;
+  // Walls can touch the strip only if the warp has tube columns and one of the
+  // rows y0 - 2 .. y1 + 1 leaves the band (warp-uniform).  Most strips of a long
+  // tube lie inside the band, and their loop holds no wall code: compiled in, the
+  // rarely taken wall path still cost the fast path about a tenth of its
+  // instructions (values the compiler computes ahead of the branch).
+  const int nrow = y1 - y0 + 4;
+  const int d0 = ((y0 - 2 - G.tube_y0) % ny + ny) % ny;
+  const bool strip_walls = warp_tube && !(d0 + nrow <= G.tube_h);
+  auto run = [&](auto WALL) {
+    int k = y0 - 1;
 #pragma unroll 1
-  while (true) {
-    step(S0, S1, S2, A0, A1, A2, k);
-    if (++k > y1) break;
-    step(S1, S2, S0, A1, A2, A0, k);
-    if (++k > y1) break;
-    step(S2, S0, S1, A2, A0, A1, k);
-    if (++k > y1) break;
-  }
+    while (true) {
+      step(S0, S1, S2, A0, A1, A2, k, WALL);
+      if (++k > y1) break;
+      step(S1, S2, S0, A1, A2, A0, k, WALL);
+      if (++k > y1) break;
+      step(S2, S0, S1, A2, A0, A1, k, WALL);
+      if (++k > y1) break;
+    }
+  };
+  if (strip_walls)
+    run(std::true_type{});
+  else
+    run(std::false_type{});
 }
 
 template <int NW, class S>
