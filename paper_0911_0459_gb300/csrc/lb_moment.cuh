@@ -418,6 +418,7 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
   const int xp = x + 1 == nx ? 0 : x + 1;
   const bool edge = lane == 0 || lane == 31;
   const int xe = lane == 0 ? xm : xp;                  // outer stencil column of an edge lane
+  const int xo_own_or_edge = edge ? xe : x;
   const bool store_lane = lane >= 1 && lane <= kMomCols && xl < nx;
   const bool tubed = G.tube_len > 0;
   const bool tc0 = tubed && col_in_tube(G, xm);
@@ -450,14 +451,11 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
     Row w;
     float rl = __shfl_up_sync(FULL, r, 1), rr = __shfl_down_sync(FULL, r, 1);
     float pl = __shfl_up_sync(FULL, p, 1), pr = __shfl_down_sync(FULL, p, 1);
-    if (lane == 0) {
-      rl = re;
-      pl = pe;
-    }
-    if (lane == 31) {
-      rr = re;
-      pr = pe;
-    }
+    // the edge lanes' outer neighbours (selects, not branches)
+    rl = lane == 0 ? re : rl;
+    pl = lane == 0 ? pe : pl;
+    rr = lane == 31 ? re : rr;
+    pr = lane == 31 ? pe : pr;
     if (decltype(WALL)::value && warp_tube && !in_band) {
       if (tc1) {
         r = 0.f;
@@ -526,11 +524,11 @@ __device__ __forceinline__ void moment_strip(const Geom& G, const MomPhys& Q, co
         load_node_rp(rowb + xe, re, pe, unused);
       }
     } else {
+      // every lane reads an "edge" value (its own node again unless it is an edge
+      // lane): one more load, no divergent branch
       load_node_rp(rowb + x, rv, pv, m);
-      if (edge) {
-        JM unused;
-        load_node_rp(rowb + xe, re, pe, unused);
-      }
+      JM unused;
+      load_node_rp(rowb + xo_own_or_edge, re, pe, unused);
     }
   };
   auto load_jm = [&](unsigned rowb, bool in_band, JM& m) {
