@@ -31,6 +31,8 @@
 // issued before it exits, so no copy lands in released shared memory.
 #pragma once
 
+#include <type_traits>
+
 #include "lb_device.cuh"
 
 namespace lbk {
@@ -342,7 +344,12 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     if (lane == 0) mbar_arrive(&R.empty[k % NS]);
   }
 
-  for (int y = y0; y < y1; ++y) {
+  // One collision row y.  WALL (std::true_type / std::false_type): whether walls
+  // can touch this tile's rows under this warp; without, the row is compiled with
+  // no wall code (no solid tests, ghosts, rest rule or bounce-back), which the
+  // node arithmetic does not depend on.
+  auto row_step = [&](int y, auto WALL) -> bool {
+    constexpr bool CW = decltype(WALL)::value;
     const unsigned kn = kbase + (y - y0) + 2;  // ring row of y + 1
     const int sn = kn % NS;
     // shift the row window and add row y + 1
@@ -350,7 +357,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     Rw[1] = Rw[2];
     if (!__all_sync(0xffffffffu, mbar_wait(&R.full[sn], (kn / NS) & 1))) return false;
     A fn[9], gn[9];
-    sums(sn, fn, gn, Rw[2], solid_row(y + 1));
+    sums(sn, fn, gn, Rw[2], CW && solid_row(y + 1));
     __syncwarp();
     if (lane == 0) mbar_arrive(&R.empty[sn]);
     A vr[3][3], vp[3][3];
@@ -368,38 +375,59 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     const int yy = wrapi(y, ny);
     const int ym = yy == 0 ? ny - 1 : yy - 1;
     const int yp = yy + 1 >= ny ? 0 : yy + 1;
-    const bool rb[3] = {row_in_band(G, ym), row_in_band(G, yy), row_in_band(G, yp)};
-    const bool fluid = act && !(tc[1] && !rb[1]);
-    // walls can touch this warp's nodes only if it has tube columns and one of the
-    // three rows leaves the band (warp-uniform)
-    const bool walls = warp_tube && !(rb[0] && rb[1] && rb[2]);
-    if (fluid) {
-      bool sol[3][3];
-      bool bnd = false;
-      if (walls) {
+    const int rowb[3] = {ym * nx, yy * nx, yp * nx};
+    A fs[9], ge[9];
+    if constexpr (CW) {
+      const bool rb[3] = {row_in_band(G, ym), row_in_band(G, yy), row_in_band(G, yp)};
+      const bool fluid = act && !(tc[1] && !rb[1]);
+      // walls can touch this warp's nodes only if it has tube columns and one of
+      // the three rows leaves the band (warp-uniform)
+      const bool walls = warp_tube && !(rb[0] && rb[1] && rb[2]);
+      if (fluid) {
+        bool sol[3][3];
+        bool bnd = false;
+        if (walls) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+          for (int j = 0; j < 3; ++j)
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            sol[j][i] = tc[i] && !rb[j];
-            bnd = bnd || sol[j][i];
-          }
-      } else {
+            for (int i = 0; i < 3; ++i) {
+              sol[j][i] = tc[i] && !rb[j];
+              bnd = bnd || sol[j][i];
+            }
+        } else {
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
+          for (int j = 0; j < 3; ++j)
 #pragma unroll
-          for (int i = 0; i < 3; ++i) sol[j][i] = false;
+            for (int i = 0; i < 3; ++i) sol[j][i] = false;
+        }
+        collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
+        push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, bnd, fs, ge);
       }
-      A fs[9], ge[9];
-      collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
-      const int rowb[3] = {ym * nx, yy * nx, yp * nx};
-      push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, bnd, fs, ge);
+    } else {
+      const bool sol[3][3] = {{false, false, false}, {false, false, false}, {false, false, false}};
+      if (act) {
+        collide_node<MODEL, A>(P, vr, vp, sol, false, fa, fs, ge);
+        push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, false, fs, ge);
+      }
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       fa[i] = fn[i];
       if (BIN) ga[i] = gn[i];
     }
+    return true;
+  };
+  // walls can touch the tile under this warp only if the warp has tube columns and
+  // one of the rows y0 - 1 .. y1 leaves the band (warp-uniform)
+  const int nrw = y1 - y0 + 2;
+  const int d0 = ((y0 - 1 - G.tube_y0) % ny + ny) % ny;
+  const bool tile_walls = warp_tube && !(d0 + nrw <= G.tube_h);
+  if (tile_walls) {
+    for (int y = y0; y < y1; ++y)
+      if (!row_step(y, std::true_type{})) return false;
+  } else {
+    for (int y = y0; y < y1; ++y)
+      if (!row_step(y, std::false_type{})) return false;
   }
   return true;
 }
