@@ -91,14 +91,26 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
  * g populations, which all relax fully to g^eq (App. A, Eq. (latbolt2)):
  * 80 bytes per node update.  lb_get_populations returns f and, for g, the
  * populations (phi, 0, ..., 0), whose phi is the only moment of g a step uses.
- * At most 429496729 nodes (10 nx ny < 2^32). */
+ * At most 429496729 nodes (10 nx ny < 2^32).
+ *
+ * LB_STORAGE_F32_BLOCKED (binary model only) keeps the eighteen FP32
+ * populations, with the values and arithmetic of LB_STORAGE_F32 (the two give
+ * identical results), in blocks of 32 consecutive nodes n = y nx + x: block
+ * b = n / 32 holds f_0..f_8 and then g_0..g_8 of its nodes, 32 consecutive
+ * values per population, so f_i of node n is float element
+ * 576 b + 32 i + n % 32 of the state and g_i is 288 elements further
+ * (lb_save_state writes this layout).  A row of a tile with its halo is then
+ * one contiguous range, which the staged step kernel fetches with one bulk copy
+ * per row instead of one per population plane.  Needs nx % 32 == 0; at most
+ * 238609294 nodes (18 nx ny < 2^32). */
 typedef enum {
   LB_STORAGE_F64 = 0,
   LB_STORAGE_F32 = 1,
   LB_STORAGE_F16DEV = 2,
   LB_STORAGE_MOMENTS = 3,
   LB_STORAGE_MOMENTS_F16 = 4,
-  LB_STORAGE_F32_GELIM = 5
+  LB_STORAGE_F32_GELIM = 5,
+  LB_STORAGE_F32_BLOCKED = 6
 } lb_storage;
 
 typedef struct {

@@ -47,7 +47,7 @@ __global__ void init_kernel(Geom G, Phys<typename S::A> P, Buf<S> B, const doubl
         // zero bits in every plane (with the FP16 offsets a stored 0 would not be),
         // the same as a fresh buffer: no step reads or writes a solid node
         for (int i = 0; i < 9; ++i) {
-          B.f[i * N + n] = typename S::T(0.0f);
+          S::zf(B.f, N, n, i);
           if (BIN) S::sg(B.g, B.g0, N, n, i, A(0));
         }
       }
@@ -234,7 +234,7 @@ __global__ void pops_in_kernel(Geom G, Buf<S> B, const double* __restrict__ fi, 
     } else {
       for (int i = 0; i < 9; ++i) {
         if (sol)
-          B.f[i * N + n] = typename S::T(0.0f);  // zero bits, as in init_kernel
+          S::zf(B.f, N, n, i);  // zero bits, as in init_kernel
         else
           S::sf(B.f, N, n, i, A(fi[i * N + n]), B.r);
         if (MODEL == MODEL_BINARY) S::sg(B.g, B.g0, N, n, i, sol ? A(0) : A(gi[i * N + n]));

@@ -107,6 +107,7 @@ static OpsFn pick_ops(int model, int storage) {
     if (storage == LB_STORAGE_MOMENTS) return ops_bin_m32;
     if (storage == LB_STORAGE_MOMENTS_F16) return ops_bin_m16;
     if (storage == LB_STORAGE_F32_GELIM) return ops_bin_g32;
+    if (storage == LB_STORAGE_F32_BLOCKED) return ops_bin_f32b;
   }
   return NULL;
 }
@@ -198,6 +199,12 @@ static size_t state_bytes(int model, int storage, size_t N, size_t* fb, size_t* 
     *g0b = 0;
     return *fb;
   }
+  if (storage == LB_STORAGE_F32_BLOCKED) {  // f and g of every 32-node block together, in the f buffer
+    *fb = 18 * N * sizeof(float);
+    *gb = 0;
+    *g0b = 0;
+    return *fb;
+  }
   size_t el = storage == LB_STORAGE_F64 ? 8 : (storage == LB_STORAGE_F32 ? 4 : 2);
   *fb = 9 * N * el;
   *gb = model == LB_MODEL_BINARY ? (storage == LB_STORAGE_F16DEV ? 8 : 9) * N * el : 0;
@@ -214,6 +221,10 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
     return set_err(c, "the moment storage holds at most 715827882 nodes"), LB_ERR_ARG;
   if (p->storage == LB_STORAGE_F32_GELIM && 10ull * g->nx * g->ny >= (1ull << 32))
     return set_err(c, "the g-eliminated storage holds at most 429496729 nodes"), LB_ERR_ARG;
+  if (p->storage == LB_STORAGE_F32_BLOCKED && g->nx % 32 != 0)
+    return set_err(c, "the block storage needs nx %% 32 == 0"), LB_ERR_ARG;
+  if (p->storage == LB_STORAGE_F32_BLOCKED && 18ull * g->nx * g->ny >= (1ull << 32))
+    return set_err(c, "the block storage holds at most 238609294 nodes"), LB_ERR_ARG;
   if (w->tube_len < 0 || w->tube_len > g->nx) return set_err(c, "tube_len outside [0, nx]"), LB_ERR_ARG;
   if (w->tube_len > 0) {
     if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny)
@@ -334,6 +345,8 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
     c->buf[k].f = dev_alloc_owned(c, fb);
     c->buf[k].g = gb ? dev_alloc_owned(c, gb) : NULL;
     c->buf[k].g0 = g0b ? (float*)dev_alloc_owned(c, g0b) : NULL;
+    // the block storage keeps g beside f in every block
+    if (params->storage == LB_STORAGE_F32_BLOCKED && c->buf[k].f) c->buf[k].g = (float*)c->buf[k].f + 288;
     if (!c->buf[k].f || (gb && !c->buf[k].g) || (g0b && !c->buf[k].g0)) {
       set_err(NULL, "device allocation of the state (%zu bytes) failed", 2 * (fb + gb + g0b));
       lb_destroy(c);

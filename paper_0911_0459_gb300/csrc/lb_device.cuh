@@ -145,6 +145,11 @@ struct SF64 {
     LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     g[i * N + n] = v;
   }
+  // zero bits at f_i of node n (a solid node, as in a fresh buffer)
+  __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, );
+    f[i * N + n] = T(0);
+  }
 };
 
 struct SF32 {
@@ -183,6 +188,11 @@ struct SF32 {
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
     LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
     g[i * N + n] = v;
+  }
+  // zero bits at f_i of node n (a solid node, as in a fresh buffer)
+  __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, );
+    f[i * N + n] = T(0);
   }
 };
 
@@ -234,6 +244,65 @@ struct SF16 {
       g0[n] = v;
     else
       g[(i - 1) * N + n] = __float2half_rn(v);
+  }
+  __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, );
+    f[i * N + n] = __float2half_rn(0.0f);
+  }
+};
+
+// FP32 populations of the binary model in blocks of 32 consecutive nodes: block
+// b = n / 32 holds f_0..f_8 and then g_0..g_8 of its nodes, each population as 32
+// consecutive values, so f_i of node n is element 576 b + 32 i + n % 32 of the
+// buffer and g_i lies 288 elements further (Buf::g = Buf::f + 288).  With
+// nx % 32 == 0 the nodes of a row segment of whole blocks, all eighteen
+// populations, are one contiguous range, which the staged step kernel copies
+// with a single bulk copy per row.  Same values and arithmetic as SF32.
+struct SF32B {
+  using T = float;
+  using A = float;
+  static constexpr int kBlock = 576;  // elements per block of 32 nodes
+  __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  // shared-memory stage of whole blocks: stage column c lies in block c / 32
+  __device__ static A pf(const T* f, int, int c, int i, const Rest&) { return f[(c >> 5) * kBlock + 32 * i + (c & 31)]; }
+  __device__ static A pg(const T* g, const float*, int, int c, int i) { return g[(c >> 5) * kBlock + 32 * i + (c & 31)]; }
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
+    LB_GUARD(at(n, i), 18 * N, A(0));
+    return __ldg(f + at(n, i));
+  }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) {
+    LB_GUARD(at(n, i), 18 * N, );
+    f[at(n, i)] = v;
+  }
+  __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
+    LB_GUARD(at(n, i), 18 * N - 288, A(0));
+    return __ldg(g + at(n, i));
+  }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) {
+    LB_GUARD(at(n, i), 18 * N - 288, );
+    g[at(n, i)] = v;
+  }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) {
+    LB_GUARD(at(n, i), 18 * N, A(0));
+    return __ldcg(f + at(n, i));
+  }
+  __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) {
+    LB_GUARD(at(n, i), 18 * N - 288, A(0));
+    return __ldcg(g + at(n, i));
+  }
+  // 32-bit element offsets (needs 18 N < 2^32)
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
+    LB_GUARD(at32(n, i), 18ull * N, );
+    f[at32(n, i)] = v;
+  }
+  __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
+    LB_GUARD(at32(n, i), 18ull * N - 288, );
+    g[at32(n, i)] = v;
+  }
+  __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(at(n, i), 18 * N, );
+    f[at(n, i)] = 0.0f;
   }
 };
 

@@ -121,14 +121,19 @@ struct TmaLayout {
   using A = typename S::A;
   static constexpr bool BIN = MODEL == MODEL_BINARY;
   static constexpr bool F16 = sizeof(T) == 2;
-  static constexpr int W = BX + 16;                  // staged columns: xb-8 .. xb+BX+7
+  // 32-node blocks (SF32B): a stage row is whole blocks, one bulk copy
+  static constexpr bool BLK = std::is_same<S, SF32B>::value;
+  static constexpr int HALO = BLK ? 32 : 8;          // staged columns either side of the tile
+  static constexpr int W = BX + 2 * HALO;            // staged columns: xb-HALO .. xb+BX+HALO-1
   static constexpr int NF = 9;
   static constexpr int NG = BIN ? NGPlanes<S>::value : 0;
   static constexpr int NG0 = (BIN && F16) ? 1 : 0;   // FP32 g_0 plane of the FP16 storage
-  static constexpr size_t STAGE_T = (size_t)(NF + NG) * W * sizeof(T);
+  static constexpr size_t STAGE_T = BLK ? (size_t)(W / 32) * SF32B::kBlock * sizeof(float)
+                                        : (size_t)(NF + NG) * W * sizeof(T);
   static constexpr size_t STAGE_G0 = (size_t)NG0 * W * sizeof(float);
   static constexpr size_t STAGE = ((STAGE_T + STAGE_G0) + 127) / 128 * 128;
   static constexpr size_t BYTES = NS * STAGE + 2 * NS * 8;
+  static_assert(!BLK || BIN, "the block storage holds the binary model");
 };
 
 template <int MODEL, class S>
@@ -155,7 +160,9 @@ struct Ring {
   uint64_t* full;
   uint64_t* empty;
   __device__ T* f(int s) const { return reinterpret_cast<T*>(smem + s * L::STAGE); }
-  __device__ T* g(int s) const { return reinterpret_cast<T*>(smem + s * L::STAGE) + 9 * L::W; }
+  __device__ T* g(int s) const {
+    return reinterpret_cast<T*>(smem + s * L::STAGE) + (L::BLK ? SF32B::kBlock / 2 : 9 * L::W);
+  }
   __device__ float* g0(int s) const { return reinterpret_cast<float*>(smem + s * L::STAGE + L::STAGE_T); }
 };
 
@@ -191,30 +198,39 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const size_t N = (size_t)nx * ny;
   const int w = min(BX, nx - xb);
   const int nrows = y1 - y0 + 2;
-  const int lo = xb >= 8 ? xb - 8 : 0;
-  const int hi = min(xb + BX + 8, nx);
+  constexpr int H = L::HALO;
+  const int lo = xb >= H ? xb - H : 0;
+  const int hi = min(xb + BX + H, nx);
   const int ncols = hi - lo;
   const bool wl = xb == 0;           // left halo wraps to the row end
-  const bool wr = xb + BX + 8 > nx;  // right halo wraps to the row start
-  const int so = lo - (xb - 8);      // stage column of global column lo
-  const int sr = nx - (xb - 8);      // stage column of the right wrap chunk
-  const uint32_t ecols = (uint32_t)(ncols + (wl ? 8 : 0) + (wr ? 8 : 0));
-  const uint32_t total = ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
+  const bool wr = xb + BX + H > nx;  // right halo wraps to the row start
+  const int so = lo - (xb - H);      // stage column of global column lo
+  const int sr = nx - (xb - H);      // stage column of the right wrap chunk
+  const uint32_t ecols = (uint32_t)(ncols + (wl ? H : 0) + (wr ? H : 0));
+  const uint32_t total = L::BLK ? ecols * (uint32_t)(SF32B::kBlock / 32 * sizeof(float))
+                                : ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
   auto planes = [&](const T* base, int nplanes, T* dst0, size_t rowoff, uint64_t* bar) {
     const size_t lim = (size_t)nplanes * N;
     for (int i = 0; i < nplanes; ++i) {
       const size_t po = (size_t)i * N + rowoff;
       T* d = dst0 + i * W;
       bulk_g2s(d + so, copy_src(base, po + lo, (size_t)ncols, lim), (uint32_t)ncols * sizeof(T), bar);
-      if (wl) bulk_g2s(d, copy_src(base, po + (nx - 8), 8, lim), 8 * sizeof(T), bar);
-      if (wr) bulk_g2s(d + sr, copy_src(base, po, 8, lim), 8 * sizeof(T), bar);
+      if (wl) bulk_g2s(d, copy_src(base, po + (nx - H), H, lim), H * sizeof(T), bar);
+      if (wr) bulk_g2s(d + sr, copy_src(base, po, H, lim), H * sizeof(T), bar);
     }
+  };
+  // whole 32-node blocks: nodes [n0, n0 + cnt) of the row to stage column c
+  auto blocks = [&](T* dst0, size_t n0, int cnt, int c, uint64_t* bar) {
+    constexpr int B = SF32B::kBlock;
+    const size_t lim = 18 * N;
+    bulk_g2s(dst0 + (c / 32) * B, copy_src(src.f, (n0 / 32) * B, (size_t)(cnt / 32) * B, lim),
+             (uint32_t)(cnt / 32) * B * sizeof(float), bar);
   };
   // every staged column inside the tube: rows outside the band are all solid and
   // their populations are never read (ghosts replace them), so they are not copied
-  int d0 = xb - 8 - G.tube_x0;
+  int d0 = xb - H - G.tube_x0;
   d0 = ((d0 % nx) + nx) % nx;
-  const bool all_tube = G.tube_len > 0 && d0 + w + 16 <= G.tube_len;
+  const bool all_tube = G.tube_len > 0 && d0 + w + 2 * H <= G.tube_len;
   for (int j = 0; j < nrows; ++j) {
     const unsigned k = kbase + j;
     const int s = k % NS;
@@ -227,6 +243,13 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     }
     const size_t rowoff = (size_t)yy * nx;
     mbar_arrive_expect_tx(&R.full[s], total);
+    if constexpr (L::BLK) {
+      blocks(R.f(s), rowoff + lo, ncols, so, &R.full[s]);
+      if (wl) blocks(R.f(s), rowoff + (nx - H), H, 0, &R.full[s]);
+      if (wr) blocks(R.f(s), rowoff, H, sr, &R.full[s]);
+      issued = k + 1;
+      continue;
+    }
     planes(src.f, L::NF, R.f(s), rowoff, &R.full[s]);
     if (BIN) planes(src.g, L::NG, R.g(s), rowoff, &R.full[s]);
     if (L::NG0) {
@@ -266,7 +289,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const int c0 = xb + warp * 32;      // first column of this warp
   const int x = c0 + lane;
   const bool act = x < xb + w;
-  const int sc = x - xb + 8;          // stage column of this lane's node
+  const int sc = x - xb + L::HALO;    // stage column of this lane's node
 
   auto load_pop = [&](int s, int c, A f[9], A g[9]) {
 #pragma unroll

@@ -114,6 +114,12 @@ def test_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
                                                                setattr(p, "storage", lb.STORAGE_F32_GELIM))
         yield "g eliminated above 429496729 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 6554),
                                                                      setattr(p, "storage", lb.STORAGE_F32_GELIM))
+        yield "block storage with nx % 32 != 0", lambda g, w, p: (setattr(g, "nx", 100),
+                                                                  setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
+        yield "liquid-gas in blocks", lambda g, w, p: (setattr(p, "model", 0),
+                                                       setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
+        yield "block storage above 238609294 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 3641),
+                                                                      setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
         yield "unknown storage", lambda g, w, p: setattr(p, "storage", 9)
         yield "tube longer than the grid", lambda g, w, p: setattr(w, "tube_len", 97)
         yield "band as tall as the grid", lambda g, w, p: setattr(w, "tube_h", 24)
@@ -169,6 +175,7 @@ def test_batch_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "wall gradient NaN": (lambda s: setattr(s[0][1], "wall_grad", float("nan")), None),
         "FP16 moments in a batch": (lambda s: [setattr(x[2], "storage", lb.STORAGE_MOMENTS_F16) for x in s], None),
         "g eliminated in a batch": (lambda s: [setattr(x[2], "storage", lb.STORAGE_F32_GELIM) for x in s], None),
+        "block storage in a batch": (lambda s: [setattr(x[2], "storage", lb.STORAGE_F32_BLOCKED) for x in s], None),
         "negative mobility": (setp(0, "M", -1.0), None),
         "viscosity table of one entry": (setp(1, "nu_table", 1), None),
         "tube longer than the grid": (lambda s: setattr(s[1][1], "tube_len", 200), None),
@@ -197,7 +204,7 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
     """lb_filled_length_noalloc checks its arguments on the host and returns LB_ERR_ARG
     before its first CUDA call (so this runs without a GPU; the device pointers below are
     never dereferenced): NULL pointers, block counts outside [1, LB_NOALLOC_MAX_BLOCKS],
-    the moment storage (it keeps no populations), a liquid-gas lattice in FP16, a binary
+    the moment storage (it keeps no populations), the 32-node block storage (another layout), a liquid-gas lattice in FP16, a binary
     call without g, an FP16 call without g0, and liquid-gas densities that are not finite
     with rho_l > rho_g (its liquid fraction divides by rho_l - rho_g)."""
     import workloads as W
@@ -224,6 +231,7 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "no blocks": call(binary, nblocks=0),
         "too many blocks": call(binary, nblocks=2049),
         "moment storage": call(binary, storage=lb.STORAGE_MOMENTS),
+        "block storage": call(binary, storage=lb.STORAGE_F32_BLOCKED),
         "unknown storage": call(binary, storage=7),
         "liquid-gas in FP16": call(lg, storage=lb.STORAGE_F16DEV),
         "binary without g": call(binary, g=None),
