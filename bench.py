@@ -117,7 +117,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("lb_device.cuh", "lb_step_tma.cuh"):
+    for f in ("lb_device.cuh", "lb_step_tma.cuh", "lb_ops_impl.cuh"):
         h.update(open(os.path.join(ROOT, "paper_0911_0459_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -160,12 +160,13 @@ def fluid_nodes_of(cap):
 
 
 # algorithmic bytes per fluid-node update and the name of each storage
-STORAGES = {"f32": (144.0, "FP32 storage", "FP32"), "f16dev": (76.0, "FP16-deviation storage", "FP16dev"),
+STORAGES = {"f32b": (144.0, "FP32 populations in 32-node blocks", "SF32B"),
+            "f32": (144.0, "FP32 populations in planes", "FP32"), "f16dev": (76.0, "FP16-deviation storage", "FP16dev"),
             "moments": (48.0, "FP32 moment storage", "SM32"), "moments_f16": (28.0, "FP16 moment storage", "SM16"),
             "gelim": (80.0, "FP32 f + phi storage (g eliminated)", "SG32")}
 
 
-def bench_config(cap, world, storage="f32"):
+def bench_config(cap, world, storage="f32b"):
     """The `config` object of both arms' JSON lines (the same workload)."""
     return {"workload": "binary_16384x256: H=200 tube over x in [512, 16384), gas 128 cols, "
                         f"viscosity ratio 50 (0.83/0.0166), theta 45 deg, {STORAGES[storage][1]}",
@@ -229,13 +230,14 @@ def cpu_baseline(sample_steps=2000, copy_steps=500):
 
 def precision_report(Lattice, orc, steps):
     """Error of each storage against the FP64 oracle on the crop after `steps` steps."""
-    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_GELIM, STORAGE_F64, STORAGE_MOMENTS,
-                                       STORAGE_MOMENTS_F16)
+    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F32_GELIM,
+                                       STORAGE_F64, STORAGE_MOMENTS, STORAGE_MOMENTS_F16)
     rho_o, _, _, phi_o = orc.fields()
     l_o = orc.filled_length()["l"]
     out = {"workload": "1024x64 crop of the large capillary, default initial state", "steps": steps}
     import dataclasses
-    for name, st, table in (("f64", STORAGE_F64, 0), ("f32", STORAGE_F32, 0), ("f16dev", STORAGE_F16DEV, 0),
+    for name, st, table in (("f64", STORAGE_F64, 0), ("f32", STORAGE_F32, 0), ("f32_blocks", STORAGE_F32_BLOCKED, 0),
+                            ("f16dev", STORAGE_F16DEV, 0),
                             ("moments_f32", STORAGE_MOMENTS, 0), ("moments_f16", STORAGE_MOMENTS_F16, 0),
                             ("f32_g_eliminated", STORAGE_F32_GELIM, 0), ("f32_nu_table_1e4", STORAGE_F32, 10000)):
         cap = W.config_binary_crop_1024x64(st)
@@ -461,7 +463,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", default=None, help="BX,YC: fixed step-kernel tile instead of autotuning")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16dev", "moments", "moments_f16", "gelim"])
+    ap.add_argument("--storage", default="f32b", choices=sorted(STORAGES))
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sweep secondary metric")
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate secondary metric")
@@ -476,8 +478,8 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_GELIM, STORAGE_MOMENTS,
-                                       STORAGE_MOMENTS_F16, Lattice)
+    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F32_GELIM,
+                                       STORAGE_MOMENTS, STORAGE_MOMENTS_F16, Lattice)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -487,8 +489,9 @@ def main():
         if world > 1:
             dist.barrier()
 
-    cap = W.config_binary_16384x256({"f32": STORAGE_F32, "f16dev": STORAGE_F16DEV, "moments": STORAGE_MOMENTS,
-                                     "moments_f16": STORAGE_MOMENTS_F16, "gelim": STORAGE_F32_GELIM}[args.storage])
+    cap = W.config_binary_16384x256({"f32b": STORAGE_F32_BLOCKED, "f32": STORAGE_F32, "f16dev": STORAGE_F16DEV,
+                                     "moments": STORAGE_MOMENTS, "moments_f16": STORAGE_MOMENTS_F16,
+                                     "gelim": STORAGE_F32_GELIM}[args.storage])
     lat = Lattice.from_workload(cap)
     if args.tile:
         tx, ty = (int(v) for v in args.tile.split(","))
@@ -527,7 +530,8 @@ def main():
     per_launch_ms = step_ms / args.steps
     achieved = fluid * bytes_per_lu / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = ncu_traffic("binary_f32", kernel_variant, [tx, ty]) if args.storage == "f32" else None
+    traffic = ncu_traffic("binary_" + args.storage, kernel_variant, [tx, ty]) if args.storage in ("f32", "f32b") \
+        else None
     kernel_mlups = fluid / (per_launch_ms * 1e-3) / 1e6
     ceilings = {"144B": peak * 1e3 / 144.0, "48B": peak * 1e3 / 48.0}   # MLUPS at the measured peak
 
@@ -568,6 +572,27 @@ def main():
     # secondary numbers on the same GPU (not the headline)
     secondary = {}
     try:
+        for key, st, bpl in (("fp32_planes_16384x256", STORAGE_F32, 144), ("fp32_blocks_16384x256", STORAGE_F32_BLOCKED, 144)):
+            if st == cap.params.storage:
+                continue
+            lp = Lattice.from_workload(W.config_binary_16384x256(st))
+            ptx, pty, _ = lp.autotune()
+            lp.step(8)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(lp.stream)
+            lp.step(512)
+            b.record(lp.stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 512
+            gbs = lp.fluid_nodes * bpl / (ms * 1e-3) / 1e9
+            secondary[key] = {"MLUPS": lp.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "tile": [ptx, pty],
+                              "kernel": step_kernel_label(lp.kernel(), ptx, pty, "FP32" if st == STORAGE_F32 else "SF32B"),
+                              "bytes_per_lu": bpl, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
+                              "what": "the same FP32 populations and arithmetic (bit-identical states), the other "
+                                      "layout; autotuned, 512 steps, CUDA events"}
+            lp.close()
         c16 = W.config_binary_16384x256(STORAGE_F16DEV)
         l16 = Lattice.from_workload(c16)
         l16.autotune()
