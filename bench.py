@@ -153,6 +153,43 @@ def ncu_traffic(kind, variant, tile):
         return None
 
 
+# FP64 work per fluid-node update of the liquid-gas step kernel (ncu instruction counts of
+# one launch on 16384 x 256: 197.9 M DFMA, 86.5 M DMUL, 228.2 M DADD over 3 305 472 fluid
+# nodes): 155 FP64 instructions, 215 flops (an FMA counts two)
+LG_FP64_INST_PER_LU = 155.0
+LG_FP64_FLOPS_PER_LU = 215.0
+
+
+def lg_fp64_roofline(torch, Lattice):
+    """The liquid-gas FP64 capillary at 16384 x 256 against the measured FP64 FMA rate
+    (lb_fp64_fma_rate): GB300's FP64 pipe, not HBM, bounds this path."""
+    from paper_0911_0459_gb300 import lb as lbmod
+    lat = Lattice.from_workload(W.config_lg_16384x256())
+    tx, ty, _ = lat.autotune()
+    lat.step(4)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(lat.stream)
+    lat.step(64)
+    b.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 64
+    fluid = lat.fluid_nodes
+    rate = max(lbmod.fp64_fma_rate() for _ in range(2))
+    achieved = fluid * LG_FP64_FLOPS_PER_LU / (ms * 1e-3) / 1e12
+    pipe = fluid * LG_FP64_INST_PER_LU / (ms * 1e-3) / 1e12           # FP64 instructions per ns
+    out = {"MLUPS": fluid / (ms * 1e-3) / 1e6, "ms_per_step": ms, "tile": [tx, ty], "kernel_variant": lat.kernel(),
+           "fp64_peak_tflops_measured": rate, "fp64_tflops_achieved": achieved,
+           "frac_of_fp64_peak": achieved / rate,
+           "frac_of_fp64_pipe": pipe / (rate / 2.0),
+           "GBps": fluid * 144 / (ms * 1e-3) / 1e9,
+           "what": "liquid-gas FP64, 144 B/LU; FP64 flops per LU from ncu instruction counts (215: 60 DFMA, "
+                   "26 DMUL, 69 DADD); frac_of_fp64_pipe counts every FP64 instruction as one FMA slot"}
+    lat.close()
+    return out
+
+
 def fluid_nodes_of(cap):
     """Fluid nodes of a workload: every node but the tube's solid rows."""
     solid = cap.tube_len * (cap.ny - cap.tube_h) if cap.tube_len > 0 else 0
@@ -469,6 +506,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate secondary metric")
     ap.add_argument("--profile", action="store_true",
                     help="only the large capillary: warm-up then --steps steps (for ncu captures)")
+    ap.add_argument("--workload", default="binary_16384x256", choices=["binary_16384x256", "lg_16384x256"],
+                    help="with --profile: the lattice to run (lg_16384x256: the liquid-gas FP64 capillary)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -492,6 +531,8 @@ def main():
     cap = W.config_binary_16384x256({"f32b": STORAGE_F32_BLOCKED, "f32": STORAGE_F32, "f16dev": STORAGE_F16DEV,
                                      "moments": STORAGE_MOMENTS, "moments_f16": STORAGE_MOMENTS_F16,
                                      "gelim": STORAGE_F32_GELIM}[args.storage])
+    if args.profile and args.workload == "lg_16384x256":
+        cap = W.config_lg_16384x256()
     lat = Lattice.from_workload(cap)
     if args.tile:
         tx, ty = (int(v) for v in args.tile.split(","))
@@ -619,6 +660,7 @@ def main():
         torch.cuda.synchronize()
         secondary["lg_256x32_fp64_us_per_step"] = 1e3 * a.elapsed_time(b) / 1984
         l1.close()
+        secondary["lg_16384x256_fp64"] = lg_fp64_roofline(torch, Lattice)
         secondary["binary_2048x64"] = small_capillary_rates(torch, Lattice)
         # the same large capillary with the reduced states of the pull kernel
         from paper_0911_0459_gb300 import STORAGE_F32_GELIM, STORAGE_MOMENTS_F16

@@ -277,6 +277,17 @@ lb_status lb_autotune(lb_ctx *ctx, int *tile_x, int *tile_y, double *us_per_step
  * ctx is NULL).  Never NULL. */
 const char *lb_last_error(const lb_ctx *ctx);
 
+/* Diagnostic: the FP64 fused multiply-add rate of the current device in
+ * TFLOP/s (2 flops per FMA), measured on `stream` (a cudaStream_t; NULL for the
+ * legacy default stream) by a kernel of independent FMA chains, 8 CTAs of 256
+ * threads per SM, best of three launches after one warm-up (tens of
+ * milliseconds; waits for the stream).  The liquid-gas model computes in FP64
+ * (the van der Waals pins of Sec. 2 and the densities near 4 want its
+ * precision), and on this GPU FP64 arithmetic, not HBM, bounds that path; this
+ * is the ceiling its roofline is quoted against.  LB_ERR_ARG if tflops is
+ * NULL, LB_ERR_CUDA if a CUDA call fails (*tflops is then 0). */
+lb_status lb_fp64_fma_rate(void *stream, double *tflops);
+
 /* ------------------------------------------------------------------------
  * Batched sweeps: many binary capillaries of different sizes and parameters
  * advanced together by one persistent kernel (every lattice of a batch takes

@@ -117,6 +117,7 @@ def library():
         "lb_batch_state_bytes": (C.c_size_t, [vp]),
         "lb_batch_save_state": (C.c_int, [vp, vp, C.c_size_t]),
         "lb_batch_load_state": (C.c_int, [vp, vp, C.c_size_t, C.c_long]),
+        "lb_fp64_fma_rate": (C.c_int, [vp, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -135,7 +136,19 @@ def exported_symbols():
             "lb_batch_populations", "lb_batch_moments", "lb_batch_set_tile", "lb_batch_autotune", "lb_batch_set_barrier",
             "lb_batch_set_kernel", "lb_batch_get_kernel", "lb_batch_time", "lb_batch_fluid_nodes", "lb_batch_last_error",
             "lb_state_bytes", "lb_save_state", "lb_load_state", "lb_batch_state_bytes", "lb_batch_save_state",
-            "lb_batch_load_state"]
+            "lb_batch_load_state", "lb_fp64_fma_rate"]
+
+
+def fp64_fma_rate(stream=None):
+    """The device's measured FP64 fused multiply-add rate in TFLOP/s (lb_fp64_fma_rate),
+    on a torch stream (default: the current one)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = C.c_double()
+    status = library().lb_fp64_fma_rate(C.c_void_p(st.cuda_stream), C.byref(v))
+    if status != LB_OK:
+        raise LbError(status, "lb_fp64_fma_rate failed")
+    return v.value
 
 
 class _TorchAllocator:

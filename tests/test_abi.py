@@ -185,6 +185,11 @@ def test_batch_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
         assert st == lb.LB_ERR_ARG and h is None and msg, what
 
 
+def test_fp64_rate_rejects_a_null_output_before_any_cuda_call(libpath):
+    from paper_0911_0459_gb300 import lb
+    assert lb.library().lb_fp64_fma_rate(None, None) == lb.LB_ERR_ARG
+
+
 def test_mlp_create_rejects_invalid_shapes_before_any_cuda_call(libpath):
     """lb_mlp_create checks the network shape on the host: the largest batch is 65535 row
     tiles of 64 (the GEMMs put row tiles on the grid's y dimension)."""

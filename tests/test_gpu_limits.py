@@ -78,3 +78,14 @@ def test_largest_lattices_of_the_staged_kernel(ny, staged):
     assert abs(m0 / (nx * ny) - cap.params.rho_g) < 1e-6 * cap.params.rho_g
     lat.close()
     torch.cuda.empty_cache()
+
+
+def test_fp64_fma_rate_is_measured():
+    """lb_fp64_fma_rate times a kernel of independent FP64 FMA chains: a positive rate,
+    below the FP32 rate this GPU's SMs could reach (152 SMs x 128 lanes x 2 flops x
+    2.1 GHz = 82 TFLOP/s), and the same on a second call within timing noise."""
+    from paper_0911_0459_gb300 import lb as lbmod
+    a = lbmod.fp64_fma_rate()
+    b = lbmod.fp64_fma_rate()
+    assert 0.05 < a < 82.0 and 0.05 < b < 82.0, (a, b)
+    assert abs(a - b) < 0.2 * max(a, b), (a, b)

@@ -139,6 +139,14 @@ def config_lg_256x32() -> Capillary:
                      lg_params(), theta_deg=60.0, wall_grad=-0.144, steps=2000)
 
 
+def config_lg_16384x256() -> Capillary:
+    """Liquid-gas FP64 capillary at the large capillary's size, 16384 x 256 (H = 200,
+    tube over x in [512, 16384), gas 128 columns), with the 256 x 32 capillary's
+    parameters: a lattice larger than L2 for the FP64 path's roofline."""
+    return Capillary("lg_16384x256", 16384, 256, 512, 16384 - 512, 28, 200, 128, 10,
+                     lg_params(), theta_deg=60.0, wall_grad=-0.144, steps=2000)
+
+
 def config_binary_2048x64() -> Capillary:
     """Binary FP32 capillary, 2048 x 64, H = 50, viscosity ratio 10, 60 degrees."""
     return Capillary("binary_2048x64", 2048, 64, 256, 1792, 7, 50, 64, 10,
