@@ -154,10 +154,10 @@ def ncu_traffic(kind, variant, tile):
 
 
 # FP64 work per fluid-node update of the liquid-gas step kernel (ncu instruction counts of
-# one launch on 16384 x 256: 197.9 M DFMA, 86.5 M DMUL, 228.2 M DADD over 3 305 472 fluid
-# nodes): 155 FP64 instructions, 215 flops (an FMA counts two)
-LG_FP64_INST_PER_LU = 155.0
-LG_FP64_FLOPS_PER_LU = 215.0
+# one launch on 16384 x 256: 129.2 M DFMA, 82.6 M DMUL, 184.4 M DADD over 3 305 472 fluid
+# nodes): 120 FP64 instructions, 159 flops (an FMA counts two)
+LG_FP64_INST_PER_LU = 120.0
+LG_FP64_FLOPS_PER_LU = 159.0
 
 
 def lg_fp64_roofline(torch, Lattice):
@@ -184,8 +184,8 @@ def lg_fp64_roofline(torch, Lattice):
            "frac_of_fp64_peak": achieved / rate,
            "frac_of_fp64_pipe": pipe / (rate / 2.0),
            "GBps": fluid * 144 / (ms * 1e-3) / 1e9,
-           "what": "liquid-gas FP64, 144 B/LU; FP64 flops per LU from ncu instruction counts (215: 60 DFMA, "
-                   "26 DMUL, 69 DADD); frac_of_fp64_pipe counts every FP64 instruction as one FMA slot"}
+           "what": "liquid-gas FP64, 144 B/LU; FP64 flops per LU from ncu instruction counts (159: 39 DFMA, "
+                   "25 DMUL, 56 DADD); frac_of_fp64_pipe counts every FP64 instruction as one FMA slot"}
     lat.close()
     return out
 

@@ -448,6 +448,7 @@ static void fill_caps(lb_batch* b, std::vector<CapDesc<A>>& caps) {
     c.P.nu = A(p.nu); c.P.lambda_scale = A(p.lambda_scale); c.P.h = A(w.wall_grad);
     c.P.lut = A(p.nu_table >= 2 ? p.nu_table - 1 : 0);
     c.P.lut_inv = p.nu_table >= 2 ? A(1.0 / (p.nu_table - 1)) : A(0);
+    c.P.omega = A(2.0 / (6.0 * p.nu + 1.0));  // liquid-gas only; a batch holds the binary model
     c.off_f = b->off_f[i];
     c.off_g = b->off_g[i];
     c.off_g0 = b->off_g0[i];

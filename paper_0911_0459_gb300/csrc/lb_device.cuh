@@ -18,6 +18,8 @@
 // non-equilibrium; the columns of M^-1 for those modes are (row of M)/4.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -41,6 +43,7 @@ struct Phys {
   A lambda_scale;      // lambda = lambda_scale * nu_local
   A h;                 // wall gradient of the wetted field
   A lut, lut_inv;      // viscosity table of App. A: K - 1 steps (0: exact nu) and 1 / (K - 1)
+  A omega;             // liquid-gas: 2 / (6 nu + 1) (Eq. (omega)), for the FP64 pair-form collision
 };
 
 // ---------------------------------------------------------- bounds checks
@@ -486,6 +489,88 @@ __host__ __device__ constexpr int OPPd(int i) { return i == 0 ? 0 : ((i & 1) ? i
 __device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double rcp_rn(double v) { return 1.0 / v; }
 
+// The FP64 collision in pair form (the same update as collide_node's FP32 path
+// in exact arithmetic, with fewer operations on the FP64 pipe, which bounds the
+// FP64 storages).  The equilibrium of Eq. (equilibrium) gives each pair of
+// opposite directions i, i' a common even part E_i and odd parts +-(e_i . j) w_i:
+//   E_1 = E_2 = (P0 + Uxx - Uyy / 2) / 3,  E_3 = E_4 = (P0 + Uyy - Uxx / 2) / 3,
+//   E_5 = E_6 = (P0 + V + 3 TG) / 12,      E_7 = E_8 = (P0 + V - 3 TG) / 12,
+// with U = T + G the second moment beyond P0 (T: rho u u and the lambda terms,
+// G: kappa times the gradient products), V = Txx + Tyy - (Gxx + Gyy) / 2 and
+// TG = Txy + Gxy; the collision adds (1 - omega) / 4 times the stress modes'
+// non-equilibrium, +-(pxx - pyy - (Uxx - Uyy)) and +-(pxy - TG), to the even
+// parts; f*_0 = rho - 2 (A_1 + A_3 + A_5 + A_7).  (In FP32 on full population
+// values this form moved phi beyond the method's bar; FP64 rounding is far below
+// it.)
+template <int MODEL, typename A>
+__device__ __forceinline__ void collide_pairs(const Phys<A>& P, const A vr[3][3], const A vp[3][3], const A fa[9],
+                                              A fs[9], A ge[9]) {
+  constexpr bool BIN = MODEL == MODEL_BINARY;
+  A rdx, rdy, rlap;
+  stencil3(vr, rdx, rdy, rlap);
+  const A rho = vr[1][1];
+  const A jx = momx(fa), jy = momy(fa);
+  // one reciprocal per node: of rho times the node's other divisor (binary:
+  // 6 nu + 1 of Eq. (nu); liquid-gas: 1 - b rho of the van der Waals p0)
+  A inv, P0, gpx, gpy, lam, omega, ux, uy;
+  if constexpr (BIN) {
+    A pdx, pdy, plap;
+    stencil3(vp, pdx, pdy, plap);
+    const A phi = vp[1][1];
+    const A phi2 = phi * phi;
+    const A p0 = rho * A(1.0 / 3.0) + P.Acoef * (A(-0.5) * phi2 + A(0.75) * phi2 * phi2);
+    const A mu = P.Acoef * (phi2 * phi - phi) - P.kappa * plap;
+    const A nu = local_nu_binary(P, phi);
+    const A s6 = fma(A(6), nu, A(1));
+    const A r = rcp_rn(rho * s6);
+    inv = s6 * r;
+    omega = A(2) * (rho * r);
+    ux = jx * inv;
+    uy = jy * inv;
+    P0 = p0 - P.kappa * phi * plap;
+    gpx = pdx;
+    gpy = pdy;
+    lam = P.lambda_scale * nu;
+    geq9<A>(phi, ux, uy, A(2) * P.M * mu, ge);
+  } else {
+    const A q = A(1) - P.b * rho;
+    const A r = rcp_rn(rho * q);
+    inv = q * r;
+    ux = jx * inv;
+    uy = jy * inv;
+    const A p0 = rho * P.T * (rho * r) - P.a * rho * rho;
+    omega = P.omega;  // 2 / (6 nu + 1), one viscosity
+    P0 = p0 - P.kappa * rho * rlap;
+    gpx = rdx;
+    gpy = rdy;
+    lam = P.lambda_scale * P.nu;
+  }
+  const A ax = ux * rdx, ay = uy * rdy;
+  const A udr = ax + ay;
+  const A Txx = jx * ux + lam * (A(2) * ax + udr);
+  const A Tyy = jy * uy + lam * (A(2) * ay + udr);
+  const A Txy = jx * uy + lam * (ux * rdy + uy * rdx);
+  const A kx = P.kappa * gpx, ky = P.kappa * gpy;
+  const A Uxx = Txx + kx * gpx, Uyy = Tyy + ky * gpy;
+  const A V = (Txx + Tyy) - A(0.5) * (kx * gpx + ky * gpy);
+  const A TG = Txy + kx * gpy;
+  const A c = (A(1) - omega) * A(0.25);
+  const A dxx = c * (((fa[1] + fa[2]) - (fa[3] + fa[4])) - (Uxx - Uyy));
+  const A dxy = c * (((fa[5] + fa[6]) - (fa[7] + fa[8])) - TG);
+  const A A1 = (P0 + (Uxx - A(0.5) * Uyy)) * A(1.0 / 3.0) + dxx;
+  const A A3 = (P0 + (Uyy - A(0.5) * Uxx)) * A(1.0 / 3.0) - dxx;
+  const A W3 = A(3) * TG;
+  const A A5 = (P0 + (V + W3)) * A(1.0 / 12.0) + dxy;
+  const A A7 = (P0 + (V - W3)) * A(1.0 / 12.0) - dxy;
+  const A bx = jx * A(1.0 / 3.0), by = jy * A(1.0 / 3.0);
+  const A bp = (jx + jy) * A(1.0 / 12.0), bm = (jy - jx) * A(1.0 / 12.0);
+  fs[1] = A1 + bx; fs[2] = A1 - bx;
+  fs[3] = A3 + by; fs[4] = A3 - by;
+  fs[5] = A5 + bp; fs[6] = A5 - bp;
+  fs[7] = A7 + bm; fs[8] = A7 - bm;
+  fs[0] = rho - A(2) * ((A1 + A3) + (A5 + A7));
+}
+
 // Per-node update shared by both step kernels: wall ghosts and rest rule (for
 // boundary nodes), stencils, local thermodynamics, equilibria and the
 // moment-space collision.  vr/vp: 3x3 rho/phi neighbourhoods (raw values at
@@ -499,6 +584,10 @@ __device__ __forceinline__ void collide_node(const Phys<A>& P, A vr[3][3], A vp[
     apply_ghosts(vr, sol, BIN ? A(0) : P.h);
     if (BIN) apply_ghosts(vp, sol, P.h);
     rest(fa);
+  }
+  if constexpr (std::is_same<A, double>::value) {
+    collide_pairs<MODEL>(P, vr, vp, fa, fs, ge);
+    return;
   }
   A rdx, rdy, rlap;
   stencil3(vr, rdx, rdy, rlap);

@@ -25,6 +25,7 @@ static Phys<A> to_phys(const OpArgs& a) {
   p.nu = A(a.nu); p.lambda_scale = A(a.lambda_scale); p.h = A(a.h);
   p.lut = A(a.lut);
   p.lut_inv = a.lut > 0 ? A(1.0 / a.lut) : A(0);
+  p.omega = A(2.0 / (6.0 * a.nu + 1.0));
   return p;
 }
 
