@@ -33,5 +33,5 @@ def test_bench_options():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True,
                          text=True, timeout=120, cwd=ROOT).stdout
     for opt in ("--gpus", "--steps", "--warmup", "--impl", "--tile", "--storage", "--profile", "--no-cpu-baseline",
-                "--no-batch", "--no-surrogate"):
+                "--no-batch", "--no-surrogate", "--workload", "lg_16384x256", "f32b"):
         assert opt in out, opt
