@@ -116,9 +116,15 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """Hash of the step kernel's code (comments and blank space removed, so that a comment
+    edit keeps a capture valid)."""
+    import re
     h = hashlib.sha256()
     for f in ("lb_device.cuh", "lb_step_tma.cuh", "lb_ops_impl.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_0911_0459_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_0911_0459_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
