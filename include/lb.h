@@ -98,11 +98,13 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
  * identical results), in blocks of 32 consecutive nodes n = y nx + x: block
  * b = n / 32 holds f_0..f_8 and then g_0..g_8 of its nodes, 32 consecutive
  * values per population, so f_i of node n is float element
- * 576 b + 32 i + n % 32 of the state and g_i is 288 elements further
- * (lb_save_state writes this layout).  A row of a tile with its halo is then
- * one contiguous range, which the staged step kernel fetches with one bulk copy
- * per row instead of one per population plane.  Needs nx % 32 == 0; at most
- * 238609294 nodes (18 nx ny < 2^32). */
+ * 576 b + 32 i + n % 32 of the state and g_i is 288 elements further; the last
+ * block is padded, so the state holds 18 * 32 * ceil(nx ny / 32) floats
+ * (lb_save_state writes this layout).  A row of a tile with its neighbour
+ * columns is then one contiguous range of blocks, which the staged step kernel
+ * fetches with one bulk copy per row (plus one block at an x-wrap) instead of one
+ * copy per population plane; any nx.  At most 238609280 nodes
+ * (18 * 32 * ceil(nx ny / 32) < 2^32). */
 typedef enum {
   LB_STORAGE_F64 = 0,
   LB_STORAGE_F32 = 1,
@@ -299,9 +301,9 @@ lb_status lb_fp64_fma_rate(void *stream, double *tflops);
 typedef struct lb_batch lb_batch;
 
 /* n lattices, each described as for lb_create (all binary, one common
- * storage: LB_STORAGE_F64, LB_STORAGE_F32, LB_STORAGE_F16DEV or
- * LB_STORAGE_MOMENTS), each set to the default initial state.  *out set only on
- * LB_OK. */
+ * storage: LB_STORAGE_F64, LB_STORAGE_F32, LB_STORAGE_F32_BLOCKED,
+ * LB_STORAGE_F16DEV or LB_STORAGE_MOMENTS), each set to the default initial
+ * state.  *out set only on LB_OK. */
 lb_status lb_batch_create(int n, const lb_grid *grids, const lb_walls *walls, const lb_params *params,
                           const lb_alloc *alloc, void *stream, lb_batch **out);
 void lb_batch_destroy(lb_batch *b);

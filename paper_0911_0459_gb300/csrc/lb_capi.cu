@@ -112,6 +112,13 @@ static OpsFn pick_ops(int model, int storage) {
   return NULL;
 }
 
+// The staged population kernel applies: 16-byte aligned rows of the planar
+// storages (nx % 8 == 0) and 32-bit offsets; the block storage stages whole
+// blocks at any nx (its node limit is checked at creation).
+static bool staged_ok(int storage, int nx, int ny) {
+  return storage == LB_STORAGE_F32_BLOCKED || staged_fits(nx, ny);
+}
+
 static OpArgs base_args(const lb_ctx* c) {
   OpArgs a;
   memset(&a, 0, sizeof a);
@@ -130,7 +137,7 @@ static OpArgs base_args(const lb_ctx* c) {
   a.thr = p.model == LB_MODEL_LIQUID_GAS ? 0.5 * (p.rho_l + p.rho_g) : 0.0;
   a.bx = c->tile_x;
   a.yc = c->tile_y;
-  a.staged = c->kernel == 2 || (c->kernel == 0 && staged_fits(c->grid.nx, c->grid.ny));
+  a.staged = c->kernel == 2 || (c->kernel == 0 && staged_ok(c->prm.storage, c->grid.nx, c->grid.ny));
   a.deep = c->deep;
   a.err = c->errflag;
   return a;
@@ -200,7 +207,7 @@ static size_t state_bytes(int model, int storage, size_t N, size_t* fb, size_t* 
     return *fb;
   }
   if (storage == LB_STORAGE_F32_BLOCKED) {  // f and g of every 32-node block together, in the f buffer
-    *fb = 18 * N * sizeof(float);
+    *fb = 18 * ((N + 31) / 32 * 32) * sizeof(float);
     *gb = 0;
     *g0b = 0;
     return *fb;
@@ -221,10 +228,8 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
     return set_err(c, "the moment storage holds at most 715827882 nodes"), LB_ERR_ARG;
   if (p->storage == LB_STORAGE_F32_GELIM && 10ull * g->nx * g->ny >= (1ull << 32))
     return set_err(c, "the g-eliminated storage holds at most 429496729 nodes"), LB_ERR_ARG;
-  if (p->storage == LB_STORAGE_F32_BLOCKED && g->nx % 32 != 0)
-    return set_err(c, "the block storage needs nx %% 32 == 0"), LB_ERR_ARG;
-  if (p->storage == LB_STORAGE_F32_BLOCKED && 18ull * g->nx * g->ny >= (1ull << 32))
-    return set_err(c, "the block storage holds at most 238609294 nodes"), LB_ERR_ARG;
+  if (p->storage == LB_STORAGE_F32_BLOCKED && 18ull * (((unsigned long long)g->nx * g->ny + 31) / 32 * 32) >= (1ull << 32))
+    return set_err(c, "the block storage holds at most 238609280 nodes"), LB_ERR_ARG;
   if (w->tube_len < 0 || w->tube_len > g->nx) return set_err(c, "tube_len outside [0, nx]"), LB_ERR_ARG;
   if (w->tube_len > 0) {
     if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny)
@@ -625,7 +630,7 @@ lb_status lb_get_kernel(const lb_ctx* c, int* variant) {
     *variant = 4;
     return LB_OK;
   }
-  const int k = c->kernel == 0 ? (staged_fits(c->grid.nx, c->grid.ny) ? 2 : 1) : c->kernel;
+  const int k = c->kernel == 0 ? (staged_ok(c->prm.storage, c->grid.nx, c->grid.ny) ? 2 : 1) : c->kernel;
   *variant = k == 2 && c->deep ? 3 : k;
   return LB_OK;
 }
@@ -636,10 +641,10 @@ lb_status lb_set_kernel(lb_ctx* c, int variant) {
     return set_err(c, "this storage has one step kernel (variant 4)"), LB_ERR_ARG;
   if (pull_storage(c->prm.storage)) return LB_OK;
   if (variant < 0 || variant > 3) return set_err(c, "kernel variant must be 0, 1, 2 or 3"), LB_ERR_ARG;
-  if (variant >= 2 && c->grid.nx % 8 != 0)
-    return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
-  if (variant >= 2 && !staged_fits(c->grid.nx, c->grid.ny))
+  if (variant >= 2 && !staged_ok(c->prm.storage, c->grid.nx, c->grid.ny)) {
+    if (c->grid.nx % 8 != 0) return set_err(c, "the staged kernel needs nx %% 8 == 0"), LB_ERR_ARG;
     return set_err(c, "the staged kernel holds at most 477218588 nodes"), LB_ERR_ARG;
+  }
   const int kernel = variant == 3 ? 2 : variant;
   const int deep = variant == 3 ? 1 : (variant == 2 ? 0 : c->deep);
   if (kernel != c->kernel || deep != c->deep) {
@@ -706,7 +711,7 @@ lb_status lb_autotune(lb_ctx* c, int* tile_x, int* tile_y, double* us_per_step) 
   const int reps = 10, trials = 3;  // each candidate: best of 3 timings of 10 steps
   // variants: sliding window, staged (shallow ring), staged (deep ring); the staged
   // kernel only where it fits (16-byte aligned rows, 32-bit offsets)
-  const int nk = moments ? 1 : (staged_fits(c->grid.nx, c->grid.ny) ? 3 : 1);
+  const int nk = moments ? 1 : (staged_ok(c->prm.storage, c->grid.nx, c->grid.ny) ? 3 : 1);
   for (int ik = 0; ik < nk && e == cudaSuccess && st == LB_OK; ++ik)
   for (int ix = 0; ix < 3 && e == cudaSuccess && st == LB_OK; ++ix)
     for (size_t iy = 0; iy < cand_y.size() && e == cudaSuccess && st == LB_OK; ++iy) {

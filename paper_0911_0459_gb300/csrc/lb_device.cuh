@@ -260,51 +260,55 @@ struct SF16 {
 // buffer and g_i lies 288 elements further (Buf::g = Buf::f + 288).  With
 // nx % 32 == 0 the nodes of a row segment of whole blocks, all eighteen
 // populations, are one contiguous range, which the staged step kernel copies
-// with a single bulk copy per row.  Same values and arithmetic as SF32.
+// with a single bulk copy per row (other widths: the whole blocks over the
+// segment, and one more block at an x-wrap).  The last block is padded to 32
+// nodes.  Same values and arithmetic as SF32.
 struct SF32B {
   using T = float;
   using A = float;
   static constexpr int kBlock = 576;  // elements per block of 32 nodes
   __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
   __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  // elements of a state of N nodes (the last block padded)
+  __device__ static unsigned long long lim(unsigned long long N) { return 18ull * ((N + 31) & ~31ull); }
   // shared-memory stage of whole blocks: stage column c lies in block c / 32
   __device__ static A pf(const T* f, int, int c, int i, const Rest&) { return f[(c >> 5) * kBlock + 32 * i + (c & 31)]; }
   __device__ static A pg(const T* g, const float*, int, int c, int i) { return g[(c >> 5) * kBlock + 32 * i + (c & 31)]; }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
-    LB_GUARD(at(n, i), 18 * N, A(0));
+    LB_GUARD(at(n, i), lim(N), A(0));
     return __ldg(f + at(n, i));
   }
   __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest&) {
-    LB_GUARD(at(n, i), 18 * N, );
+    LB_GUARD(at(n, i), lim(N), );
     f[at(n, i)] = v;
   }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
-    LB_GUARD(at(n, i), 18 * N - 288, A(0));
+    LB_GUARD(at(n, i), lim(N) - 288, A(0));
     return __ldg(g + at(n, i));
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) {
-    LB_GUARD(at(n, i), 18 * N - 288, );
+    LB_GUARD(at(n, i), lim(N) - 288, );
     g[at(n, i)] = v;
   }
   __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) {
-    LB_GUARD(at(n, i), 18 * N, A(0));
+    LB_GUARD(at(n, i), lim(N), A(0));
     return __ldcg(f + at(n, i));
   }
   __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) {
-    LB_GUARD(at(n, i), 18 * N - 288, A(0));
+    LB_GUARD(at(n, i), lim(N) - 288, A(0));
     return __ldcg(g + at(n, i));
   }
   // 32-bit element offsets (needs 18 N < 2^32)
   __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
-    LB_GUARD(at32(n, i), 18ull * N, );
+    LB_GUARD(at32(n, i), lim(N), );
     f[at32(n, i)] = v;
   }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
-    LB_GUARD(at32(n, i), 18ull * N - 288, );
+    LB_GUARD(at32(n, i), lim(N) - 288, );
     g[at32(n, i)] = v;
   }
   __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
-    LB_GUARD(at(n, i), 18 * N, );
+    LB_GUARD(at(n, i), lim(N), );
     f[at(n, i)] = 0.0f;
   }
 };

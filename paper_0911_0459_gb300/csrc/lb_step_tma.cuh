@@ -141,6 +141,34 @@ struct TmaLayout {
   static_assert(!BLK || BIN, "the block storage holds the binary model");
 };
 
+// Block storage, rows that need not start on a block boundary (nx % 32 != 0):
+// row rowoff's staged range is the whole blocks over nodes lo .. hi, the tile's
+// columns with the neighbour column on either side that is not an x-wrap, at
+// stage blocks 0, 1, ...; a tile at one end of a row that does not hold the whole
+// row also stages the block of the wrapped neighbour (the row's last node for the
+// first tile, its first node for the last) at stage block BX / 32 + 1.  Such a
+// tile's range holds at most w + 1 <= BX + 1 nodes, so at most BX / 32 + 1 blocks;
+// an interior tile's at most BX / 32 + 2.
+template <int BX>
+struct BlkRow {
+  static constexpr int kSpare = (BX / 32 + 1) * 32;  // stage column of the spare block
+  int sbase;       // node at stage column 0
+  unsigned span;   // nodes the range's blocks cover
+  int spare_node;  // node whose block is the spare (-1: none)
+  __device__ BlkRow(int rowoff, int xb, int w, int nx) {
+    const int lo = rowoff + (xb > 0 ? xb - 1 : 0);
+    const int hi = rowoff + (xb + w < nx ? xb + w : nx - 1);
+    sbase = lo & ~31;
+    span = (unsigned)(((hi >> 5) + 1) * 32 - sbase);
+    spare_node = w >= nx ? -1 : (xb == 0 ? rowoff + nx - 1 : (xb + w == nx ? rowoff : -1));
+  }
+  // stage column of node n (in the range, else in the spare block)
+  __device__ int col(int n) const {
+    const unsigned d = (unsigned)(n - sbase);
+    return d < span ? (int)d : kSpare + (n & 31);
+  }
+};
+
 template <int MODEL, class S>
 struct TmaArgs {
   Geom G;
@@ -247,14 +275,32 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       continue;
     }
     const size_t rowoff = (size_t)yy * nx;
-    mbar_arrive_expect_tx(&R.full[s], total);
     if constexpr (L::BLK) {
+      if (nx % 32 != 0) {
+        // rows that start inside a block: the range's whole blocks, and the block
+        // of a wrapped neighbour outside it
+        constexpr int B = SF32B::kBlock;
+        const BlkRow<BX> br((int)rowoff, xb, w, nx);
+        const int nb = (int)(br.span / 32);
+        const uint32_t bytes = (uint32_t)(nb + (br.spare_node >= 0 ? 1 : 0)) * B * (uint32_t)sizeof(float);
+        const size_t lim = 18 * (((size_t)N + 31) & ~(size_t)31);
+        mbar_arrive_expect_tx(&R.full[s], bytes);
+        bulk_g2s(R.f(s), copy_src(src.f, (size_t)(br.sbase / 32) * B, (size_t)nb * B, lim),
+                 (uint32_t)nb * B * sizeof(float), &R.full[s]);
+        if (br.spare_node >= 0)
+          bulk_g2s(R.f(s) + (BlkRow<BX>::kSpare / 32) * B, copy_src(src.f, (size_t)(br.spare_node / 32) * B, B, lim),
+                   B * sizeof(float), &R.full[s]);
+        issued = k + 1;
+        continue;
+      }
+      mbar_arrive_expect_tx(&R.full[s], total);
       blocks(R.f(s), rowoff + lo, ncols, so, &R.full[s]);
       if (wl) blocks(R.f(s), rowoff + (nx - H), H, 0, &R.full[s]);
       if (wr) blocks(R.f(s), rowoff, H, sr, &R.full[s]);
       issued = k + 1;
       continue;
     }
+    mbar_arrive_expect_tx(&R.full[s], total);
     planes(src.f, L::NF, R.f(s), rowoff, &R.full[s]);
     if (BIN) planes(src.g, L::NG, R.g(s), rowoff, &R.full[s]);
     if (L::NG0) {
@@ -315,19 +361,37 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   // Sum this lane's column (f, g keep its populations for the collision); the edge
   // lanes also sum the warp's halo column; then take the neighbours by shuffles.
   // A row solid under all the warp's columns (skip) is left unread.
-  auto sums = [&](int s, A f[9], A g[9], Row& Rw, bool skip) {
+  // Block storage with rows that start inside a block: this lane's stage columns
+  // (own node, edge column) in the row of lattice row yr.  Elsewhere they are sc, sx.
+  [[maybe_unused]] const bool blk_rows = L::BLK && nx % 32 != 0;
+  [[maybe_unused]] auto row_cols = [&](int yr, int& co, int& ce) {
+    const int rowoff = wrapi(yr, ny) * nx;
+    const BlkRow<BX> br(rowoff, xb, w, nx);
+    // a lane past the row's end stands for the wrapped column (the last active
+    // lane's right neighbour); lanes further on feed no active lane
+    const int xw = x < nx ? x : (x - nx < nx ? x - nx : 0);
+    const int t = lane == 0 ? (x == 0 ? nx - 1 : x - 1) : x + 1;
+    const int xe = t < nx ? t : (t - nx < nx ? t - nx : 0);
+    co = br.col(rowoff + xw);
+    ce = br.col(rowoff + xe);
+  };
+  auto sums = [&](int s, A f[9], A g[9], Row& Rw, bool skip, int yr) {
     if (skip) {
       Rw.rc = Rw.rl = Rw.rr = A(0);
       Rw.pc = Rw.pl = Rw.pr = A(0);
       return;
     }
-    load_pop(s, sc, f, g);
+    int co = sc, ce = sx;
+    if constexpr (L::BLK) {
+      if (blk_rows) row_cols(yr, co, ce);
+    }
+    load_pop(s, co, f, g);
     const A r = sum9(f);
     const A p = BIN ? sum9(g) : A(0);
     A re = A(0), pe = A(0);
     if (edge) {
       A fe[9], ge[9];
-      load_pop(s, sx, fe, ge);
+      load_pop(s, ce, fe, ge);
       re = sum9(fe);
       pe = BIN ? sum9(ge) : A(0);
     }
@@ -366,7 +430,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   for (int j = 0; j < 2; ++j) {
     const unsigned k = kbase + j;
     if (!__all_sync(0xffffffffu, mbar_wait(&R.full[k % NS], (k / NS) & 1))) return false;
-    sums(k % NS, fa, ga, Rw[j + 1], solid_row(y0 - 1 + j));
+    sums(k % NS, fa, ga, Rw[j + 1], solid_row(y0 - 1 + j), y0 - 1 + j);
     // the populations are in registers now: the stage can be refilled
     __syncwarp();
     if (lane == 0) mbar_arrive(&R.empty[k % NS]);
@@ -385,7 +449,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     Rw[1] = Rw[2];
     if (!__all_sync(0xffffffffu, mbar_wait(&R.full[sn], (kn / NS) & 1))) return false;
     A fn[9], gn[9];
-    sums(sn, fn, gn, Rw[2], CW && solid_row(y + 1));
+    sums(sn, fn, gn, Rw[2], CW && solid_row(y + 1), y + 1);
     __syncwarp();
     if (lane == 0) mbar_arrive(&R.empty[sn]);
     A vr[3][3], vp[3][3];

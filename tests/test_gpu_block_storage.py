@@ -4,8 +4,11 @@ The block storage keeps the values of the FP32 population storage in another ord
 (f_i of node n at float 576 (n // 32) + 32 i + n % 32, g_i 288 further) and runs the
 same arithmetic, so every result equals the FP32 storage's bit for bit: states after
 many steps in every kernel variant and tile, through walls, the x-wrap and ragged last
-tiles, the reductions and the fields.  One step from a random state also matches the
-FP64 oracle within FP32's 2e-6 per population, as the FP32 storage does.
+tiles, the reductions and the fields, for rows that start on a block boundary
+(nx % 32 == 0) and rows that do not (then a staged row is the whole blocks over its
+nodes, and the x-wrap neighbour's block is staged apart).  One step from a random
+state also matches the FP64 oracle within FP32's 2e-6 per population, as the FP32
+storage does.
 """
 import numpy as np
 import pytest
@@ -31,6 +34,15 @@ GEOMS = {
     "periodic": lambda p: W.periodic_box(64, 29, p),
     # the fewest rows a tube allows
     "three_rows": lambda p: W.Capillary("b3", 96, 3, 10, 60, 0, 2, 4, 5, p, wall_grad=-0.1),
+    # rows that start inside a block
+    "unaligned_ragged": lambda p: W.Capillary("u1", 203, 37, 61, 120, 5, 27, 12, 8, p, wall_grad=-0.11),
+    "unaligned_tube_wraps": lambda p: W.Capillary("u2", 150, 30, 100, 90, 27, 20, 0, 0, p, wall_grad=-0.1),
+    "unaligned_channel": lambda p: W.channel(131, 19, 15, p, wall_grad=-0.15),
+    "unaligned_periodic": lambda p: W.periodic_box(77, 29, p),
+    "unaligned_three_rows": lambda p: W.Capillary("u3", 45, 3, 10, 25, 0, 2, 4, 5, p, wall_grad=-0.1),
+    "unaligned_narrow": lambda p: W.Capillary("u4", 20, 12, 6, 10, 2, 7, 2, 3, p, wall_grad=-0.2),
+    # two tiles of 256 and a one-column remainder at the end of every row
+    "unaligned_one_column_tail": lambda p: W.Capillary("u5", 513, 9, 100, 300, 1, 6, 20, 10, p, wall_grad=-0.1),
 }
 # (variant, tile): sliding window, staged shallow ring at three widths, staged deep ring
 RUNS = [(1, (128, 16)), (2, (256, 8)), (2, (128, 5)), (2, (64, 1)), (3, (256, 16))]
@@ -39,8 +51,9 @@ RUNS = [(1, (128, 16)), (2, (256, 8)), (2, (128, 5)), (2, (64, 1)), (3, (256, 16
 def to_planes(state, nx, ny):
     """The block storage's saved state as the FP32 storage's (f planes, then g planes)."""
     N = nx * ny
-    b = np.frombuffer(state.tobytes(), dtype=np.float32).reshape(N // 32, 18, 32)
-    return np.ascontiguousarray(b.transpose(1, 0, 2)).reshape(18 * N)
+    nb = (N + 31) // 32
+    b = np.frombuffer(state.tobytes(), dtype=np.float32).reshape(nb, 18, 32)
+    return np.ascontiguousarray(b.transpose(1, 0, 2)).reshape(18, nb * 32)[:, :N].reshape(18 * N)
 
 
 def planes(lat):
@@ -56,12 +69,12 @@ def assert_same_state(blk, ref, nx, ny):
 def test_saved_state_follows_the_documented_layout():
     """lb_save_state of the block storage holds f_i of node n at float 576 (n // 32) +
     32 i + n % 32 and g_i 288 floats further: read back against lb_get_populations."""
-    cap = GEOMS["capillary_ragged"](W.binary_params(nu_l=0.7, nu_g=0.05))
+    cap = GEOMS["unaligned_ragged"](W.binary_params(nu_l=0.7, nu_g=0.05))
     lat = Lattice.from_workload(cap, storage=STORAGE_F32_BLOCKED)
     lat.step(37)
     f, g = lat.populations(rested=False)
     st = np.frombuffer(lat.save_state()[0].tobytes(), dtype=np.float32)
-    assert st.size == 18 * cap.nx * cap.ny
+    assert st.size == 18 * 32 * ((cap.nx * cap.ny + 31) // 32)
     n = np.arange(cap.nx * cap.ny)
     for i in range(9):
         assert np.array_equal(st[576 * (n // 32) + 32 * i + n % 32].astype(np.float64), f[i].ravel())

@@ -3,7 +3,8 @@
 In that build every global load and store of the step kernels checks its index against
 its buffer; an index outside would be counted and skipped.  Small lattices of every
 model and storage run through every step kernel (the staged and the sliding-window
-population kernels with both ring depths, the pull kernel of the reduced states) and
+population kernels with both ring depths, on the planar storages and on the 32-node
+block storage with aligned and unaligned rows, the pull kernel of the reduced states) and
 through the batch bodies, in a child process that loads the checked library; every
 counter must stay at zero, and the states must equal bit for bit those of the normal
 build (the checks change nothing for accesses inside their buffers)."""
@@ -55,6 +56,11 @@ for st in (0, 1, 2):             # FP64, FP32, FP16 deviations: sliding window, 
     for nm, c in (("c8", cap8), ("cw", capw)):
         lattice(f"bin{st}_{nm}", c, st, (1, 2, 3), tiles)
     lattice(f"bin{st}_cr", capr, st, (1,), tiles)
+cap96 = W.Capillary("c9", 96, 24, 24, 64, 3, 18, 8, 6, bp, theta_deg=45.0)       # nx % 32 == 0
+tail = W.Capillary("ct", 513, 9, 100, 300, 1, 6, 20, 10, bp, wall_grad=-0.1)      # one-column last tile
+for nm, c in (("c96", cap96), ("cw", capw), ("cr", capr), ("nw", narrow), ("ct", tail)):
+    # FP32 in 32-node blocks: aligned and unaligned rows, every kernel variant
+    lattice(f"blk_{nm}", c, 6, (1, 2, 3), tiles)
 for st in (3, 4, 5):             # the pull kernel's reduced states
     for nm, c in (("c8", cap8), ("cw", capw), ("cr", capr), ("nw", narrow)):
         lattice(f"pull{st}_{nm}", c, st, (4,), tiles)
