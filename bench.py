@@ -314,7 +314,7 @@ def run_reference(args, rank, world):
 
 def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
     """The seeded sweep of 256 uneven binary capillaries (H 16..128, tube 1024..8192,
-    ratios 1..100, 30..80 degrees), FP32: one persistent CUDA-graph launch per
+    ratios 1..100, 30..80 degrees) in the given storage: one persistent CUDA-graph launch per
     sampled run for all capillaries against one lattice per capillary run in
     turn (same storage), both with l(t) sampled 4 times over `steps` steps."""
     from paper_0911_0459_gb300 import Batch, shard
@@ -373,7 +373,8 @@ def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
         t_batch, t_seq, t_one, fluid = float(mx[0]), float(mx[1]), float(mx[2]), int(sm[3])
     cs_batch = n * steps / t_batch
     cs_seq = n * steps / t_seq
-    return {"speedup_vs_single_lattice_path": cs_batch / cs_seq,
+    return {"storage": {None: "workload's", 1: "FP32 planes", 3: "FP32 moments", 6: "FP32 in 32-node blocks"}.get(storage),
+            "speedup_vs_single_lattice_path": cs_batch / cs_seq,
             "speedup_vs_one_launch_per_run": t_one / t_batch,
             "capillary_steps_per_s": cs_batch, "sequential_capillary_steps_per_s": cs_seq,
             "capillaries_per_s_at_20k_steps_extrapolated": cs_batch / 20000.0,
@@ -697,7 +698,9 @@ def main():
         secondary["error"] = repr(ex)
     if not args.no_batch:
         try:
-            secondary["batched_sweep_256"] = batched_vs_sequential(torch, Lattice, args.batch_steps)
+            # FP32 populations in 32-node blocks (the same bits as the planar FP32 storage)
+            secondary["batched_sweep_256"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
+                                                                   storage=STORAGE_F32_BLOCKED)
             secondary["batched_sweep_256_moments"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
                                                                            storage=STORAGE_MOMENTS)
         except Exception as ex:

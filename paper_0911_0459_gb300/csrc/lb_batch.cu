@@ -116,7 +116,8 @@ static void bfree_all(lb_batch* b) {
 }
 
 static size_t elem_size(int storage) {
-  return storage == LB_STORAGE_F64 ? 8 : ((storage == LB_STORAGE_F32 || storage == LB_STORAGE_MOMENTS) ? 4 : 2);
+  return storage == LB_STORAGE_F64 ? 8
+       : ((storage == LB_STORAGE_F32 || storage == LB_STORAGE_MOMENTS || storage == LB_STORAGE_F32_BLOCKED) ? 4 : 2);
 }
 
 // Columns of a tile of tile_x threads (the moment kernel's warps produce 30).
@@ -147,7 +148,8 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
   const size_t el = elem_size(b->storage);
   OpBufs ob;
   ob.f = (char*)b->f[k] + b->off_f[i] * el;
-  ob.g = b->g[k] ? (char*)b->g[k] + b->off_g[i] * el : NULL;
+  ob.g = b->storage == LB_STORAGE_F32_BLOCKED ? (char*)ob.f + 288 * el  // g beside f in every block
+                                              : (b->g[k] ? (char*)b->g[k] + b->off_g[i] * el : NULL);
   ob.g0 = b->g0[k] ? b->g0[k] + b->off_g0[i] : NULL;
   a.src = ob;
   a.dst = ob;
@@ -156,6 +158,7 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
 
 static OpsFn batch_ops(int storage) {
   if (storage == LB_STORAGE_MOMENTS) return ops_bin_m32;
+  if (storage == LB_STORAGE_F32_BLOCKED) return ops_bin_f32b;
   return storage == LB_STORAGE_F64 ? ops_bin_f64 : (storage == LB_STORAGE_F32 ? ops_bin_f32 : ops_bin_f16);
 }
 
@@ -300,6 +303,7 @@ static cudaError_t run_batch(lb_batch* b, int nsteps, cudaStream_t s, int* per) 
   }
   if (b->storage == LB_STORAGE_F64) return run_s<SF64>(b, nsteps, s, per);
   if (b->storage == LB_STORAGE_F32) return run_s<SF32>(b, nsteps, s, per);
+  if (b->storage == LB_STORAGE_F32_BLOCKED) return run_s<SF32B>(b, nsteps, s, per);
   return run_s<SF16>(b, nsteps, s, per);
 }
 
@@ -431,6 +435,7 @@ static cudaError_t launch_reduce(lb_batch* b, int buf, int nsamples, int col, do
   if (b->storage == LB_STORAGE_MOMENTS) return launch_reduce_s<SM32>(b, buf, nsamples, col, out, s);
   if (b->storage == LB_STORAGE_F64) return launch_reduce_s<SF64>(b, buf, nsamples, col, out, s);
   if (b->storage == LB_STORAGE_F32) return launch_reduce_s<SF32>(b, buf, nsamples, col, out, s);
+  if (b->storage == LB_STORAGE_F32_BLOCKED) return launch_reduce_s<SF32B>(b, buf, nsamples, col, out, s);
   return launch_reduce_s<SF16>(b, buf, nsamples, col, out, s);
 }
 
@@ -489,7 +494,7 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   *out = NULL;
   const int storage = params[0].storage;
   if (storage != LB_STORAGE_F64 && storage != LB_STORAGE_F32 && storage != LB_STORAGE_F16DEV &&
-      storage != LB_STORAGE_MOMENTS)
+      storage != LB_STORAGE_MOMENTS && storage != LB_STORAGE_F32_BLOCKED)
     return berr(NULL, "unknown storage %d", storage), LB_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (params[i].model != LB_MODEL_BINARY) return berr(NULL, "batches hold binary lattices"), LB_ERR_ARG;
@@ -499,6 +504,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
     if (g.nx < 3 || g.ny < 3 || (long)g.nx * g.ny > (1L << 31) - 1) return berr(NULL, "lattice %d: bad grid", i), LB_ERR_ARG;
     if (storage == LB_STORAGE_MOMENTS && (unsigned long long)M_PLANES * g.nx * g.ny >= (1ull << 32))
       return berr(NULL, "lattice %d: the moment storage holds at most 715827882 nodes", i), LB_ERR_ARG;
+    if (storage == LB_STORAGE_F32_BLOCKED && 18ull * (((unsigned long long)g.nx * g.ny + 31) / 32 * 32) >= (1ull << 32))
+      return berr(NULL, "lattice %d: the block storage holds at most 238609280 nodes", i), LB_ERR_ARG;
     if (!isfinite(w.wall_grad)) return berr(NULL, "lattice %d: wall_grad not finite", i), LB_ERR_ARG;
     if (!(params[i].M >= 0)) return berr(NULL, "lattice %d: mobility must be >= 0", i), LB_ERR_ARG;
     if (w.tube_len < 0 || w.tube_len > g.nx) return berr(NULL, "lattice %d: tube_len outside [0, nx]", i), LB_ERR_ARG;
@@ -524,7 +531,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   b->tile_x = 128;
   b->tile_y = 8;
   b->staged_ok = 1;
-  for (int i = 0; i < n; ++i) b->staged_ok = b->staged_ok && staged_fits(grids[i].nx, grids[i].ny);
+  for (int i = 0; i < n; ++i)  // the block storage stages whole blocks at any nx
+    b->staged_ok = b->staged_ok && (storage == LB_STORAGE_F32_BLOCKED || staged_fits(grids[i].nx, grids[i].ny));
   b->limit_ns = kDefaultLimitNs;
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     berr(NULL, "cudaStreamCreate failed");
@@ -533,15 +541,16 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   }
   const size_t el = elem_size(storage);
   const int moments = storage == LB_STORAGE_MOMENTS;
+  const int blocked = storage == LB_STORAGE_F32_BLOCKED;  // f and g in 32-node blocks, one arena
   const int nf = moments ? M_PLANES : 9;
-  const int ng = moments ? 0 : (storage == LB_STORAGE_F16DEV ? 8 : 9);
+  const int ng = (moments || blocked) ? 0 : (storage == LB_STORAGE_F16DEV ? 8 : 9);
   size_t of = 0, og = 0, o0 = 0;
   for (int i = 0; i < n; ++i) {
     const size_t N = (size_t)grids[i].nx * grids[i].ny;
     b->off_f.push_back(of);
     b->off_g.push_back(og);
     b->off_g0.push_back(o0);
-    of += (nf * N + 63) / 64 * 64;
+    of += blocked ? (18 * ((N + 31) / 32 * 32) + 63) / 64 * 64 : (nf * N + 63) / 64 * 64;
     og += (ng * N + 63) / 64 * 64;
     o0 += (N + 63) / 64 * 64;
     // solid nodes: the tube's columns outside its band

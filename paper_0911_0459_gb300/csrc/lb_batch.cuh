@@ -90,6 +90,8 @@ struct BatchArgs {
 template <class S>
 __device__ __forceinline__ Buf<S> cap_buf(typename S::T* f, typename S::T* g, float* g0,
                                           const CapDesc<typename S::A>& c) {
+  if constexpr (std::is_same<S, SF32B>::value)  // g beside f in every 32-node block
+    return Buf<S>{f + c.off_f, f + c.off_f + SF32B::kBlock / 2, nullptr, c.r};
   return Buf<S>{f + c.off_f, g ? g + c.off_g : nullptr, g0 ? g0 + c.off_g0 : nullptr, c.r};
 }
 

@@ -114,11 +114,9 @@ def test_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
                                                                setattr(p, "storage", lb.STORAGE_F32_GELIM))
         yield "g eliminated above 429496729 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 6554),
                                                                      setattr(p, "storage", lb.STORAGE_F32_GELIM))
-        yield "block storage with nx % 32 != 0", lambda g, w, p: (setattr(g, "nx", 100),
-                                                                  setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
         yield "liquid-gas in blocks", lambda g, w, p: (setattr(p, "model", 0),
                                                        setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
-        yield "block storage above 238609294 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 3641),
+        yield "block storage above 238609280 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 3641),
                                                                       setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
         yield "unknown storage", lambda g, w, p: setattr(p, "storage", 9)
         yield "tube longer than the grid", lambda g, w, p: setattr(w, "tube_len", 97)
@@ -175,7 +173,9 @@ def test_batch_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "wall gradient NaN": (lambda s: setattr(s[0][1], "wall_grad", float("nan")), None),
         "FP16 moments in a batch": (lambda s: [setattr(x[2], "storage", lb.STORAGE_MOMENTS_F16) for x in s], None),
         "g eliminated in a batch": (lambda s: [setattr(x[2], "storage", lb.STORAGE_F32_GELIM) for x in s], None),
-        "block storage in a batch": (lambda s: [setattr(x[2], "storage", lb.STORAGE_F32_BLOCKED) for x in s], None),
+        "block storage above 238609280 nodes": (lambda s: ([setattr(x[2], "storage", lb.STORAGE_F32_BLOCKED) for x in s],
+                                                          setattr(s[1][0], "nx", 65536), setattr(s[1][0], "ny", 3641),
+                                                          setattr(s[1][1], "tube_len", 0)), None),
         "negative mobility": (setp(0, "M", -1.0), None),
         "viscosity table of one entry": (setp(1, "nu_table", 1), None),
         "tube longer than the grid": (lambda s: setattr(s[1][1], "tube_len", 200), None),

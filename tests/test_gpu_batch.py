@@ -13,7 +13,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STORAGE_MOMENTS, Batch,  # noqa: E402
+from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F64,  # noqa: E402
+                                   STORAGE_MOMENTS, Batch,
                                    Lattice, LbError)
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
 
@@ -29,7 +30,7 @@ def small_sweep(seed=7, n=6, align=8, vary_gamma=False):
 
 
 @pytest.mark.parametrize("body", [1, 2, 3])
-@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F64, STORAGE_F16DEV])
+@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F64, STORAGE_F16DEV])
 def test_batch_is_bitwise_identical_to_independent_lattices(storage, body):
     """Every body of the persistent kernel (sliding window; staged with the
     shallow and the deep ring) against one lattice per capillary, over tiles
@@ -125,6 +126,31 @@ def test_batch_with_unaligned_rows_uses_the_sliding_window_body():
     b.close()
 
 
+@pytest.mark.parametrize("body", [1, 2, 3])
+def test_block_storage_batch_with_unaligned_rows_equals_fp32_lattices(body):
+    """The 32-node block storage stages whole blocks at any nx, so a batch of lattices
+    whose rows start inside blocks runs the staged body too; every lattice equals the
+    planar FP32 storage run alone, bit for bit (the same arithmetic)."""
+    caps = small_sweep(seed=9, n=4, align=1)
+    assert any(c.nx % 32 for c in caps)
+    b = Batch(caps, storage=STORAGE_F32_BLOCKED)
+    assert b.kernel() == 2
+    b.set_kernel(body)
+    for tx, ty in ((64, 4), (128, 16), (256, 64), (128, 5)):
+        b.set_tile(tx, ty)
+        b.step(11)
+    red = b.lengths()
+    for i, c in enumerate(caps):
+        lat = Lattice.from_workload(c, storage=STORAGE_F32)
+        lat.step(b.time)
+        fb, gb = b.populations(i, rested=False)
+        fl, gl = lat.populations(rested=False)
+        assert np.array_equal(fb, fl) and np.array_equal(gb, gl), i
+        assert red[i, 0] == lat.filled_length()["l"], i
+        lat.close()
+    b.close()
+
+
 def test_staged_body_long_run_matches_sliding_body():
     """Many steps in one persistent launch: the ring counter runs across
     hundreds of tiles and steps (and is renormalised) without drifting."""
@@ -201,7 +227,7 @@ def test_grid_barrier_timeout_is_reported_without_hanging(body):
     b2.close()
 
 
-@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_MOMENTS])
+@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_MOMENTS])
 def test_full_sweep_of_256_capillaries_in_the_benchmarked_configuration(storage):
     """The seeded sweep at full size (256 capillaries, H 16..128, tubes 1024..8192,
     about 88 M fluid nodes), autotuned and run through sampled CUDA-graph launches as the
