@@ -379,12 +379,12 @@ def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
             "capillary_steps_per_s": cs_batch, "sequential_capillary_steps_per_s": cs_seq,
             "capillaries_per_s_at_20k_steps_extrapolated": cs_batch / 20000.0,
             "sequential_capillaries_per_s_at_20k_steps_extrapolated": cs_seq / 20000.0,
-            "baselines": "single_lattice_path: each capillary its own lattice on its autotuned single-lattice "
-                         "kernel (64-step CUDA graphs), run in turn; one_launch_per_run: each capillary alone "
+            "baselines": "single_lattice_path: each capillary its own lattice in the same storage on the "
+                         "library's default kernel and tile (the staged kernel where it applies, bands of 16 "
+                         "rows; 64-step CUDA graphs), run in turn; one_launch_per_run: each capillary alone "
                          "in the batch's persistent kernel and tile (a batch of one), launched in turn",
             "GLUPS_batched": fluid * steps / t_batch / 1e9, "fluid_nodes": fluid, "steps": steps,
             "tile": [tx, ty], "l_finite": bool(np.isfinite(out).all()),
-            "storage": "moments (FP32)" if storage == 3 else "FP32 populations",
             "what": f"{steps} steps with 4 l(t) samples, wall clock"}
 
 
@@ -698,9 +698,12 @@ def main():
         secondary["error"] = repr(ex)
     if not args.no_batch:
         try:
-            # FP32 populations in 32-node blocks (the same bits as the planar FP32 storage)
             secondary["batched_sweep_256"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
-                                                                   storage=STORAGE_F32_BLOCKED)
+                                                                   storage=STORAGE_F32)
+            # the same sweep in 32-node blocks (the same bits): the fastest batch, and faster
+            # one-capillary baselines too
+            secondary["batched_sweep_256_blocks"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
+                                                                          storage=STORAGE_F32_BLOCKED)
             secondary["batched_sweep_256_moments"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
                                                                            storage=STORAGE_MOMENTS)
         except Exception as ex:
