@@ -189,7 +189,13 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_ker
           // kernel (parameters that live behind a pointer the pushes might alias led the
           // compiler to fuse multiply-adds differently, a last-bit difference)
           const Phys<typename S::A> P = c.P;
-          ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+          if constexpr (TmaLayout<MODEL_BINARY, S, BX, NS>::BLK) {
+            ok = c.G.nx % 32 != 0
+                     ? consume_tile<MODEL_BINARY, S, BX, NS, true>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane)
+                     : consume_tile<MODEL_BINARY, S, BX, NS, false>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+          } else {
+            ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+          }
         }
       }
       k += (unsigned)(td.y1 - td.y0 + 2);

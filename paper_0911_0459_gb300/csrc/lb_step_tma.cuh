@@ -327,7 +327,10 @@ __device__ void drain_ring(const Ring<MODEL, S, BX, NS>& R, unsigned issued) {
 // Consumer warp `warp` (0 .. BX/32 - 1): collide rows y0 .. y1 - 1 of the tile
 // from ring rows kbase, kbase + 1, ... and push the results to dst.  Returns
 // false (in every lane of the warp) if a wait ran out of time.
-template <int MODEL, class S, int BX, int NS>
+// UROWS: block storage with rows that start inside a block (nx % 32 != 0): the
+// stage columns of a lane change from row to row (a separate instantiation, so
+// that aligned rows keep constant columns and no per-row work).
+template <int MODEL, class S, int BX, int NS, bool UROWS = false>
 __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, const Phys<typename S::A>& P,
                              const Buf<S>& dst, int xb, int y0, int y1, unsigned kbase, int warp, int lane) {
   using L = TmaLayout<MODEL, S, BX, NS>;
@@ -363,7 +366,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   // A row solid under all the warp's columns (skip) is left unread.
   // Block storage with rows that start inside a block: this lane's stage columns
   // (own node, edge column) in the row of lattice row yr.  Elsewhere they are sc, sx.
-  [[maybe_unused]] const bool blk_rows = L::BLK && nx % 32 != 0;
+  constexpr bool BR = L::BLK && UROWS;
   [[maybe_unused]] auto row_cols = [&](int yr, int& co, int& ce) {
     const int rowoff = wrapi(yr, ny) * nx;
     const BlkRow<BX> br(rowoff, xb, w, nx);
@@ -382,9 +385,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       return;
     }
     int co = sc, ce = sx;
-    if constexpr (L::BLK) {
-      if (blk_rows) row_cols(yr, co, ce);
-    }
+    if constexpr (BR) row_cols(yr, co, ce);
     load_pop(s, co, f, g);
     const A r = sum9(f);
     const A p = BIN ? sum9(g) : A(0);
@@ -558,7 +559,14 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) step_tma_kern
     drain_ring<MODEL, S, BX, NS>(R, issued);
     return;
   }
-  if (!consume_tile<MODEL, S, BX, NS>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane) && lane == 0)
+  bool ok;
+  if constexpr (TmaLayout<MODEL, S, BX, NS>::BLK) {
+    ok = a.G.nx % 32 != 0 ? consume_tile<MODEL, S, BX, NS, true>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane)
+                          : consume_tile<MODEL, S, BX, NS, false>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane);
+  } else {
+    ok = consume_tile<MODEL, S, BX, NS>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane);
+  }
+  if (!ok && lane == 0)
     atomicExch(a.err, 1);
 }
 
