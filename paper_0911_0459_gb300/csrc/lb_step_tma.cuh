@@ -327,6 +327,28 @@ __device__ void drain_ring(const Ring<MODEL, S, BX, NS>& R, unsigned issued) {
 // Consumer warp `warp` (0 .. BX/32 - 1): collide rows y0 .. y1 - 1 of the tile
 // from ring rows kbase, kbase + 1, ... and push the results to dst.  Returns
 // false (in every lane of the warp) if a wait ran out of time.
+// Push streaming into the block storage when rows start on block boundaries
+// (nx % 32 == 0): node (x, y)'s populations start at rpart(y) + cpart(x), with
+// rpart = (y nx / 32) * 576 and cpart = (x / 32) * 576 + x % 32, so that every
+// destination costs one add; f_i lies 32 i further and g_i 288 + 32 i.  Bounce-back
+// as in push_node_u32.  lim: elements of the state.
+template <int MODEL>
+__device__ __forceinline__ void push_node_blk(float* __restrict__ f, unsigned long long lim, const uint32_t rpart[3],
+                                              const uint32_t cpart[3], const bool sol[3][3], bool bnd,
+                                              const float fs[9], const float ge[9]) {
+  static_assert(MODEL == MODEL_BINARY, "the block storage holds the binary model");
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int ex = EXd(i), ey = EYd(i);
+    const bool back = bnd && sol[1 + ey][1 + ex];
+    const uint32_t base = back ? rpart[1] + cpart[1] : rpart[1 + ey] + cpart[1 + ex];
+    const int di = back ? OPPd(i) : i;
+    LB_GUARD((unsigned long long)base + 288 + 32 * di, lim, );
+    f[base + 32 * di] = fs[i];
+    f[base + 288 + 32 * di] = ge[i];
+  }
+}
+
 // UROWS: block storage with rows that start inside a block (nx % 32 != 0): the
 // stage columns of a lane change from row to row (a separate instantiation, so
 // that aligned rows keep constant columns and no per-row work).
@@ -423,6 +445,24 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const bool warp_all_tube = __all_sync(0xffffffffu, tc[0] && tc[1] && tc[2]);
   auto solid_row = [&](int y) { return warp_all_tube && !row_in_band(G, wrapi(y, ny)); };
   const uint32_t N32 = (uint32_t)N;
+  // block storage, rows on block boundaries: the column parts of this lane's three
+  // destination columns' block addresses
+  constexpr bool BA = L::BLK && !UROWS;
+  [[maybe_unused]] uint32_t cpart[3] = {0u, 0u, 0u};
+  if constexpr (BA) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) cpart[i] = (uint32_t)(col[i] >> 5) * SF32B::kBlock + (uint32_t)(col[i] & 31);
+  }
+  [[maybe_unused]] const unsigned long long blk_lim = 18ull * ((N + 31) & ~31ull);
+  auto push = [&](const int rowb[3], const bool sol[3][3], bool bnd, const A fs[9], const A ge[9]) {
+    if constexpr (BA) {
+      const uint32_t rpart[3] = {(uint32_t)(rowb[0] >> 5) * SF32B::kBlock, (uint32_t)(rowb[1] >> 5) * SF32B::kBlock,
+                                 (uint32_t)(rowb[2] >> 5) * SF32B::kBlock};
+      push_node_blk<MODEL>(reinterpret_cast<float*>(dst.f), blk_lim, rpart, cpart, sol, bnd, fs, ge);
+    } else {
+      push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, bnd, fs, ge);
+    }
+  };
 
   // rows k-1, k, k+1 of the stencil window
   Row Rw[3];
@@ -494,13 +534,13 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
             for (int i = 0; i < 3; ++i) sol[j][i] = false;
         }
         collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
-        push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, bnd, fs, ge);
+        push(rowb, sol, bnd, fs, ge);
       }
     } else {
       const bool sol[3][3] = {{false, false, false}, {false, false, false}, {false, false, false}};
       if (act) {
         collide_node<MODEL, A>(P, vr, vp, sol, false, fa, fs, ge);
-        push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, false, fs, ge);
+        push(rowb, sol, false, fs, ge);
       }
     }
 #pragma unroll
