@@ -441,23 +441,27 @@ def surrogate_metric(torch, threshold=0.02):
 
 def small_capillary_rates(torch, Lattice, steps=10000):
     """The 2048 x 64 binary FP32 capillary (9.4 MB per state copy, held in L2): the
-    autotuned single-lattice path (replayed 64-step graphs, CUDA events) and one
-    persistent launch of a batch of one (wall clock around the sampled run)."""
-    from paper_0911_0459_gb300 import Batch
+    autotuned single-lattice path (replayed 64-step graphs, CUDA events) in the 32-node
+    block storage and in planes (the same bits), and one persistent launch of a batch of
+    one (wall clock around the sampled run)."""
+    from paper_0911_0459_gb300 import STORAGE_F32, STORAGE_F32_BLOCKED, Batch
     cap = W.config_binary_2048x64()
-    lat = Lattice.from_workload(cap)
-    tx, ty, _ = lat.autotune()
-    lat.step(64)
-    torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(lat.stream)
-    lat.step(steps)
-    b.record(lat.stream)
-    torch.cuda.synchronize()
-    us = 1e3 * a.elapsed_time(b) / steps
-    fluid = lat.fluid_nodes
-    lat.close()
+    rates = {}
+    for key, st in (("blocks", STORAGE_F32_BLOCKED), ("planes", STORAGE_F32)):
+        lat = Lattice.from_workload(cap, storage=st)
+        tx, ty, _ = lat.autotune()
+        lat.step(64)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(lat.stream)
+        lat.step(steps)
+        b.record(lat.stream)
+        torch.cuda.synchronize()
+        rates[key] = (1e3 * a.elapsed_time(b) / steps, [tx, ty], lat.kernel())
+        fluid = lat.fluid_nodes
+        lat.close()
+    us, tile, kern = rates["blocks"]
     bt = Batch([cap])
     btx, bty, _ = bt.autotune(steps=2)
     bt.run_sampled([64])
@@ -466,9 +470,12 @@ def small_capillary_rates(torch, Lattice, steps=10000):
     bt.run_sampled([steps])
     us_p = 1e6 * (time.perf_counter() - t0) / steps
     bt.close()
-    return {"us_per_step": us, "MLUPS": fluid / us, "tile": [tx, ty],
+    return {"us_per_step": us, "MLUPS": fluid / us, "tile": tile, "kernel_variant": kern,
+            "storage": "FP32 in 32-node blocks",
+            "planes_us_per_step": rates["planes"][0], "planes_tile": rates["planes"][1],
             "persistent_us_per_step": us_p, "persistent_MLUPS": fluid / us_p, "persistent_tile": [btx, bty],
-            "what": f"{steps} steps; state in L2, so no HBM fraction is quoted"}
+            "what": f"{steps} steps; state in L2, so no HBM fraction is quoted; the persistent form is "
+                    "a batch of one in planar FP32"}
 
 
 def timed_steps(lat, torch, K, red_every):
