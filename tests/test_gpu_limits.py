@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_0911_0459_gb300 import STORAGE_F32, Batch, Lattice, LbError  # noqa: E402
+from paper_0911_0459_gb300 import STORAGE_F32, STORAGE_F32_BLOCKED, Batch, Lattice, LbError  # noqa: E402
 
 # the staged kernel stores at 32-bit element offsets over 9 planes: 9 nx ny < 2^32
 STAGED_MAX_NODES = (2 ** 32 - 1) // 9
@@ -76,6 +76,31 @@ def test_largest_lattices_of_the_staged_kernel(ny, staged):
     m1 = lat.filled_length()["mass"]
     assert np.isfinite(m1) and abs(m1 / m0 - 1) < 1e-6
     assert abs(m0 / (nx * ny) - cap.params.rho_g) < 1e-6 * cap.params.rho_g
+    lat.close()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("nx", [65536, 65535])
+def test_largest_lattices_of_the_block_storage(nx):
+    """The block storage addresses its state with 32-bit element offsets, 18 * 32 *
+    ceil(N / 32) < 2^32, so at most 238,609,280 nodes: 3640 rows of 65536 (rows on block
+    boundaries) or of 65535 (rows starting inside blocks) fit (about 34 GB for both
+    buffers) and run the staged kernel; one more row is refused at creation.  Two steps of
+    a binary box keep its mass and its phi sum to FP32 rounding."""
+    ny = 3640
+    p = W.binary_params(storage=STORAGE_F32_BLOCKED)
+    assert 18 * 32 * ((nx * ny + 31) // 32) < 2 ** 32 <= 18 * 32 * ((nx * (ny + 1) + 31) // 32)
+    with pytest.raises(LbError):
+        Lattice.from_workload(W.periodic_box(nx, ny + 1, p))
+    lat = Lattice.from_workload(W.periodic_box(nx, ny, p))
+    assert lat.kernel() == 2
+    d0 = lat.filled_length()
+    lat.step(2)
+    torch.cuda.synchronize()
+    d1 = lat.filled_length()
+    assert np.isfinite([d1["mass"], d1["phi_sum"]]).all()
+    assert abs(d1["mass"] / d0["mass"] - 1) < 1e-6
+    assert abs(d1["phi_sum"] - d0["phi_sum"]) < 1e-6 * nx * ny
     lat.close()
     torch.cuda.empty_cache()
 
