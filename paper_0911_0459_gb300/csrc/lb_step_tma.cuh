@@ -8,8 +8,9 @@
 //     side) into a shared-memory ring of NS stages with cp.async.bulk copies,
 //     signalled on a per-stage "full" mbarrier (complete_tx).  The planar
 //     storages take one copy per plane and row; the 32-node block storage
-//     (SF32B) one copy per row, of whole blocks with one halo block either
-//     side: a CTA's bulk copies, not their bytes, limited the planar ring;
+//     (SF32B) one copy per row, of the whole blocks over the tile's nodes and
+//     their neighbour columns: a CTA's bulk copies, not their bytes, limited
+//     the planar ring;
 //   - BX/32 consumer warps work independently: each keeps rho/phi of rows
 //     y-1, y, y+1 for its 32 columns in registers, takes the neighbouring
 //     columns by warp shuffles (its edge lanes sum the halo columns from the
@@ -25,11 +26,11 @@
 //   - a row that is solid under every column a warp reads (inside the tube,
 //     outside the band) is not summed: the wall ghosts replace all its values;
 //     a tile whose nodes are all solid exits at once.
-// Requires nx % 8 == 0 (16-byte aligned rows for every storage type; the block
-// storage needs nx % 32 == 0), 9 nx ny < 2^32 (32-bit offsets; 18 nx ny for the
-// block storage) and BX % 32 == 0.  Halo columns at the x-wrap come from a second
-// 16-byte-aligned copy of the 8 elements (the block storage: the 32-node block)
-// at the other end of the row.
+// Requires, for the planar storages, nx % 8 == 0 (16-byte aligned rows) and
+// 9 nx ny < 2^32 (32-bit offsets); the block storage takes any nx with
+// 18 * 32 * ceil(nx ny / 32) < 2^32.  BX % 32 == 0.  Halo columns at the x-wrap
+// come from a second 16-byte-aligned copy of the 8 elements (the block storage:
+// the 32-node block) at the other end of the row.
 //
 // Every mbarrier wait gives up after a time limit and records the failure in
 // the error word; the producer waits (also with a limit) for the copies it
