@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(BatchArgs<S> a) {
       const CapDesc<typename S::A> c = a.caps[td.cap];
       const Buf<S> src = fromA ? cap_buf<S>(a.fa, a.ga, a.g0a, c) : cap_buf<S>(a.fb, a.gb, a.g0b, c);
       const Buf<S> dst = fromA ? cap_buf<S>(a.fb, a.gb, a.g0b, c) : cap_buf<S>(a.fa, a.ga, a.g0a, c);
-      step_band<MODEL_BINARY, S, BX, true>(c.G, c.P, src, dst, td.xb, td.y0, td.y1, sm);
+      step_band<MODEL_BINARY, S, BX, true>(c.G, c.P, c.Q, src, dst, td.xb, td.y0, td.y1, sm);
       __syncthreads();
     }
     if (!grid_barrier(a.bar, a.expected, a.limit_ns)) {
@@ -191,10 +191,10 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_ker
           const Phys<typename S::A> P = c.P;
           if constexpr (TmaLayout<MODEL_BINARY, S, BX, NS>::BLK) {
             ok = c.G.nx % 32 != 0
-                     ? consume_tile<MODEL_BINARY, S, BX, NS, true>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane)
-                     : consume_tile<MODEL_BINARY, S, BX, NS, false>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+                     ? consume_tile<MODEL_BINARY, S, BX, NS, true>(R, c.G, P, c.Q, dst, td.xb, td.y0, td.y1, k, warp, lane)
+                     : consume_tile<MODEL_BINARY, S, BX, NS, false>(R, c.G, P, c.Q, dst, td.xb, td.y0, td.y1, k, warp, lane);
           } else {
-            ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, P, dst, td.xb, td.y0, td.y1, k, warp, lane);
+            ok = consume_tile<MODEL_BINARY, S, BX, NS>(R, c.G, P, c.Q, dst, td.xb, td.y0, td.y1, k, warp, lane);
           }
         }
       }

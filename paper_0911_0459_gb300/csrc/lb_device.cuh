@@ -248,6 +248,25 @@ struct SF16 {
     else
       g[(i - 1) * N + n] = __float2half_rn(v);
   }
+  // the stored deviations f_i - w_i themselves (the population kernels compute in
+  // deviations for this storage)
+  __device__ static A pfr(const T* f, int W, int c, int i) { return __half2float(f[i * W + c]); }
+  __device__ static A lfr(const T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
+    return __half2float(__ldg(f + i * N + n));
+  }
+  __device__ static A lfcr(const T* f, size_t N, size_t n, int i) {
+    LB_GUARD(i * N + n, 9 * N, A(0));
+    return __half2float(__ldcg(f + i * N + n));
+  }
+  __device__ static void sfr(T* __restrict__ f, size_t N, size_t n, int i, A v) {
+    LB_GUARD(i * N + n, 9 * N, );
+    f[i * N + n] = __float2half_rn(v);
+  }
+  __device__ static void sfor(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) {
+    LB_GUARD((unsigned long long)i * N + n, 9ull * N, );
+    f[i * N + n] = __float2half_rn(v);
+  }
   __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
     LB_GUARD(i * N + n, 9 * N, );
     f[i * N + n] = __float2half_rn(0.0f);
@@ -311,6 +330,13 @@ struct SF32B {
     LB_GUARD(at(n, i), lim(N), );
     f[at(n, i)] = 0.0f;
   }
+};
+
+// Population storages whose step kernels compute in deviations from the stored
+// rest offsets (the FP16 storage): raw loads and stores, collide_node_f16.
+template <class S>
+struct dev_arith {
+  static constexpr bool value = std::is_same<S, SF16>::value;
 };
 
 template <class S>
@@ -493,6 +519,164 @@ __host__ __device__ constexpr int OPPd(int i) { return i == 0 ? 0 : ((i & 1) ? i
 __device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double rcp_rn(double v) { return 1.0 / v; }
 
+// Hardware reciprocal (relative error below 2^-22), for 1/rho and omega.
+__device__ __forceinline__ float rcp_fast(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+// ---------------------------------------------------------------- collision
+
+// Constants of the collision, with the stencils' normalisations folded in: the
+// gradient stencils enter as 12 x the gradient and the Laplacian as 6 x the
+// Laplacian (see stencil_rows).
+struct MomPhys {
+  float A;          // phi^4 coefficient (Sec. 3.1)
+  float nkap6;      // -kappa / 6: -kappa lap = nkap6 (6 lap)
+  float kap144;     // kappa / 144: kappa (d phi)^2 = kap144 (12 d phi)^2
+  float lam12;      // lambda_scale / 12: lambda u . d rho = (lam12 nu) u . (12 d rho)
+  float nu_g, dnu;  // Eq. (nu): nu = nu_g + c (nu_l - nu_g)
+  float M3, M12;    // 2M/3 and 2M/12, g^eq's mobility terms (App. A)
+  float h;          // wall gradient d_n phi|_b
+  float lut, lut_inv;
+  float p0off;      // -A / 4: P0 of the FP16 deviation storage's rest offsets (P0 = 1/3 + A/4) less 1/3
+};
+
+inline MomPhys mom_phys(double kappa, double A, double M, double nu_l, double nu_g, double lambda_scale, double h,
+                        double lut) {
+  MomPhys q;
+  q.A = float(A);
+  q.nkap6 = float(-kappa / 6.0);
+  q.kap144 = float(kappa / 144.0);
+  q.lam12 = float(lambda_scale / 12.0);
+  q.nu_g = float(nu_g);
+  q.dnu = float(nu_l - nu_g);
+  q.M3 = float(2.0 * M / 3.0);
+  q.M12 = float(2.0 * M / 12.0);
+  q.h = float(h);
+  q.lut = float(lut);
+  q.lut_inv = lut > 0 ? float(1.0 / lut) : 0.f;
+  q.p0off = float(-0.25 * A);
+  return q;
+}
+
+// Gradient and Laplacian stencils of Eq. (best) at one node, from per-row
+// summaries of the 3x3 neighbourhood: c (centre), s = right - left and
+// d = (left - c) + (right - c) of rows y-1 (0), y (1), y+1 (2), formed once per
+// row.  The sums of Eq. (best) regrouped into differences of neighbouring
+// values:
+//   12 dx = 4 s1 + s0 + s2,  12 dy = 6 (c2 - c0) + (d2 - d0),
+//   6 lap = 6 ((c0 - c1) + (c2 - c1)) + (4 d1 + d0 + d2).
+// Neighbouring values are close, so those differences are exact in floating
+// point and no large partial sums cancel (in a nearly uniform phase the direct
+// sums of about twenty times the field value would leave a rounding error of
+// fixed sign).  Returned unnormalised; the collision's constants carry the
+// factors 1/12 and 1/6.
+__device__ __forceinline__ void stencil_rows(const float c[3], const float sv[3], const float d[3], float& dx12,
+                                             float& dy12, float& lap6) {
+  dx12 = fmaf(4.f, sv[1], sv[0]) + sv[2];
+  dy12 = fmaf(6.f, c[2] - c[0], d[2] - d[0]);
+  lap6 = fmaf(6.f, (c[0] - c[1]) + (c[2] - c[1]), fmaf(4.f, d[1], d[0] + d[2]));
+}
+__device__ __forceinline__ void grad_rows(const float c[3], const float sv[3], const float d[3], float& dx12,
+                                          float& dy12) {
+  dx12 = fmaf(4.f, sv[1], sv[0]) + sv[2];
+  dy12 = fmaf(6.f, c[2] - c[0], d[2] - d[0]);
+}
+
+// Eq. (best) on an explicit 3x3 neighbourhood (boundary nodes, after the wall
+// ghosts), unnormalised as above.
+__device__ __forceinline__ void stencil3_unnorm(const float v[3][3], float& dx12, float& dy12, float& lap6) {
+  dx12 = fmaf(4.f, v[1][2] - v[1][0], v[0][2] - v[0][0]) + (v[2][2] - v[2][0]);
+  dy12 = fmaf(4.f, v[2][1], v[2][0] + v[2][2]) - fmaf(4.f, v[0][1], v[0][0] + v[0][2]);
+  lap6 = fmaf(-20.f, v[1][1], fmaf(4.f, (v[0][1] + v[1][0]) + (v[1][2] + v[2][1]),
+                                   (v[0][0] + v[0][2]) + (v[2][0] + v[2][2])));
+}
+
+// Post-collision f (fs_i = f*_i - w_i) and g (ge = g^eq) of one node from its
+// moments and the unnormalised stencils: Eq. (equilibrium) for f^eq with the
+// binary pressure of Sec. 3.1, g^eq of App. A, and the collision with every
+// mode but pxx - pyy and pxy relaxed fully.
+//
+// With T = (Txx, Tyy, Txy) the second moment of f^eq beyond the pressure (the
+// rho u u and lambda terms of Eq. (equilibrium)) and G = kappa (dphi dphi) its
+// gradient terms, the even part of each pair of opposite directions, less w_i, is
+//   A1 = (P0 + Uxx - Uyy / 2) / 3 + dxx,   A3 = (P0 + Uyy - Uxx / 2) / 3 - dxx,
+//   A5 = (P0 + V + 3 (Txy + Gxy)) / 12 + dxy,  A7 = (P0 + V - 3 (Txy + Gxy)) / 12 - dxy,
+// with U = T + G, V = (Txx + Tyy) - (Gxx + Gyy) / 2, P0 the pressure less 1/3,
+// and dxx, dxy the stress non-equilibria relaxed at omega, (1 - omega)/4 times
+// (m - m^eq).  The odd parts are the momenta j/3 and j/12.
+//
+// F16OFF: the populations are deviations from the FP16 storage's rest offsets
+// w_i(P0b), P0b = 1/3 + A/4 (SF16), not from 4/9, 1/9, 1/36: the pressure term
+// carries Q.p0off = -A/4, which moves each pair's even part by w_i(1/3) - w_i(P0b)
+// (A/12, A/48) and the rest population by the opposite sum (5A/12).
+template <bool F16OFF = false>
+__device__ __forceinline__ void collide_moment_node(const MomPhys& Q, float drho, float jx, float jy, float mxx,
+                                                    float mxy, float phi, float rdx, float rdy, float pdx,
+                                                    float pdy, float plap, float fs[9], float ge[9]) {
+  // Every product that feeds a sum is an explicit fused multiply-add and every
+  // other product an explicit __fmul_rn, so the compiler fuses nothing on its
+  // own and every kernel that inlines this function rounds a node alike.
+  const float inv = rcp_fast(1.f + drho);
+  const float ux = __fmul_rn(jx, inv), uy = __fmul_rn(jy, inv);
+  const float phi2 = __fmul_rn(phi, phi);
+  // chemical potential (Eq. chempot): A (phi^3 - phi) - kappa lap phi
+  const float mu = fmaf(Q.nkap6, plap, __fmul_rn(Q.A, fmaf(phi2, phi, -phi)));
+  // viscosity (Eq. nu, the liquid fraction clamped) and c = (1 - omega) / 4
+  float cl = __saturatef(fmaf(phi, 0.5f, 0.5f));
+  if (Q.lut > 0.f) cl = __fmul_rn(rintf(__fmul_rn(cl, Q.lut)), Q.lut_inv);  // viscosity table of App. A
+  const float nu = fmaf(cl, Q.dnu, Q.nu_g);
+  const float r = rcp_fast(fmaf(6.f, nu, 1.f));  // omega / 2
+  const float c = fmaf(-0.5f, r, 0.25f);
+  const float lam = __fmul_rn(Q.lam12, nu);
+  // P0 - 1/3: p0 = rho/3 + A (-phi^2/2 + 3 phi^4/4) less kappa phi lap phi
+  const float P0r = fmaf(__fmul_rn(Q.nkap6, phi), plap,
+                         fmaf(drho, 1.f / 3.f, __fmul_rn(__fmul_rn(Q.A, phi2), fmaf(0.75f, phi2, -0.5f))));
+  const float P0 = F16OFF ? P0r + Q.p0off : P0r;
+  // second moment of f^eq beyond P0: T (rho u u and the lambda terms) and the
+  // gradient terms G = kappa (dphi dphi), with U = T + G
+  const float ax = __fmul_rn(ux, rdx), ay = __fmul_rn(uy, rdy);
+  const float udr = ax + ay;
+  const float Txx = fmaf(jx, ux, __fmul_rn(lam, fmaf(2.f, ax, udr)));
+  const float Tyy = fmaf(jy, uy, __fmul_rn(lam, fmaf(2.f, ay, udr)));
+  const float Txy = fmaf(jx, uy, __fmul_rn(lam, fmaf(ux, rdy, __fmul_rn(uy, rdx))));
+  const float kx = __fmul_rn(Q.kap144, pdx), ky = __fmul_rn(Q.kap144, pdy);
+  const float Uxx = fmaf(kx, pdx, Txx), Uyy = fmaf(ky, pdy, Tyy);
+  const float GS = fmaf(kx, pdx, __fmul_rn(ky, pdy));   // Gxx + Gyy
+  const float V = fmaf(-0.5f, GS, Txx + Tyy);
+  const float TG = fmaf(kx, pdy, Txy);                  // Txy + Gxy
+  const float dxx = __fmul_rn(c, mxx - (Uxx - Uyy));
+  const float dxy = __fmul_rn(c, mxy - TG);
+  const float A1 = fmaf(P0 + fmaf(-0.5f, Uyy, Uxx), 1.f / 3.f, dxx);
+  const float A3 = fmaf(P0 + fmaf(-0.5f, Uxx, Uyy), 1.f / 3.f, -dxx);
+  const float W3 = __fmul_rn(3.f, TG);
+  const float A5 = fmaf(P0 + (V + W3), 1.f / 12.f, dxy);
+  const float A7 = fmaf(P0 + (V - W3), 1.f / 12.f, -dxy);
+  const float jp = jx + jy, jm = jy - jx;
+  fs[1] = fmaf(jx, 1.f / 3.f, A1); fs[2] = fmaf(jx, -1.f / 3.f, A1);
+  fs[3] = fmaf(jy, 1.f / 3.f, A3); fs[4] = fmaf(jy, -1.f / 3.f, A3);
+  fs[5] = fmaf(jp, 1.f / 12.f, A5); fs[6] = fmaf(jp, -1.f / 12.f, A5);
+  fs[7] = fmaf(jm, 1.f / 12.f, A7); fs[8] = fmaf(jm, -1.f / 12.f, A7);
+  fs[0] = fmaf(-2.f, (A1 + A3) + (A5 + A7), drho);
+  // g^eq (App. A, dt = 1)
+  const float Q3 = __fmul_rn(Q.M3, mu), Q12 = __fmul_rn(Q.M12, mu);
+  const float nu2 = __fmul_rn(fmaf(ux, ux, __fmul_rn(uy, uy)), -1.f / 3.f);  // -u.u / 3
+  const float hp = __fmul_rn(0.5f, phi), hq = __fmul_rn(0.125f, phi);
+  const float upp = ux + uy, ump = ux - uy;
+  const float B1 = fmaf(hp, fmaf(ux, ux, nu2), Q3);
+  const float B3 = fmaf(hp, fmaf(uy, uy, nu2), Q3);
+  const float B5 = fmaf(hq, fmaf(upp, upp, nu2), Q12);
+  const float B7 = fmaf(hq, fmaf(ump, ump, nu2), Q12);
+  const float p3 = __fmul_rn(phi, 1.f / 3.f), p12 = __fmul_rn(phi, 1.f / 12.f);
+  ge[1] = fmaf(p3, ux, B1); ge[2] = fmaf(-p3, ux, B1);
+  ge[3] = fmaf(p3, uy, B3); ge[4] = fmaf(-p3, uy, B3);
+  ge[5] = fmaf(p12, upp, B5); ge[6] = fmaf(-p12, upp, B5);
+  ge[7] = fmaf(-p12, ump, B7); ge[8] = fmaf(p12, ump, B7);
+  ge[0] = fmaf(-2.f, (B1 + B3) + (B5 + B7), phi);
+}
+
 // The FP64 collision in pair form (the same update as collide_node's FP32 path
 // in exact arithmetic, with fewer operations on the FP64 pipe, which bounds the
 // FP64 storages).  The equilibrium of Eq. (equilibrium) gives each pair of
@@ -632,7 +816,34 @@ __device__ __forceinline__ void collide_node(const Phys<A>& P, A vr[3][3], A vp[
 
 // Push streaming from node (col[1], row yy) with bounce-back into solid
 // neighbours.  rowb: y*nx of rows y-1, y, y+1 (wrapped); col: x-1, x, x+1.
-template <int MODEL, class S>
+// Per-node update of the FP16 deviation storage (binary model), in deviations:
+// vr holds rho - 1 (the sums of the stored deviations f_i - w_i, whose offsets add
+// up to 1), fa the node's deviations; fs returns post-collision deviations from
+// the same offsets, ge g^eq.  The wall ghosts and the rest rule as in
+// collide_node (the rest rule acts on j, to which the offsets add nothing), then
+// the pair-form collision of the moment kernel with its pressure shifted to the
+// offsets' P0 (the same update in exact arithmetic, without adding and removing
+// the offsets at every load and store).
+template <int MODEL>
+__device__ __forceinline__ void collide_node_f16(const MomPhys& Q, float vr[3][3], float vp[3][3],
+                                                 const bool sol[3][3], bool bnd, float fa[9], float fs[9],
+                                                 float ge[9]) {
+  static_assert(MODEL == MODEL_BINARY, "the FP16 deviation storage holds the binary model");
+  if (bnd) {
+    apply_ghosts(vr, sol, 0.f);
+    apply_ghosts(vp, sol, Q.h);
+    rest(fa);
+  }
+  float rdx, rdy, rlap, pdx, pdy, plap;
+  stencil3_unnorm(vr, rdx, rdy, rlap);
+  stencil3_unnorm(vp, pdx, pdy, plap);
+  const float mxx = (fa[1] + fa[2]) - (fa[3] + fa[4]);
+  const float mxy = (fa[5] + fa[6]) - (fa[7] + fa[8]);
+  collide_moment_node<true>(Q, vr[1][1], momx(fa), momy(fa), mxx, mxy, vp[1][1], rdx, rdy, pdx, pdy, plap, fs, ge);
+}
+
+// RAW: store f as the storage's raw values (the deviations of dev_arith storages).
+template <int MODEL, class S, bool RAW = false>
 __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int rowb[3], const int col[3],
                                           const bool sol[3][3], bool bnd, const typename S::A fs[9],
                                           const typename S::A ge[9]) {
@@ -641,7 +852,10 @@ __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int dn = rowb[1 + EYd(i)] + col[1 + EXd(i)];
-      S::sf(dst.f, N, (size_t)dn, i, fs[i], dst.r);
+      if constexpr (RAW)
+        S::sfr(dst.f, N, (size_t)dn, i, fs[i]);
+      else
+        S::sf(dst.f, N, (size_t)dn, i, fs[i], dst.r);
       if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, i, ge[i]);
     }
   } else {
@@ -652,7 +866,10 @@ __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int
       const bool back = sol[1 + ey][1 + ex];
       const int dn = back ? self : rowb[1 + ey] + col[1 + ex];
       const int di = back ? OPPd(i) : i;
-      S::sf(dst.f, N, (size_t)dn, di, fs[i], dst.r);
+      if constexpr (RAW)
+        S::sfr(dst.f, N, (size_t)dn, di, fs[i]);
+      else
+        S::sf(dst.f, N, (size_t)dn, di, fs[i], dst.r);
       if (BIN) S::sg(dst.g, dst.g0, N, (size_t)dn, di, ge[i]);
     }
   }
@@ -661,7 +878,7 @@ __device__ __forceinline__ void push_node(const Buf<S>& dst, size_t N, const int
 // push_node with 32-bit element offsets from the buffer bases (the staged
 // kernels; the host admits them only for lattices with 9 N < 2^32 nodes).
 // rowb/col as in push_node.
-template <int MODEL, class S>
+template <int MODEL, class S, bool RAW = false>
 __device__ __forceinline__ void push_node_u32(const Buf<S>& dst, uint32_t N, const int rowb[3], const int col[3],
                                               const bool sol[3][3], bool bnd, const typename S::A fs[9],
                                               const typename S::A ge[9]) {
@@ -670,7 +887,10 @@ __device__ __forceinline__ void push_node_u32(const Buf<S>& dst, uint32_t N, con
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const uint32_t dn = (uint32_t)(rowb[1 + EYd(i)] + col[1 + EXd(i)]);
-      S::sfo(dst.f, N, dn, i, fs[i], dst.r);
+      if constexpr (RAW)
+        S::sfor(dst.f, N, dn, i, fs[i]);
+      else
+        S::sfo(dst.f, N, dn, i, fs[i], dst.r);
       if (BIN) S::sgo(dst.g, dst.g0, N, dn, i, ge[i]);
     }
   } else {
@@ -681,7 +901,10 @@ __device__ __forceinline__ void push_node_u32(const Buf<S>& dst, uint32_t N, con
       const bool back = sol[1 + ey][1 + ex];
       const uint32_t dn = back ? self : (uint32_t)(rowb[1 + ey] + col[1 + ex]);
       const int di = back ? OPPd(i) : i;
-      S::sfo(dst.f, N, dn, di, fs[i], dst.r);
+      if constexpr (RAW)
+        S::sfor(dst.f, N, dn, di, fs[i]);
+      else
+        S::sfo(dst.f, N, dn, di, fs[i], dst.r);
       if (BIN) S::sgo(dst.g, dst.g0, N, dn, di, ge[i]);
     }
   }
@@ -693,6 +916,7 @@ template <int MODEL, class S>
 struct StepArgs {
   Geom G;
   Phys<typename S::A> P;
+  MomPhys Q;  // the pair-form constants (storages that compute in deviations)
   Buf<S> src, dst;
   int yc;  // rows per CTA band
 };
@@ -703,11 +927,16 @@ struct StepSmem {
   typename S::A p[MODEL == MODEL_BINARY ? 4 : 1][BX + 2];
 };
 
-template <int MODEL, class S, bool COHERENT = false>
+template <int MODEL, class S, bool COHERENT = false, bool RAW = false>
 __device__ __forceinline__ void load_node(const Buf<S>& B, size_t N, size_t n, typename S::A f[9],
                                           typename S::A g[9]) {
 #pragma unroll
-  for (int i = 0; i < 9; ++i) f[i] = COHERENT ? S::lfc(B.f, N, n, i, B.r) : S::lf(B.f, N, n, i, B.r);
+  for (int i = 0; i < 9; ++i) {
+    if constexpr (RAW)
+      f[i] = COHERENT ? S::lfcr(B.f, N, n, i) : S::lfr(B.f, N, n, i);
+    else
+      f[i] = COHERENT ? S::lfc(B.f, N, n, i, B.r) : S::lf(B.f, N, n, i, B.r);
+  }
   if (MODEL == MODEL_BINARY) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) g[i] = COHERENT ? S::lgc(B.g, B.g0, N, n, i) : S::lg(B.g, B.g0, N, n, i);
@@ -718,11 +947,12 @@ __device__ __forceinline__ void load_node(const Buf<S>& B, size_t N, size_t n, t
 // COHERENT loads bypass the non-coherent read path (buffers written earlier in
 // the same launch, as in the persistent batched kernel).
 template <int MODEL, class S, int BX, bool COHERENT = false>
-__device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::A>& P, const Buf<S>& src,
-                                          const Buf<S>& dst, int xb, int y0, int y1,
+__device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::A>& P, const MomPhys& Q,
+                                          const Buf<S>& src, const Buf<S>& dst, int xb, int y0, int y1,
                                           StepSmem<MODEL, S, BX>& sm) {
   using A = typename S::A;
   constexpr bool BIN = MODEL == MODEL_BINARY;
+  constexpr bool RAW = dev_arith<S>::value;
   const int nx = G.nx, ny = G.ny;
   const size_t N = (size_t)nx * ny;
   const int tid = threadIdx.x;
@@ -753,9 +983,9 @@ __device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::
   auto fetch = [&](int r, A* f, A* g, bool& fluid, bool& hfluid) {
     const int rr = wrapi(r, ny);
     fluid = act && !is_solid(G, x, rr);
-    if (fluid) load_node<MODEL, S, COHERENT>(src, N, (size_t)rr * nx + x, f, g);
+    if (fluid) load_node<MODEL, S, COHERENT, RAW>(src, N, (size_t)rr * nx + x, f, g);
     hfluid = hal && !is_solid(G, hx, rr);
-    if (hfluid) load_node<MODEL, S, COHERENT>(src, N, (size_t)rr * nx + hx, hf, hg);
+    if (hfluid) load_node<MODEL, S, COHERENT, RAW>(src, N, (size_t)rr * nx + hx, hf, hg);
   };
 
   bool fl_a, fl_b, fl_c, hfl;
@@ -788,10 +1018,13 @@ __device__ __forceinline__ void step_band(const Geom& G, const Phys<typename S::
           if (BIN) vp[j][i] = sm.p[slot(y - 1 + j)][tid + i];
         }
       A fs[9], ge[9];
-      collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
+      if constexpr (RAW)
+        collide_node_f16<MODEL>(Q, vr, vp, sol, bnd, fa, fs, ge);
+      else
+        collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
       const int rowb[3] = {wrapi(yy - 1, ny) * nx, yy * nx, wrapi(yy + 1, ny) * nx};
       const int col[3] = {wrapi(x - 1, nx), x, wrapi(x + 1, nx)};
-      push_node<MODEL, S>(dst, N, rowb, col, sol, bnd, fs, ge);
+      push_node<MODEL, S, RAW>(dst, N, rowb, col, sol, bnd, fs, ge);
     }
 
     if (more) publish(y + 2, fc, gc, fl_c, hf, hg, hfl);
@@ -818,7 +1051,7 @@ __global__ void __launch_bounds__(BX) step_kernel(StepArgs<MODEL, S> a) {
   const int xb = cb * BX;
   const int y0 = band * a.yc;
   const int y1 = min(y0 + a.yc, a.G.ny);
-  step_band<MODEL, S, BX>(a.G, a.P, a.src, a.dst, xb, y0, y1, sm);
+  step_band<MODEL, S, BX>(a.G, a.P, a.Q, a.src, a.dst, xb, y0, y1, sm);
 }
 
 }  // namespace lbk

@@ -229,155 +229,6 @@ __device__ __forceinline__ float2 pull_rho_phi(const void* base, size_t N, size_
 __host__ __device__ constexpr int SXXd(int i) { return (i == 1 || i == 2) ? 1 : ((i == 3 || i == 4) ? -1 : 0); }
 __host__ __device__ constexpr int SXYd(int i) { return (i == 5 || i == 6) ? 1 : ((i == 7 || i == 8) ? -1 : 0); }
 
-// Hardware reciprocal (relative error below 2^-22), for 1/rho and omega.
-__device__ __forceinline__ float rcp_fast(float v) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-
-// ---------------------------------------------------------------- collision
-
-// Constants of the collision, with the stencils' normalisations folded in: the
-// gradient stencils enter as 12 x the gradient and the Laplacian as 6 x the
-// Laplacian (see stencil_rows).
-struct MomPhys {
-  float A;          // phi^4 coefficient (Sec. 3.1)
-  float nkap6;      // -kappa / 6: -kappa lap = nkap6 (6 lap)
-  float kap144;     // kappa / 144: kappa (d phi)^2 = kap144 (12 d phi)^2
-  float lam12;      // lambda_scale / 12: lambda u . d rho = (lam12 nu) u . (12 d rho)
-  float nu_g, dnu;  // Eq. (nu): nu = nu_g + c (nu_l - nu_g)
-  float M3, M12;    // 2M/3 and 2M/12, g^eq's mobility terms (App. A)
-  float h;          // wall gradient d_n phi|_b
-  float lut, lut_inv;
-};
-
-inline MomPhys mom_phys(double kappa, double A, double M, double nu_l, double nu_g, double lambda_scale, double h,
-                        double lut) {
-  MomPhys q;
-  q.A = float(A);
-  q.nkap6 = float(-kappa / 6.0);
-  q.kap144 = float(kappa / 144.0);
-  q.lam12 = float(lambda_scale / 12.0);
-  q.nu_g = float(nu_g);
-  q.dnu = float(nu_l - nu_g);
-  q.M3 = float(2.0 * M / 3.0);
-  q.M12 = float(2.0 * M / 12.0);
-  q.h = float(h);
-  q.lut = float(lut);
-  q.lut_inv = lut > 0 ? float(1.0 / lut) : 0.f;
-  return q;
-}
-
-// Gradient and Laplacian stencils of Eq. (best) at one node, from per-row
-// summaries of the 3x3 neighbourhood: c (centre), s = right - left and
-// d = (left - c) + (right - c) of rows y-1 (0), y (1), y+1 (2), formed once per
-// row.  The sums of Eq. (best) regrouped into differences of neighbouring
-// values:
-//   12 dx = 4 s1 + s0 + s2,  12 dy = 6 (c2 - c0) + (d2 - d0),
-//   6 lap = 6 ((c0 - c1) + (c2 - c1)) + (4 d1 + d0 + d2).
-// Neighbouring values are close, so those differences are exact in floating
-// point and no large partial sums cancel (in a nearly uniform phase the direct
-// sums of about twenty times the field value would leave a rounding error of
-// fixed sign).  Returned unnormalised; the collision's constants carry the
-// factors 1/12 and 1/6.
-__device__ __forceinline__ void stencil_rows(const float c[3], const float sv[3], const float d[3], float& dx12,
-                                             float& dy12, float& lap6) {
-  dx12 = fmaf(4.f, sv[1], sv[0]) + sv[2];
-  dy12 = fmaf(6.f, c[2] - c[0], d[2] - d[0]);
-  lap6 = fmaf(6.f, (c[0] - c[1]) + (c[2] - c[1]), fmaf(4.f, d[1], d[0] + d[2]));
-}
-__device__ __forceinline__ void grad_rows(const float c[3], const float sv[3], const float d[3], float& dx12,
-                                          float& dy12) {
-  dx12 = fmaf(4.f, sv[1], sv[0]) + sv[2];
-  dy12 = fmaf(6.f, c[2] - c[0], d[2] - d[0]);
-}
-
-// Eq. (best) on an explicit 3x3 neighbourhood (boundary nodes, after the wall
-// ghosts), unnormalised as above.
-__device__ __forceinline__ void stencil3_unnorm(const float v[3][3], float& dx12, float& dy12, float& lap6) {
-  dx12 = fmaf(4.f, v[1][2] - v[1][0], v[0][2] - v[0][0]) + (v[2][2] - v[2][0]);
-  dy12 = fmaf(4.f, v[2][1], v[2][0] + v[2][2]) - fmaf(4.f, v[0][1], v[0][0] + v[0][2]);
-  lap6 = fmaf(-20.f, v[1][1], fmaf(4.f, (v[0][1] + v[1][0]) + (v[1][2] + v[2][1]),
-                                   (v[0][0] + v[0][2]) + (v[2][0] + v[2][2])));
-}
-
-// Post-collision f (fs_i = f*_i - w_i) and g (ge = g^eq) of one node from its
-// moments and the unnormalised stencils: Eq. (equilibrium) for f^eq with the
-// binary pressure of Sec. 3.1, g^eq of App. A, and the collision with every
-// mode but pxx - pyy and pxy relaxed fully.
-//
-// With T = (Txx, Tyy, Txy) the second moment of f^eq beyond the pressure (the
-// rho u u and lambda terms of Eq. (equilibrium)) and G = kappa (dphi dphi) its
-// gradient terms, the even part of each pair of opposite directions, less w_i, is
-//   A1 = (P0 + Uxx - Uyy / 2) / 3 + dxx,   A3 = (P0 + Uyy - Uxx / 2) / 3 - dxx,
-//   A5 = (P0 + V + 3 (Txy + Gxy)) / 12 + dxy,  A7 = (P0 + V - 3 (Txy + Gxy)) / 12 - dxy,
-// with U = T + G, V = (Txx + Tyy) - (Gxx + Gyy) / 2, P0 the pressure less 1/3,
-// and dxx, dxy the stress non-equilibria relaxed at omega, (1 - omega)/4 times
-// (m - m^eq).  The odd parts are the momenta j/3 and j/12.
-__device__ __forceinline__ void collide_moment_node(const MomPhys& Q, float drho, float jx, float jy, float mxx,
-                                                    float mxy, float phi, float rdx, float rdy, float pdx,
-                                                    float pdy, float plap, float fs[9], float ge[9]) {
-  // Every product that feeds a sum is an explicit fused multiply-add and every
-  // other product an explicit __fmul_rn, so the compiler fuses nothing on its
-  // own and every kernel that inlines this function rounds a node alike.
-  const float inv = rcp_fast(1.f + drho);
-  const float ux = __fmul_rn(jx, inv), uy = __fmul_rn(jy, inv);
-  const float phi2 = __fmul_rn(phi, phi);
-  // chemical potential (Eq. chempot): A (phi^3 - phi) - kappa lap phi
-  const float mu = fmaf(Q.nkap6, plap, __fmul_rn(Q.A, fmaf(phi2, phi, -phi)));
-  // viscosity (Eq. nu, the liquid fraction clamped) and c = (1 - omega) / 4
-  float cl = __saturatef(fmaf(phi, 0.5f, 0.5f));
-  if (Q.lut > 0.f) cl = __fmul_rn(rintf(__fmul_rn(cl, Q.lut)), Q.lut_inv);  // viscosity table of App. A
-  const float nu = fmaf(cl, Q.dnu, Q.nu_g);
-  const float r = rcp_fast(fmaf(6.f, nu, 1.f));  // omega / 2
-  const float c = fmaf(-0.5f, r, 0.25f);
-  const float lam = __fmul_rn(Q.lam12, nu);
-  // P0 - 1/3: p0 = rho/3 + A (-phi^2/2 + 3 phi^4/4) less kappa phi lap phi
-  const float P0 = fmaf(__fmul_rn(Q.nkap6, phi), plap,
-                        fmaf(drho, 1.f / 3.f, __fmul_rn(__fmul_rn(Q.A, phi2), fmaf(0.75f, phi2, -0.5f))));
-  // second moment of f^eq beyond P0: T (rho u u and the lambda terms) and the
-  // gradient terms G = kappa (dphi dphi), with U = T + G
-  const float ax = __fmul_rn(ux, rdx), ay = __fmul_rn(uy, rdy);
-  const float udr = ax + ay;
-  const float Txx = fmaf(jx, ux, __fmul_rn(lam, fmaf(2.f, ax, udr)));
-  const float Tyy = fmaf(jy, uy, __fmul_rn(lam, fmaf(2.f, ay, udr)));
-  const float Txy = fmaf(jx, uy, __fmul_rn(lam, fmaf(ux, rdy, __fmul_rn(uy, rdx))));
-  const float kx = __fmul_rn(Q.kap144, pdx), ky = __fmul_rn(Q.kap144, pdy);
-  const float Uxx = fmaf(kx, pdx, Txx), Uyy = fmaf(ky, pdy, Tyy);
-  const float GS = fmaf(kx, pdx, __fmul_rn(ky, pdy));   // Gxx + Gyy
-  const float V = fmaf(-0.5f, GS, Txx + Tyy);
-  const float TG = fmaf(kx, pdy, Txy);                  // Txy + Gxy
-  const float dxx = __fmul_rn(c, mxx - (Uxx - Uyy));
-  const float dxy = __fmul_rn(c, mxy - TG);
-  const float A1 = fmaf(P0 + fmaf(-0.5f, Uyy, Uxx), 1.f / 3.f, dxx);
-  const float A3 = fmaf(P0 + fmaf(-0.5f, Uxx, Uyy), 1.f / 3.f, -dxx);
-  const float W3 = __fmul_rn(3.f, TG);
-  const float A5 = fmaf(P0 + (V + W3), 1.f / 12.f, dxy);
-  const float A7 = fmaf(P0 + (V - W3), 1.f / 12.f, -dxy);
-  const float jp = jx + jy, jm = jy - jx;
-  fs[1] = fmaf(jx, 1.f / 3.f, A1); fs[2] = fmaf(jx, -1.f / 3.f, A1);
-  fs[3] = fmaf(jy, 1.f / 3.f, A3); fs[4] = fmaf(jy, -1.f / 3.f, A3);
-  fs[5] = fmaf(jp, 1.f / 12.f, A5); fs[6] = fmaf(jp, -1.f / 12.f, A5);
-  fs[7] = fmaf(jm, 1.f / 12.f, A7); fs[8] = fmaf(jm, -1.f / 12.f, A7);
-  fs[0] = fmaf(-2.f, (A1 + A3) + (A5 + A7), drho);
-  // g^eq (App. A, dt = 1)
-  const float Q3 = __fmul_rn(Q.M3, mu), Q12 = __fmul_rn(Q.M12, mu);
-  const float nu2 = __fmul_rn(fmaf(ux, ux, __fmul_rn(uy, uy)), -1.f / 3.f);  // -u.u / 3
-  const float hp = __fmul_rn(0.5f, phi), hq = __fmul_rn(0.125f, phi);
-  const float upp = ux + uy, ump = ux - uy;
-  const float B1 = fmaf(hp, fmaf(ux, ux, nu2), Q3);
-  const float B3 = fmaf(hp, fmaf(uy, uy, nu2), Q3);
-  const float B5 = fmaf(hq, fmaf(upp, upp, nu2), Q12);
-  const float B7 = fmaf(hq, fmaf(ump, ump, nu2), Q12);
-  const float p3 = __fmul_rn(phi, 1.f / 3.f), p12 = __fmul_rn(phi, 1.f / 12.f);
-  ge[1] = fmaf(p3, ux, B1); ge[2] = fmaf(-p3, ux, B1);
-  ge[3] = fmaf(p3, uy, B3); ge[4] = fmaf(-p3, uy, B3);
-  ge[5] = fmaf(p12, upp, B5); ge[6] = fmaf(-p12, upp, B5);
-  ge[7] = fmaf(-p12, ump, B7); ge[8] = fmaf(p12, ump, B7);
-  ge[0] = fmaf(-2.f, (B1 + B3) + (B5 + B7), phi);
-}
-
 struct MomArgs {
   Geom G;
   MomPhys Q;

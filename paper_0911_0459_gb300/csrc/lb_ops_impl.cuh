@@ -47,6 +47,7 @@ static cudaError_t launch_step(const OpArgs& a, cudaStream_t s) {
   StepArgs<MODEL, S> k;
   k.G = to_geom(a);
   k.P = to_phys<typename S::A>(a);
+  k.Q = mom_phys(a.kappa, a.Acoef, a.M, a.nu_l, a.nu_g, a.lambda_scale, a.h, a.lut);
   k.src = to_buf<S>(a.src, a);
   k.dst = to_buf<S>(a.dst, a);
   k.yc = a.yc;
@@ -68,6 +69,7 @@ static cudaError_t launch_staged(const OpArgs& a, cudaStream_t s) {
   TmaArgs<MODEL, S> k;
   k.G = to_geom(a);
   k.P = to_phys<typename S::A>(a);
+  k.Q = mom_phys(a.kappa, a.Acoef, a.M, a.nu_l, a.nu_g, a.lambda_scale, a.h, a.lut);
   k.src = to_buf<S>(a.src, a);
   k.dst = to_buf<S>(a.dst, a);
   k.yc = a.yc;

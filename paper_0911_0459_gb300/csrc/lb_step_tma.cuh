@@ -174,6 +174,7 @@ template <int MODEL, class S>
 struct TmaArgs {
   Geom G;
   Phys<typename S::A> P;
+  MomPhys Q;  // the pair-form constants (storages that compute in deviations)
   Buf<S> src, dst;
   int yc;
   int* err;  // set to 1 when a wait gave up
@@ -355,9 +356,11 @@ __device__ __forceinline__ void push_node_blk(float* __restrict__ f, unsigned lo
 // that aligned rows keep constant columns and no per-row work).
 template <int MODEL, class S, int BX, int NS, bool UROWS = false>
 __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, const Phys<typename S::A>& P,
-                             const Buf<S>& dst, int xb, int y0, int y1, unsigned kbase, int warp, int lane) {
+                             const MomPhys& Q, const Buf<S>& dst, int xb, int y0, int y1, unsigned kbase, int warp,
+                             int lane) {
   using L = TmaLayout<MODEL, S, BX, NS>;
   using A = typename S::A;
+  constexpr bool RAW = dev_arith<S>::value;
   constexpr bool BIN = L::BIN;
   constexpr int W = L::W;
   const int nx = G.nx, ny = G.ny;
@@ -370,7 +373,12 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
 
   auto load_pop = [&](int s, int c, A f[9], A g[9]) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = S::pf(R.f(s), W, c, i, dst.r);  // the stage holds this lattice
+    for (int i = 0; i < 9; ++i) {
+      if constexpr (RAW)
+        f[i] = S::pfr(R.f(s), W, c, i);
+      else
+        f[i] = S::pf(R.f(s), W, c, i, dst.r);  // the stage holds this lattice
+    }
     if (BIN) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) g[i] = S::pg(R.g(s), R.g0(s), W, c, i);
@@ -461,7 +469,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
                                  (uint32_t)(rowb[2] >> 5) * SF32B::kBlock};
       push_node_blk<MODEL>(reinterpret_cast<float*>(dst.f), blk_lim, rpart, cpart, sol, bnd, fs, ge);
     } else {
-      push_node_u32<MODEL, S>(dst, N32, rowb, col, sol, bnd, fs, ge);
+      push_node_u32<MODEL, S, RAW>(dst, N32, rowb, col, sol, bnd, fs, ge);
     }
   };
 
@@ -534,13 +542,19 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
 #pragma unroll
             for (int i = 0; i < 3; ++i) sol[j][i] = false;
         }
-        collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
+        if constexpr (RAW)
+          collide_node_f16<MODEL>(Q, vr, vp, sol, bnd, fa, fs, ge);
+        else
+          collide_node<MODEL, A>(P, vr, vp, sol, bnd, fa, fs, ge);
         push(rowb, sol, bnd, fs, ge);
       }
     } else {
       const bool sol[3][3] = {{false, false, false}, {false, false, false}, {false, false, false}};
       if (act) {
-        collide_node<MODEL, A>(P, vr, vp, sol, false, fa, fs, ge);
+        if constexpr (RAW)
+          collide_node_f16<MODEL>(Q, vr, vp, sol, false, fa, fs, ge);
+        else
+          collide_node<MODEL, A>(P, vr, vp, sol, false, fa, fs, ge);
         push(rowb, sol, false, fs, ge);
       }
     }
@@ -602,10 +616,10 @@ __global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) step_tma_kern
   }
   bool ok;
   if constexpr (TmaLayout<MODEL, S, BX, NS>::BLK) {
-    ok = a.G.nx % 32 != 0 ? consume_tile<MODEL, S, BX, NS, true>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane)
-                          : consume_tile<MODEL, S, BX, NS, false>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane);
+    ok = a.G.nx % 32 != 0 ? consume_tile<MODEL, S, BX, NS, true>(R, a.G, a.P, a.Q, a.dst, xb, y0, y1, 0u, warp, lane)
+                          : consume_tile<MODEL, S, BX, NS, false>(R, a.G, a.P, a.Q, a.dst, xb, y0, y1, 0u, warp, lane);
   } else {
-    ok = consume_tile<MODEL, S, BX, NS>(R, a.G, a.P, a.dst, xb, y0, y1, 0u, warp, lane);
+    ok = consume_tile<MODEL, S, BX, NS>(R, a.G, a.P, a.Q, a.dst, xb, y0, y1, 0u, warp, lane);
   }
   if (!ok && lane == 0)
     atomicExch(a.err, 1);
