@@ -160,7 +160,7 @@ __device__ __forceinline__ bool grid_barrier_checked(GridBarrier* b, unsigned in
 // 16-byte alignment).  Per-node arithmetic is the single-lattice kernels', so
 // results are bitwise those of lb_step with the staged kernel.
 template <class S, int BX, int NS>
-__global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) batch_tma_kernel(BatchArgs<S> a) {
+__global__ void __launch_bounds__(BX + 32, (tma_min_blocks_of<MODEL_BINARY, S, BX, NS>())) batch_tma_kernel(BatchArgs<S> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Ring<MODEL_BINARY, S, BX, NS> R = ring_init<MODEL_BINARY, S, BX, NS>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

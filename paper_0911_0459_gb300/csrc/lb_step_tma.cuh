@@ -592,12 +592,26 @@ __device__ __forceinline__ bool tile_all_solid(const Geom& G, int xb, int w, int
 }
 
 // Resident CTAs per SM the staged kernels are compiled for (caps their registers).
+// The block storage's stages are larger, so its rings set the count: as many CTAs
+// as the SM's 228 KB of shared memory holds (each with its 1 KB reservation), and
+// the registers that count leaves (96 per thread at 128 columns and 4 stages
+// instead of 72: 1 % faster on 16384 x 256).
 constexpr int tma_min_blocks(int bx, int ns) {
   return bx == 64 ? (ns > 4 ? 4 : 8) : (bx == 128 ? (ns > 4 ? 3 : 5) : (ns > 3 ? 2 : 3));
 }
+template <int MODEL, class S, int BX, int NS>
+constexpr int tma_min_blocks_of() {
+  using L = TmaLayout<MODEL, S, BX, NS>;
+  if constexpr (L::BLK) {
+    constexpr int b = int(233472 / (L::BYTES + 1024));
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+  } else {
+    return tma_min_blocks(BX, NS);
+  }
+}
 
 template <int MODEL, class S, int BX, int NS>
-__global__ void __launch_bounds__(BX + 32, tma_min_blocks(BX, NS)) step_tma_kernel(TmaArgs<MODEL, S> a) {
+__global__ void __launch_bounds__(BX + 32, (tma_min_blocks_of<MODEL, S, BX, NS>())) step_tma_kernel(TmaArgs<MODEL, S> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Ring<MODEL, S, BX, NS> R = ring_init<MODEL, S, BX, NS>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
