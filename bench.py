@@ -205,6 +205,7 @@ def fluid_nodes_of(cap):
 # algorithmic bytes per fluid-node update and the name of each storage
 STORAGES = {"f32b": (144.0, "FP32 populations in 32-node blocks", "SF32B"),
             "f32": (144.0, "FP32 populations in planes", "FP32"), "f16dev": (76.0, "FP16-deviation storage", "FP16dev"),
+            "f16b": (76.0, "FP16-deviation storage in 32-node blocks", "SF16B"),
             "moments": (48.0, "FP32 moment storage", "SM32"), "moments_f16": (28.0, "FP16 moment storage", "SM16"),
             "gelim": (80.0, "FP32 f + phi storage (g eliminated)", "SG32")}
 
@@ -273,14 +274,14 @@ def cpu_baseline(sample_steps=2000, copy_steps=500):
 
 def precision_report(Lattice, orc, steps):
     """Error of each storage against the FP64 oracle on the crop after `steps` steps."""
-    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F32_GELIM,
-                                       STORAGE_F64, STORAGE_MOMENTS, STORAGE_MOMENTS_F16)
+    from paper_0911_0459_gb300 import (STORAGE_F16_BLOCKED, STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED,
+                                       STORAGE_F32_GELIM, STORAGE_F64, STORAGE_MOMENTS, STORAGE_MOMENTS_F16)
     rho_o, _, _, phi_o = orc.fields()
     l_o = orc.filled_length()["l"]
     out = {"workload": "1024x64 crop of the large capillary, default initial state", "steps": steps}
     import dataclasses
     for name, st, table in (("f64", STORAGE_F64, 0), ("f32", STORAGE_F32, 0), ("f32_blocks", STORAGE_F32_BLOCKED, 0),
-                            ("f16dev", STORAGE_F16DEV, 0),
+                            ("f16dev", STORAGE_F16DEV, 0), ("f16_blocks", STORAGE_F16_BLOCKED, 0),
                             ("moments_f32", STORAGE_MOMENTS, 0), ("moments_f16", STORAGE_MOMENTS_F16, 0),
                             ("f32_g_eliminated", STORAGE_F32_GELIM, 0), ("f32_nu_table_1e4", STORAGE_F32, 10000)):
         cap = W.config_binary_crop_1024x64(st)
@@ -531,8 +532,8 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F32_GELIM,
-                                       STORAGE_MOMENTS, STORAGE_MOMENTS_F16, Lattice)
+    from paper_0911_0459_gb300 import (STORAGE_F16_BLOCKED, STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED,
+                                       STORAGE_F32_GELIM, STORAGE_MOMENTS, STORAGE_MOMENTS_F16, Lattice)
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -543,8 +544,8 @@ def main():
             dist.barrier()
 
     cap = W.config_binary_16384x256({"f32b": STORAGE_F32_BLOCKED, "f32": STORAGE_F32, "f16dev": STORAGE_F16DEV,
-                                     "moments": STORAGE_MOMENTS, "moments_f16": STORAGE_MOMENTS_F16,
-                                     "gelim": STORAGE_F32_GELIM}[args.storage])
+                                     "f16b": STORAGE_F16_BLOCKED, "moments": STORAGE_MOMENTS,
+                                     "moments_f16": STORAGE_MOMENTS_F16, "gelim": STORAGE_F32_GELIM}[args.storage])
     if args.profile and args.workload == "lg_16384x256":
         cap = W.config_lg_16384x256()
     lat = Lattice.from_workload(cap)
@@ -648,21 +649,28 @@ def main():
                               "what": "the same FP32 populations and arithmetic (bit-identical states), the other "
                                       "layout; autotuned, 512 steps, CUDA events"}
             lp.close()
-        c16 = W.config_binary_16384x256(STORAGE_F16DEV)
-        l16 = Lattice.from_workload(c16)
-        l16.autotune()
-        l16.step(8)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(l16.stream)
-        l16.step(512)
-        b.record(l16.stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 512
-        secondary["fp16dev_16384x256"] = {"MLUPS": l16.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms,
-                                          "bytes_per_lu": 76, "GBps": l16.fluid_nodes * 76 / (ms * 1e-3) / 1e9}
-        l16.close()
+        for key, st, lbl, what in (
+                ("fp16dev_16384x256", STORAGE_F16DEV, "FP16dev",
+                 "FP16 f_i - w_i and g_1..g_8 in planes, FP32 g_0 plane"),
+                ("fp16_blocks_16384x256", STORAGE_F16_BLOCKED, "SF16B",
+                 "the same FP16 values in 32-node blocks (bit-identical states), one bulk copy per staged row")):
+            l16 = Lattice.from_workload(W.config_binary_16384x256(st))
+            htx, hty, _ = l16.autotune()
+            l16.step(8)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(l16.stream)
+            l16.step(512)
+            b.record(l16.stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 512
+            gbs = l16.fluid_nodes * 76 / (ms * 1e-3) / 1e9
+            secondary[key] = {"MLUPS": l16.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms, "tile": [htx, hty],
+                              "kernel": step_kernel_label(l16.kernel(), htx, hty, lbl),
+                              "bytes_per_lu": 76, "GBps": gbs, "frac_of_measured_hbm": gbs / peak,
+                              "what": what + "; autotuned, 512 steps, CUDA events"}
+            l16.close()
         c1 = W.config_lg_256x32()
         l1 = Lattice.from_workload(c1)
         l1.autotune()

@@ -104,7 +104,18 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
  * columns is then one contiguous range of blocks, which the staged step kernel
  * fetches with one bulk copy per row (plus one block at an x-wrap) instead of one
  * copy per population plane; any nx.  At most 238609280 nodes
- * (18 * 32 * ceil(nx ny / 32) < 2^32). */
+ * (18 * 32 * ceil(nx ny / 32) < 2^32).
+ *
+ * LB_STORAGE_F16_BLOCKED (binary model only) keeps the values of
+ * LB_STORAGE_F16DEV (FP16 f_i - w_i rho0 and g_1..g_8, FP32 g_0; the two give
+ * identical results) in blocks of 32 consecutive nodes: block b = n / 32 is
+ * 1216 bytes, f_0..f_8 less the offsets (FP16, 32 values each), then g_1..g_8
+ * (FP16), then g_0 (FP32), so f_i of node n is half element 608 b + 32 i + n % 32
+ * of the state, g_i (i >= 1) half 608 b + 288 + 32 (i - 1) + n % 32 and g_0
+ * float 304 b + 272 + n % 32; the last block is padded (the state is
+ * 1216 ceil(nx ny / 32) bytes; lb_save_state writes this layout).  One bulk copy
+ * per staged row, as for LB_STORAGE_F32_BLOCKED; any nx.  At most 226050880 nodes
+ * (19 * 32 * ceil(nx ny / 32) < 2^32). */
 typedef enum {
   LB_STORAGE_F64 = 0,
   LB_STORAGE_F32 = 1,
@@ -112,7 +123,8 @@ typedef enum {
   LB_STORAGE_MOMENTS = 3,
   LB_STORAGE_MOMENTS_F16 = 4,
   LB_STORAGE_F32_GELIM = 5,
-  LB_STORAGE_F32_BLOCKED = 6
+  LB_STORAGE_F32_BLOCKED = 6,
+  LB_STORAGE_F16_BLOCKED = 7
 } lb_storage;
 
 typedef struct {
@@ -260,7 +272,8 @@ lb_status lb_get_tile(const lb_ctx *ctx, int *tile_x, int *tile_y);
 /* Choose the step kernel: 0 = automatic (the staged kernel whenever it fits,
  * else the sliding-window kernel), 1 = sliding-window kernel (rows held in
  * registers), 2 = staged kernel (rows brought into shared memory by bulk
- * copies; fits when nx % 8 == 0 and nx * ny <= 477218588, else LB_ERR_ARG)
+ * copies; fits when nx % 8 == 0 and nx * ny <= 477218588, and at any nx for
+ * the block storages, else LB_ERR_ARG)
  * with its shallow ring of row stages, 3 = staged kernel with its deep ring.
  * All compute the same update bit for bit.  LB_STORAGE_MOMENTS,
  * LB_STORAGE_MOMENTS_F16 and LB_STORAGE_F32_GELIM have one kernel of their own,
@@ -302,7 +315,8 @@ typedef struct lb_batch lb_batch;
 
 /* n lattices, each described as for lb_create (all binary, one common
  * storage: LB_STORAGE_F64, LB_STORAGE_F32, LB_STORAGE_F32_BLOCKED,
- * LB_STORAGE_F16DEV or LB_STORAGE_MOMENTS), each set to the default initial
+ * LB_STORAGE_F16DEV, LB_STORAGE_F16_BLOCKED or LB_STORAGE_MOMENTS), each set to
+ * the default initial
  * state.  *out set only on LB_OK. */
 lb_status lb_batch_create(int n, const lb_grid *grids, const lb_walls *walls, const lb_params *params,
                           const lb_alloc *alloc, void *stream, lb_batch **out);

@@ -151,6 +151,10 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
   ob.g = b->storage == LB_STORAGE_F32_BLOCKED ? (char*)ob.f + 288 * el  // g beside f in every block
                                               : (b->g[k] ? (char*)b->g[k] + b->off_g[i] * el : NULL);
   ob.g0 = b->g0[k] ? b->g0[k] + b->off_g0[i] : NULL;
+  if (b->storage == LB_STORAGE_F16_BLOCKED) {  // g_1..g_8 at byte 576 and g_0 at byte 1088 of every block
+    ob.g = (char*)ob.f + 576;
+    ob.g0 = (float*)((char*)ob.f + 1088);
+  }
   a.src = ob;
   a.dst = ob;
   return a;
@@ -159,6 +163,7 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
 static OpsFn batch_ops(int storage) {
   if (storage == LB_STORAGE_MOMENTS) return ops_bin_m32;
   if (storage == LB_STORAGE_F32_BLOCKED) return ops_bin_f32b;
+  if (storage == LB_STORAGE_F16_BLOCKED) return ops_bin_f16b;
   return storage == LB_STORAGE_F64 ? ops_bin_f64 : (storage == LB_STORAGE_F32 ? ops_bin_f32 : ops_bin_f16);
 }
 
@@ -304,6 +309,7 @@ static cudaError_t run_batch(lb_batch* b, int nsteps, cudaStream_t s, int* per) 
   if (b->storage == LB_STORAGE_F64) return run_s<SF64>(b, nsteps, s, per);
   if (b->storage == LB_STORAGE_F32) return run_s<SF32>(b, nsteps, s, per);
   if (b->storage == LB_STORAGE_F32_BLOCKED) return run_s<SF32B>(b, nsteps, s, per);
+  if (b->storage == LB_STORAGE_F16_BLOCKED) return run_s<SF16B>(b, nsteps, s, per);
   return run_s<SF16>(b, nsteps, s, per);
 }
 
@@ -436,6 +442,7 @@ static cudaError_t launch_reduce(lb_batch* b, int buf, int nsamples, int col, do
   if (b->storage == LB_STORAGE_F64) return launch_reduce_s<SF64>(b, buf, nsamples, col, out, s);
   if (b->storage == LB_STORAGE_F32) return launch_reduce_s<SF32>(b, buf, nsamples, col, out, s);
   if (b->storage == LB_STORAGE_F32_BLOCKED) return launch_reduce_s<SF32B>(b, buf, nsamples, col, out, s);
+  if (b->storage == LB_STORAGE_F16_BLOCKED) return launch_reduce_s<SF16B>(b, buf, nsamples, col, out, s);
   return launch_reduce_s<SF16>(b, buf, nsamples, col, out, s);
 }
 
@@ -494,7 +501,7 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   *out = NULL;
   const int storage = params[0].storage;
   if (storage != LB_STORAGE_F64 && storage != LB_STORAGE_F32 && storage != LB_STORAGE_F16DEV &&
-      storage != LB_STORAGE_MOMENTS && storage != LB_STORAGE_F32_BLOCKED)
+      storage != LB_STORAGE_MOMENTS && storage != LB_STORAGE_F32_BLOCKED && storage != LB_STORAGE_F16_BLOCKED)
     return berr(NULL, "unknown storage %d", storage), LB_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     if (params[i].model != LB_MODEL_BINARY) return berr(NULL, "batches hold binary lattices"), LB_ERR_ARG;
@@ -506,6 +513,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
       return berr(NULL, "lattice %d: the moment storage holds at most 715827882 nodes", i), LB_ERR_ARG;
     if (storage == LB_STORAGE_F32_BLOCKED && 18ull * (((unsigned long long)g.nx * g.ny + 31) / 32 * 32) >= (1ull << 32))
       return berr(NULL, "lattice %d: the block storage holds at most 238609280 nodes", i), LB_ERR_ARG;
+    if (storage == LB_STORAGE_F16_BLOCKED && 19ull * (((unsigned long long)g.nx * g.ny + 31) / 32 * 32) >= (1ull << 32))
+      return berr(NULL, "lattice %d: the FP16 block storage holds at most 226050880 nodes", i), LB_ERR_ARG;
     if (!isfinite(w.wall_grad)) return berr(NULL, "lattice %d: wall_grad not finite", i), LB_ERR_ARG;
     if (!(params[i].M >= 0)) return berr(NULL, "lattice %d: mobility must be >= 0", i), LB_ERR_ARG;
     if (w.tube_len < 0 || w.tube_len > g.nx) return berr(NULL, "lattice %d: tube_len outside [0, nx]", i), LB_ERR_ARG;
@@ -531,8 +540,9 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   b->tile_x = 128;
   b->tile_y = 8;
   b->staged_ok = 1;
-  for (int i = 0; i < n; ++i)  // the block storage stages whole blocks at any nx
-    b->staged_ok = b->staged_ok && (storage == LB_STORAGE_F32_BLOCKED || staged_fits(grids[i].nx, grids[i].ny));
+  for (int i = 0; i < n; ++i)  // the block storages stage whole blocks at any nx
+    b->staged_ok = b->staged_ok && (storage == LB_STORAGE_F32_BLOCKED || storage == LB_STORAGE_F16_BLOCKED ||
+                                    staged_fits(grids[i].nx, grids[i].ny));
   b->limit_ns = kDefaultLimitNs;
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     berr(NULL, "cudaStreamCreate failed");
@@ -541,7 +551,8 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
   }
   const size_t el = elem_size(storage);
   const int moments = storage == LB_STORAGE_MOMENTS;
-  const int blocked = storage == LB_STORAGE_F32_BLOCKED;  // f and g in 32-node blocks, one arena
+  // f and g in 32-node blocks, one arena: elements per 32 nodes (floats or halves)
+  const int blocked = storage == LB_STORAGE_F32_BLOCKED ? 18 : (storage == LB_STORAGE_F16_BLOCKED ? 19 : 0);
   const int nf = moments ? M_PLANES : 9;
   const int ng = (moments || blocked) ? 0 : (storage == LB_STORAGE_F16DEV ? 8 : 9);
   size_t of = 0, og = 0, o0 = 0;
@@ -550,7 +561,7 @@ lb_status lb_batch_create(int n, const lb_grid* grids, const lb_walls* walls, co
     b->off_f.push_back(of);
     b->off_g.push_back(og);
     b->off_g0.push_back(o0);
-    of += blocked ? (18 * ((N + 31) / 32 * 32) + 63) / 64 * 64 : (nf * N + 63) / 64 * 64;
+    of += blocked ? (blocked * ((N + 31) / 32 * 32) + 63) / 64 * 64 : (nf * N + 63) / 64 * 64;
     og += (ng * N + 63) / 64 * 64;
     o0 += (N + 63) / 64 * 64;
     // solid nodes: the tube's columns outside its band

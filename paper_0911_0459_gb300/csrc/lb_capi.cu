@@ -108,6 +108,7 @@ static OpsFn pick_ops(int model, int storage) {
     if (storage == LB_STORAGE_MOMENTS_F16) return ops_bin_m16;
     if (storage == LB_STORAGE_F32_GELIM) return ops_bin_g32;
     if (storage == LB_STORAGE_F32_BLOCKED) return ops_bin_f32b;
+    if (storage == LB_STORAGE_F16_BLOCKED) return ops_bin_f16b;
   }
   return NULL;
 }
@@ -116,7 +117,7 @@ static OpsFn pick_ops(int model, int storage) {
 // storages (nx % 8 == 0) and 32-bit offsets; the block storage stages whole
 // blocks at any nx (its node limit is checked at creation).
 static bool staged_ok(int storage, int nx, int ny) {
-  return storage == LB_STORAGE_F32_BLOCKED || staged_fits(nx, ny);
+  return storage == LB_STORAGE_F32_BLOCKED || storage == LB_STORAGE_F16_BLOCKED || staged_fits(nx, ny);
 }
 
 static OpArgs base_args(const lb_ctx* c) {
@@ -206,8 +207,9 @@ static size_t state_bytes(int model, int storage, size_t N, size_t* fb, size_t* 
     *g0b = 0;
     return *fb;
   }
-  if (storage == LB_STORAGE_F32_BLOCKED) {  // f and g of every 32-node block together, in the f buffer
-    *fb = 18 * ((N + 31) / 32 * 32) * sizeof(float);
+  if (storage == LB_STORAGE_F32_BLOCKED || storage == LB_STORAGE_F16_BLOCKED) {
+    // f and g of every 32-node block together, in the f buffer
+    *fb = (N + 31) / 32 * (storage == LB_STORAGE_F32_BLOCKED ? 2304 : 1216);
     *gb = 0;
     *g0b = 0;
     return *fb;
@@ -230,6 +232,8 @@ static lb_status validate(const lb_grid* g, const lb_walls* w, const lb_params* 
     return set_err(c, "the g-eliminated storage holds at most 429496729 nodes"), LB_ERR_ARG;
   if (p->storage == LB_STORAGE_F32_BLOCKED && 18ull * (((unsigned long long)g->nx * g->ny + 31) / 32 * 32) >= (1ull << 32))
     return set_err(c, "the block storage holds at most 238609280 nodes"), LB_ERR_ARG;
+  if (p->storage == LB_STORAGE_F16_BLOCKED && 19ull * (((unsigned long long)g->nx * g->ny + 31) / 32 * 32) >= (1ull << 32))
+    return set_err(c, "the FP16 block storage holds at most 226050880 nodes"), LB_ERR_ARG;
   if (w->tube_len < 0 || w->tube_len > g->nx) return set_err(c, "tube_len outside [0, nx]"), LB_ERR_ARG;
   if (w->tube_len > 0) {
     if (w->tube_x0 < 0 || w->tube_x0 >= g->nx || w->tube_y0 < 0 || w->tube_y0 >= g->ny)
@@ -352,6 +356,11 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
     c->buf[k].g0 = g0b ? (float*)dev_alloc_owned(c, g0b) : NULL;
     // the block storage keeps g beside f in every block
     if (params->storage == LB_STORAGE_F32_BLOCKED && c->buf[k].f) c->buf[k].g = (float*)c->buf[k].f + 288;
+    // the FP16 block storage: g_1..g_8 at byte 576 and g_0 at byte 1088 of every block
+    if (params->storage == LB_STORAGE_F16_BLOCKED && c->buf[k].f) {
+      c->buf[k].g = (char*)c->buf[k].f + 576;
+      c->buf[k].g0 = (float*)((char*)c->buf[k].f + 1088);
+    }
     if (!c->buf[k].f || (gb && !c->buf[k].g) || (g0b && !c->buf[k].g0)) {
       set_err(NULL, "device allocation of the state (%zu bytes) failed", 2 * (fb + gb + g0b));
       lb_destroy(c);

@@ -285,7 +285,10 @@ struct SF16 {
 struct SF32B {
   using T = float;
   using A = float;
-  static constexpr int kBlock = 576;  // elements per block of 32 nodes
+  static constexpr int kBlock = 576;       // elements per block of 32 nodes
+  static constexpr int kBlockBytes = 2304;
+  static constexpr int kGOff = 288;        // elements from a block's f_0 to its g_1 (g_0 here)
+  static constexpr int kG0 = 0;            // (g_0 lies among the g elements)
   __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
   __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
   // elements of a state of N nodes (the last block padded)
@@ -332,11 +335,122 @@ struct SF32B {
   }
 };
 
+// The FP16 deviations of SF16 in blocks of 32 consecutive nodes: block b = n / 32
+// is 1216 bytes (608 halves): f_0..f_8 less the rest offsets (FP16, 32 values
+// each), then g_1..g_8 (FP16), then g_0 (FP32, 32 values at byte 1088).  So f_i of
+// node n is half 608 b + 32 i + n % 32 of the buffer, g_i (i >= 1) half
+// 608 b + 288 + 32 (i - 1) + n % 32 (Buf::g = Buf::f + 288 halves) and g_0 float
+// 304 b + 272 + n % 32 (Buf::g0 = Buf::f + 1088 bytes).  A row segment of whole
+// blocks is again one contiguous range, which the staged kernel copies with one
+// bulk copy per row.  The last block is padded to 32 nodes.  Same values and
+// arithmetic as SF16.
+struct SF16B {
+  using T = __half;
+  using A = float;
+  static constexpr int kBlock = 608;       // halves per block of 32 nodes
+  static constexpr int kBlockBytes = 1216;
+  static constexpr int kGOff = 288;        // halves from a block's f_0 to its g_1
+  static constexpr int kG0 = 272;          // floats from a block's start to its g_0
+  static constexpr int kG0Stride = 304;    // floats per block
+  __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  __device__ static size_t at0(size_t n) { return (n >> 5) * kG0Stride + (n & 31); }
+  // halves of a state of N nodes (the last block padded)
+  __device__ static unsigned long long lim(unsigned long long N) { return 19ull * ((N + 31) & ~31ull); }
+  __device__ static unsigned long long lim0(unsigned long long N) { return lim(N) / 2 - kG0; }
+  // shared-memory stage of whole blocks: stage column c lies in block c / 32
+  __device__ static A pf(const T* f, int, int c, int i, const Rest& r) {
+    return __half2float(f[(c >> 5) * kBlock + 32 * i + (c & 31)]) + rest_w(r, i);
+  }
+  __device__ static A pfr(const T* f, int, int c, int i) { return __half2float(f[(c >> 5) * kBlock + 32 * i + (c & 31)]); }
+  __device__ static A pg(const T* g, const float* g0, int, int c, int i) {
+    return i == 0 ? g0[(c >> 5) * kG0Stride + (c & 31)] : __half2float(g[(c >> 5) * kBlock + 32 * (i - 1) + (c & 31)]);
+  }
+  __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest& r) {
+    LB_GUARD(at(n, i), lim(N), A(0));
+    return __half2float(__ldg(f + at(n, i))) + rest_w(r, i);
+  }
+  __device__ static A lfr(const T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(at(n, i), lim(N), A(0));
+    return __half2float(__ldg(f + at(n, i)));
+  }
+  __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest& r) {
+    LB_GUARD(at(n, i), lim(N), A(0));
+    return __half2float(__ldcg(f + at(n, i))) + rest_w(r, i);
+  }
+  __device__ static A lfcr(const T* f, size_t N, size_t n, int i) {
+    LB_GUARD(at(n, i), lim(N), A(0));
+    return __half2float(__ldcg(f + at(n, i)));
+  }
+  __device__ static void sf(T* __restrict__ f, size_t N, size_t n, int i, A v, const Rest& r) {
+    LB_GUARD(at(n, i), lim(N), );
+    f[at(n, i)] = __float2half_rn(v - rest_w(r, i));
+  }
+  __device__ static void sfr(T* __restrict__ f, size_t N, size_t n, int i, A v) {
+    LB_GUARD(at(n, i), lim(N), );
+    f[at(n, i)] = __float2half_rn(v);
+  }
+  __device__ static A lg(const T* __restrict__ g, const float* __restrict__ g0, size_t N, size_t n, int i) {
+    if (i == 0) {
+      LB_GUARD(at0(n), lim0(N), A(0));
+      return __ldg(g0 + at0(n));
+    }
+    LB_GUARD(at(n, i - 1), lim(N) - kGOff, A(0));
+    return __half2float(__ldg(g + at(n, i - 1)));
+  }
+  __device__ static A lgc(const T* g, const float* g0, size_t N, size_t n, int i) {
+    if (i == 0) {
+      LB_GUARD(at0(n), lim0(N), A(0));
+      return __ldcg(g0 + at0(n));
+    }
+    LB_GUARD(at(n, i - 1), lim(N) - kGOff, A(0));
+    return __half2float(__ldcg(g + at(n, i - 1)));
+  }
+  __device__ static void sg(T* __restrict__ g, float* __restrict__ g0, size_t N, size_t n, int i, A v) {
+    if (i == 0) {
+      LB_GUARD(at0(n), lim0(N), );
+      g0[at0(n)] = v;
+      return;
+    }
+    LB_GUARD(at(n, i - 1), lim(N) - kGOff, );
+    g[at(n, i - 1)] = __float2half_rn(v);
+  }
+  // 32-bit element offsets (needs 19 * 32 * ceil(N / 32) < 2^32)
+  __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest& r) {
+    LB_GUARD(at32(n, i), lim(N), );
+    f[at32(n, i)] = __float2half_rn(v - rest_w(r, i));
+  }
+  __device__ static void sfor(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v) {
+    LB_GUARD(at32(n, i), lim(N), );
+    f[at32(n, i)] = __float2half_rn(v);
+  }
+  __device__ static void sgo(T* __restrict__ g, float* __restrict__ g0, uint32_t N, uint32_t n, int i, A v) {
+    if (i == 0) {
+      const uint32_t o = (n >> 5) * kG0Stride + (n & 31);
+      LB_GUARD(o, lim0(N), );
+      g0[o] = v;
+      return;
+    }
+    LB_GUARD(at32(n, i - 1), lim(N) - kGOff, );
+    g[at32(n, i - 1)] = __float2half_rn(v);
+  }
+  __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
+    LB_GUARD(at(n, i), lim(N), );
+    f[at(n, i)] = __float2half_rn(0.0f);
+  }
+};
+
+// Population storages in 32-node blocks (one bulk copy per staged row).
+template <class S>
+struct is_blocked {
+  static constexpr bool value = std::is_same<S, SF32B>::value || std::is_same<S, SF16B>::value;
+};
+
 // Population storages whose step kernels compute in deviations from the stored
-// rest offsets (the FP16 storage): raw loads and stores, collide_node_f16.
+// rest offsets (the FP16 storages): raw loads and stores, collide_node_f16.
 template <class S>
 struct dev_arith {
-  static constexpr bool value = std::is_same<S, SF16>::value;
+  static constexpr bool value = std::is_same<S, SF16>::value || std::is_same<S, SF16B>::value;
 };
 
 template <class S>

@@ -82,5 +82,6 @@ cudaError_t ops_bin_m32(OpKind, const OpArgs&, cudaStream_t);  // moment storage
 cudaError_t ops_bin_m16(OpKind, const OpArgs&, cudaStream_t);  // FP16 moments, FP32 phi
 cudaError_t ops_bin_g32(OpKind, const OpArgs&, cudaStream_t);  // f and phi (g eliminated)
 cudaError_t ops_bin_f32b(OpKind, const OpArgs&, cudaStream_t);  // FP32 populations in 32-node blocks
+cudaError_t ops_bin_f16b(OpKind, const OpArgs&, cudaStream_t);  // FP16 deviations in 32-node blocks
 
 }  // namespace lbk

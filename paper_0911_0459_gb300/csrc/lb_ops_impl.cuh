@@ -112,7 +112,7 @@ cudaError_t ops_impl(OpKind op, const OpArgs& a, cudaStream_t s) {
     case OP_STEP:
       if constexpr (!is_moments<S>::value) {
         if (a.staged) {
-          if ((!std::is_same<S, SF32B>::value && !staged_fits(a.nx, a.ny)) || !a.err) return cudaErrorInvalidValue;
+          if ((!is_blocked<S>::value && !staged_fits(a.nx, a.ny)) || !a.err) return cudaErrorInvalidValue;
           if (a.bx == 64) return a.deep ? launch_staged<MODEL, S, 64, 8>(a, s) : launch_staged<MODEL, S, 64, 4>(a, s);
           if (a.bx == 128) return a.deep ? launch_staged<MODEL, S, 128, 6>(a, s) : launch_staged<MODEL, S, 128, 4>(a, s);
           if (a.bx == 256) return a.deep ? launch_staged<MODEL, S, 256, 4>(a, s) : launch_staged<MODEL, S, 256, 3>(a, s);

@@ -7,8 +7,8 @@
 //     brings every row of all 18 population planes (plus 8 halo columns either
 //     side) into a shared-memory ring of NS stages with cp.async.bulk copies,
 //     signalled on a per-stage "full" mbarrier (complete_tx).  The planar
-//     storages take one copy per plane and row; the 32-node block storage
-//     (SF32B) one copy per row, of the whole blocks over the tile's nodes and
+//     storages take one copy per plane and row; the 32-node block storages
+//     (SF32B, SF16B) one copy per row, of the whole blocks over the tile's nodes and
 //     their neighbour columns: a CTA's bulk copies, not their bytes, limited
 //     the planar ring;
 //   - BX/32 consumer warps work independently: each keeps rho/phi of rows
@@ -27,8 +27,8 @@
 //     outside the band) is not summed: the wall ghosts replace all its values;
 //     a tile whose nodes are all solid exits at once.
 // Requires, for the planar storages, nx % 8 == 0 (16-byte aligned rows) and
-// 9 nx ny < 2^32 (32-bit offsets); the block storage takes any nx with
-// 18 * 32 * ceil(nx ny / 32) < 2^32.  BX % 32 == 0.  Halo columns at the x-wrap
+// 9 nx ny < 2^32 (32-bit offsets); the block storages take any nx with
+// 18 * 32 * ceil(nx ny / 32) < 2^32 (FP32) or 19 * 32 * ceil(nx ny / 32) < 2^32 (FP16).  BX % 32 == 0.  Halo columns at the x-wrap
 // come from a second 16-byte-aligned copy of the 8 elements (the block storage:
 // the 32-node block) at the other end of the row.
 //
@@ -121,21 +121,30 @@ struct NGPlanes<SF16> {
   static constexpr int value = 8;
 };
 
+// Bytes of one 32-node block of a block storage (0 for the planar storages).
+template <class S, bool = is_blocked<S>::value>
+struct BlkBytes {
+  static constexpr size_t value = 0;
+};
+template <class S>
+struct BlkBytes<S, true> {
+  static constexpr size_t value = S::kBlockBytes;
+};
+
 template <int MODEL, class S, int BX, int NS>
 struct TmaLayout {
   using T = typename S::T;
   using A = typename S::A;
   static constexpr bool BIN = MODEL == MODEL_BINARY;
   static constexpr bool F16 = sizeof(T) == 2;
-  // 32-node blocks (SF32B): a stage row is whole blocks, one bulk copy
-  static constexpr bool BLK = std::is_same<S, SF32B>::value;
+  // 32-node blocks (SF32B, SF16B): a stage row is whole blocks, one bulk copy
+  static constexpr bool BLK = is_blocked<S>::value;
   static constexpr int HALO = BLK ? 32 : 8;          // staged columns either side of the tile
   static constexpr int W = BX + 2 * HALO;            // staged columns: xb-HALO .. xb+BX+HALO-1
   static constexpr int NF = 9;
   static constexpr int NG = BIN ? NGPlanes<S>::value : 0;
-  static constexpr int NG0 = (BIN && F16) ? 1 : 0;   // FP32 g_0 plane of the FP16 storage
-  static constexpr size_t STAGE_T = BLK ? (size_t)(W / 32) * SF32B::kBlock * sizeof(float)
-                                        : (size_t)(NF + NG) * W * sizeof(T);
+  static constexpr int NG0 = (BIN && F16 && !BLK) ? 1 : 0;  // FP32 g_0 plane of the planar FP16 storage
+  static constexpr size_t STAGE_T = BLK ? (size_t)(W / 32) * BlkBytes<S>::value : (size_t)(NF + NG) * W * sizeof(T);
   static constexpr size_t STAGE_G0 = (size_t)NG0 * W * sizeof(float);
   static constexpr size_t STAGE = ((STAGE_T + STAGE_G0) + 127) / 128 * 128;
   static constexpr size_t BYTES = NS * STAGE + 2 * NS * 8;
@@ -196,9 +205,17 @@ struct Ring {
   uint64_t* empty;
   __device__ T* f(int s) const { return reinterpret_cast<T*>(smem + s * L::STAGE); }
   __device__ T* g(int s) const {
-    return reinterpret_cast<T*>(smem + s * L::STAGE) + (L::BLK ? SF32B::kBlock / 2 : 9 * L::W);
+    if constexpr (L::BLK)
+      return reinterpret_cast<T*>(smem + s * L::STAGE) + S::kGOff;
+    else
+      return reinterpret_cast<T*>(smem + s * L::STAGE) + 9 * L::W;
   }
-  __device__ float* g0(int s) const { return reinterpret_cast<float*>(smem + s * L::STAGE + L::STAGE_T); }
+  __device__ float* g0(int s) const {
+    if constexpr (L::BLK)
+      return reinterpret_cast<float*>(smem + s * L::STAGE) + S::kG0;  // inside each block (SF16B)
+    else
+      return reinterpret_cast<float*>(smem + s * L::STAGE + L::STAGE_T);
+  }
 };
 
 template <int MODEL, class S, int BX, int NS>
@@ -242,7 +259,7 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const int so = lo - (xb - H);      // stage column of global column lo
   const int sr = nx - (xb - H);      // stage column of the right wrap chunk
   const uint32_t ecols = (uint32_t)(ncols + (wl ? H : 0) + (wr ? H : 0));
-  const uint32_t total = L::BLK ? ecols * (uint32_t)(SF32B::kBlock / 32 * sizeof(float))
+  const uint32_t total = L::BLK ? ecols * (uint32_t)(BlkBytes<S>::value / 32)
                                 : ecols * (uint32_t)sizeof(T) * (L::NF + L::NG) + (L::NG0 ? ecols * 4u : 0u);
   auto planes = [&](const T* base, int nplanes, T* dst0, size_t rowoff, uint64_t* bar) {
     const size_t lim = (size_t)nplanes * N;
@@ -255,11 +272,13 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     }
   };
   // whole 32-node blocks: nodes [n0, n0 + cnt) of the row to stage column c
-  auto blocks = [&](T* dst0, size_t n0, int cnt, int c, uint64_t* bar) {
-    constexpr int B = SF32B::kBlock;
-    const size_t lim = 18 * N;
-    bulk_g2s(dst0 + (c / 32) * B, copy_src(src.f, (n0 / 32) * B, (size_t)(cnt / 32) * B, lim),
-             (uint32_t)(cnt / 32) * B * sizeof(float), bar);
+  [[maybe_unused]] auto blocks = [&](T* dst0, size_t n0, int cnt, int c, uint64_t* bar) {
+    if constexpr (L::BLK) {
+      constexpr int B = S::kBlock;
+      const size_t lim = (N + 31) / 32 * B;
+      bulk_g2s(dst0 + (c / 32) * B, copy_src(src.f, (n0 / 32) * B, (size_t)(cnt / 32) * B, lim),
+               (uint32_t)(cnt / 32) * B * sizeof(T), bar);
+    }
   };
   // every staged column inside the tube: rows outside the band are all solid and
   // their populations are never read (ghosts replace them), so they are not copied
@@ -281,17 +300,17 @@ __device__ bool produce_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       if (nx % 32 != 0) {
         // rows that start inside a block: the range's whole blocks, and the block
         // of a wrapped neighbour outside it
-        constexpr int B = SF32B::kBlock;
+        constexpr int B = S::kBlock;
         const BlkRow<BX> br((int)rowoff, xb, w, nx);
         const int nb = (int)(br.span / 32);
-        const uint32_t bytes = (uint32_t)(nb + (br.spare_node >= 0 ? 1 : 0)) * B * (uint32_t)sizeof(float);
-        const size_t lim = 18 * (((size_t)N + 31) & ~(size_t)31);
+        const uint32_t bytes = (uint32_t)(nb + (br.spare_node >= 0 ? 1 : 0)) * B * (uint32_t)sizeof(T);
+        const size_t lim = (N + 31) / 32 * B;
         mbar_arrive_expect_tx(&R.full[s], bytes);
         bulk_g2s(R.f(s), copy_src(src.f, (size_t)(br.sbase / 32) * B, (size_t)nb * B, lim),
-                 (uint32_t)nb * B * sizeof(float), &R.full[s]);
+                 (uint32_t)nb * B * sizeof(T), &R.full[s]);
         if (br.spare_node >= 0)
           bulk_g2s(R.f(s) + (BlkRow<BX>::kSpare / 32) * B, copy_src(src.f, (size_t)(br.spare_node / 32) * B, B, lim),
-                   B * sizeof(float), &R.full[s]);
+                   B * sizeof(T), &R.full[s]);
         issued = k + 1;
         continue;
       }
@@ -348,6 +367,33 @@ __device__ __forceinline__ void push_node_blk(float* __restrict__ f, unsigned lo
     LB_GUARD((unsigned long long)base + 288 + 32 * di, lim, );
     f[base + 32 * di] = fs[i];
     f[base + 288 + 32 * di] = ge[i];
+  }
+}
+
+// The same for the FP16 block storage (SF16B; elements are halves, 608 per
+// block): f_i (deviations, stored as they are) 32 i from the node's start, g_i
+// (i >= 1) 288 + 32 (i - 1), and g_0, which stays at the node (direction 0 never
+// bounces back), at float self0 of the g_0 base.  lim: halves of the state.
+template <int MODEL>
+__device__ __forceinline__ void push_node_blk16(__half* __restrict__ f, float* __restrict__ g0, unsigned long long lim,
+                                                const uint32_t rpart[3], const uint32_t cpart[3], uint32_t self0,
+                                                const bool sol[3][3], bool bnd, const float fs[9], const float ge[9]) {
+  static_assert(MODEL == MODEL_BINARY, "the block storage holds the binary model");
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int ex = EXd(i), ey = EYd(i);
+    const bool back = bnd && sol[1 + ey][1 + ex];
+    const uint32_t base = back ? rpart[1] + cpart[1] : rpart[1 + ey] + cpart[1 + ex];
+    const int di = back ? OPPd(i) : i;
+    LB_GUARD((unsigned long long)base + 32 * di, lim, );
+    f[base + 32 * di] = __float2half_rn(fs[i]);
+    if (i == 0) {
+      LB_GUARD(self0, lim / 2 - SF16B::kG0, );
+      g0[self0] = ge[0];
+    } else {
+      LB_GUARD((unsigned long long)base + SF16B::kGOff + 32 * (di - 1), lim, );
+      f[base + SF16B::kGOff + 32 * (di - 1)] = __float2half_rn(ge[i]);
+    }
   }
 }
 
@@ -458,16 +504,25 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   // destination columns' block addresses
   constexpr bool BA = L::BLK && !UROWS;
   [[maybe_unused]] uint32_t cpart[3] = {0u, 0u, 0u};
+  [[maybe_unused]] uint32_t cpart0 = 0u;  // SF16B: this lane's g_0 float, less its row's part
+  [[maybe_unused]] unsigned long long blk_lim = 0;
   if constexpr (BA) {
+    constexpr int B = S::kBlock;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) cpart[i] = (uint32_t)(col[i] >> 5) * SF32B::kBlock + (uint32_t)(col[i] & 31);
+    for (int i = 0; i < 3; ++i) cpart[i] = (uint32_t)(col[i] >> 5) * B + (uint32_t)(col[i] & 31);
+    blk_lim = (unsigned long long)(N + 31) / 32 * B;
+    if constexpr (!std::is_same<S, SF32B>::value) cpart0 = (uint32_t)(x >> 5) * SF16B::kG0Stride + (uint32_t)(x & 31);
   }
-  [[maybe_unused]] const unsigned long long blk_lim = 18ull * ((N + 31) & ~31ull);
   auto push = [&](const int rowb[3], const bool sol[3][3], bool bnd, const A fs[9], const A ge[9]) {
     if constexpr (BA) {
-      const uint32_t rpart[3] = {(uint32_t)(rowb[0] >> 5) * SF32B::kBlock, (uint32_t)(rowb[1] >> 5) * SF32B::kBlock,
-                                 (uint32_t)(rowb[2] >> 5) * SF32B::kBlock};
-      push_node_blk<MODEL>(reinterpret_cast<float*>(dst.f), blk_lim, rpart, cpart, sol, bnd, fs, ge);
+      constexpr int B = S::kBlock;
+      const uint32_t rpart[3] = {(uint32_t)(rowb[0] >> 5) * B, (uint32_t)(rowb[1] >> 5) * B,
+                                 (uint32_t)(rowb[2] >> 5) * B};
+      if constexpr (std::is_same<S, SF32B>::value)
+        push_node_blk<MODEL>(reinterpret_cast<float*>(dst.f), blk_lim, rpart, cpart, sol, bnd, fs, ge);
+      else
+        push_node_blk16<MODEL>(dst.f, dst.g0, blk_lim, rpart, cpart,
+                               (uint32_t)(rowb[1] >> 5) * SF16B::kG0Stride + cpart0, sol, bnd, fs, ge);
     } else {
       push_node_u32<MODEL, S, RAW>(dst, N32, rowb, col, sol, bnd, fs, ge);
     }
@@ -592,10 +647,10 @@ __device__ __forceinline__ bool tile_all_solid(const Geom& G, int xb, int w, int
 }
 
 // Resident CTAs per SM the staged kernels are compiled for (caps their registers).
-// The block storage's stages are larger, so its rings set the count: as many CTAs
-// as the SM's 228 KB of shared memory holds (each with its 1 KB reservation), and
-// the registers that count leaves (96 per thread at 128 columns and 4 stages
-// instead of 72: 1 % faster on 16384 x 256).
+// For the block storages the count is what the SM's 228 KB of shared memory holds
+// (each CTA with its 1 KB reservation), but no more than leaves 72 registers per
+// thread: the FP32 blocks at 128 columns and 4 stages fit four CTAs, which gives
+// 96 registers instead of the 72 of a five-CTA bound (1 % faster on 16384 x 256).
 constexpr int tma_min_blocks(int bx, int ns) {
   return bx == 64 ? (ns > 4 ? 4 : 8) : (bx == 128 ? (ns > 4 ? 3 : 5) : (ns > 3 ? 2 : 3));
 }
@@ -603,7 +658,9 @@ template <int MODEL, class S, int BX, int NS>
 constexpr int tma_min_blocks_of() {
   using L = TmaLayout<MODEL, S, BX, NS>;
   if constexpr (L::BLK) {
-    constexpr int b = int(233472 / (L::BYTES + 1024));
+    constexpr int by_smem = int(233472 / (L::BYTES + 1024));
+    constexpr int by_regs = 65536 / ((BX + 32) * 72);
+    constexpr int b = by_smem < by_regs ? by_smem : by_regs;
     return b < 1 ? 1 : (b > 8 ? 8 : b);
   } else {
     return tma_min_blocks(BX, NS);

@@ -23,7 +23,7 @@ STATUS_NAMES = ["LB_OK", "LB_ERR_ARG", "LB_ERR_CUDA", "LB_ERR_NONFINITE", "LB_ER
                 "LB_ERR_STATE", "LB_ERR_NOMEM"]
 MODEL_LIQUID_GAS, MODEL_BINARY = 0, 1
 STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS = 0, 1, 2, 3
-STORAGE_MOMENTS_F16, STORAGE_F32_GELIM, STORAGE_F32_BLOCKED = 4, 5, 6
+STORAGE_MOMENTS_F16, STORAGE_F32_GELIM, STORAGE_F32_BLOCKED, STORAGE_F16_BLOCKED = 4, 5, 6, 7
 
 
 class LbError(RuntimeError):

@@ -118,6 +118,10 @@ def test_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
                                                        setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
         yield "block storage above 238609280 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 3641),
                                                                       setattr(p, "storage", lb.STORAGE_F32_BLOCKED))
+        yield "liquid-gas in FP16 blocks", lambda g, w, p: (setattr(p, "model", 0),
+                                                            setattr(p, "storage", lb.STORAGE_F16_BLOCKED))
+        yield "FP16 blocks above 226050880 nodes", lambda g, w, p: (setattr(g, "nx", 65536), setattr(g, "ny", 3450),
+                                                                    setattr(p, "storage", lb.STORAGE_F16_BLOCKED))
         yield "unknown storage", lambda g, w, p: setattr(p, "storage", 9)
         yield "tube longer than the grid", lambda g, w, p: setattr(w, "tube_len", 97)
         yield "band as tall as the grid", lambda g, w, p: setattr(w, "tube_h", 24)
@@ -176,6 +180,9 @@ def test_batch_create_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "block storage above 238609280 nodes": (lambda s: ([setattr(x[2], "storage", lb.STORAGE_F32_BLOCKED) for x in s],
                                                           setattr(s[1][0], "nx", 65536), setattr(s[1][0], "ny", 3641),
                                                           setattr(s[1][1], "tube_len", 0)), None),
+        "FP16 blocks above 226050880 nodes": (lambda s: ([setattr(x[2], "storage", lb.STORAGE_F16_BLOCKED) for x in s],
+                                                        setattr(s[1][0], "nx", 65536), setattr(s[1][0], "ny", 3450),
+                                                        setattr(s[1][1], "tube_len", 0)), None),
         "negative mobility": (setp(0, "M", -1.0), None),
         "viscosity table of one entry": (setp(1, "nu_table", 1), None),
         "tube longer than the grid": (lambda s: setattr(s[1][1], "tube_len", 200), None),
@@ -209,7 +216,7 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
     """lb_filled_length_noalloc checks its arguments on the host and returns LB_ERR_ARG
     before its first CUDA call (so this runs without a GPU; the device pointers below are
     never dereferenced): NULL pointers, block counts outside [1, LB_NOALLOC_MAX_BLOCKS],
-    the moment storage (it keeps no populations), the 32-node block storage (another layout), a liquid-gas lattice in FP16, a binary
+    the moment storage (it keeps no populations), the 32-node block storages (another layout), a liquid-gas lattice in FP16, a binary
     call without g, an FP16 call without g0, and liquid-gas densities that are not finite
     with rho_l > rho_g (its liquid fraction divides by rho_l - rho_g)."""
     import workloads as W
@@ -237,7 +244,8 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "too many blocks": call(binary, nblocks=2049),
         "moment storage": call(binary, storage=lb.STORAGE_MOMENTS),
         "block storage": call(binary, storage=lb.STORAGE_F32_BLOCKED),
-        "unknown storage": call(binary, storage=7),
+        "FP16 block storage": call(binary, storage=lb.STORAGE_F16_BLOCKED),
+        "unknown storage": call(binary, storage=8),
         "liquid-gas in FP16": call(lg, storage=lb.STORAGE_F16DEV),
         "binary without g": call(binary, g=None),
         "FP16 without g0": call(binary, g0=None, storage=lb.STORAGE_F16DEV),

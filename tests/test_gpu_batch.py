@@ -13,7 +13,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F64,  # noqa: E402
+from paper_0911_0459_gb300 import (STORAGE_F16_BLOCKED, STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED,  # noqa: E402
+                                   STORAGE_F64,
                                    STORAGE_MOMENTS, Batch,
                                    Lattice, LbError)
 from paper_0911_0459_gb300 import lb as lbmod  # noqa: E402
@@ -30,7 +31,8 @@ def small_sweep(seed=7, n=6, align=8, vary_gamma=False):
 
 
 @pytest.mark.parametrize("body", [1, 2, 3])
-@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F64, STORAGE_F16DEV])
+@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_F64, STORAGE_F16DEV,
+                                     STORAGE_F16_BLOCKED])
 def test_batch_is_bitwise_identical_to_independent_lattices(storage, body):
     """Every body of the persistent kernel (sliding window; staged with the
     shallow and the deep ring) against one lattice per capillary, over tiles
@@ -126,14 +128,16 @@ def test_batch_with_unaligned_rows_uses_the_sliding_window_body():
     b.close()
 
 
+@pytest.mark.parametrize("blocked,planar", [(STORAGE_F32_BLOCKED, STORAGE_F32), (STORAGE_F16_BLOCKED, STORAGE_F16DEV)])
 @pytest.mark.parametrize("body", [1, 2, 3])
-def test_block_storage_batch_with_unaligned_rows_equals_fp32_lattices(body):
-    """The 32-node block storage stages whole blocks at any nx, so a batch of lattices
-    whose rows start inside blocks runs the staged body too; every lattice equals the
-    planar FP32 storage run alone, bit for bit (the same arithmetic)."""
+def test_block_storage_batch_with_unaligned_rows_equals_planar_lattices(body, blocked, planar):
+    """The 32-node block storages stage whole blocks at any nx, so a batch of lattices
+    whose rows start inside blocks runs the staged body too; every lattice equals its
+    planar storage (FP32, or the FP16 deviations) run alone, bit for bit (the same
+    arithmetic)."""
     caps = small_sweep(seed=9, n=4, align=1)
     assert any(c.nx % 32 for c in caps)
-    b = Batch(caps, storage=STORAGE_F32_BLOCKED)
+    b = Batch(caps, storage=blocked)
     assert b.kernel() == 2
     b.set_kernel(body)
     for tx, ty in ((64, 4), (128, 16), (256, 64), (128, 5)):
@@ -141,7 +145,7 @@ def test_block_storage_batch_with_unaligned_rows_equals_fp32_lattices(body):
         b.step(11)
     red = b.lengths()
     for i, c in enumerate(caps):
-        lat = Lattice.from_workload(c, storage=STORAGE_F32)
+        lat = Lattice.from_workload(c, storage=planar)
         lat.step(b.time)
         fb, gb = b.populations(i, rested=False)
         fl, gl = lat.populations(rested=False)

@@ -4,7 +4,7 @@ In that build every global load and store of the step kernels checks its index a
 its buffer; an index outside would be counted and skipped.  Small lattices of every
 model and storage run through every step kernel (the staged and the sliding-window
 population kernels with both ring depths, on the planar storages and on the 32-node
-block storage with aligned and unaligned rows, the pull kernel of the reduced states) and
+block storages (FP32 and FP16) with aligned and unaligned rows, the pull kernel of the reduced states) and
 through the batch bodies, in a child process that loads the checked library; every
 counter must stay at zero, and the states must equal bit for bit those of the normal
 build (the checks change nothing for accesses inside their buffers)."""
@@ -59,8 +59,9 @@ for st in (0, 1, 2):             # FP64, FP32, FP16 deviations: sliding window, 
 cap96 = W.Capillary("c9", 96, 24, 24, 64, 3, 18, 8, 6, bp, theta_deg=45.0)       # nx % 32 == 0
 tail = W.Capillary("ct", 513, 9, 100, 300, 1, 6, 20, 10, bp, wall_grad=-0.1)      # one-column last tile
 for nm, c in (("c96", cap96), ("cw", capw), ("cr", capr), ("nw", narrow), ("ct", tail)):
-    # FP32 in 32-node blocks: aligned and unaligned rows, every kernel variant
+    # FP32 and FP16 in 32-node blocks: aligned and unaligned rows, every kernel variant
     lattice(f"blk_{nm}", c, 6, (1, 2, 3), tiles)
+    lattice(f"blk16_{nm}", c, 7, (1, 2, 3), tiles)
 for st in (3, 4, 5):             # the pull kernel's reduced states
     for nm, c in (("c8", cap8), ("cw", capw), ("cr", capr), ("nw", narrow)):
         lattice(f"pull{st}_{nm}", c, st, (4,), tiles)
@@ -85,6 +86,15 @@ for v in (2, 3):
     b.step(7)
 out["batch_f32_staged"] = {"check": b.check_report(), "state": digest(b.save_state()[0])}
 b.close()
+for st, key in ((6, "batch_blk32"), (7, "batch_blk16")):   # block storages: staged at any nx
+    b = Batch(caps + [capr], storage=st)
+    for v in (1, 2, 3):
+        b.set_kernel(v)
+        b.set_tile(128, 16)
+        b.step(7)
+    b.run_sampled([3, 9])
+    out[key] = {"check": b.check_report(), "state": digest(b.save_state()[0])}
+    b.close()
 print(json.dumps(out))
 '''
 

@@ -16,7 +16,8 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_0911_0459_gb300 import (STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_GELIM, STORAGE_F64,  # noqa: E402
+from paper_0911_0459_gb300 import (STORAGE_F16_BLOCKED, STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED,  # noqa: E402
+                                   STORAGE_F32_GELIM, STORAGE_F64,
                                    STORAGE_MOMENTS, STORAGE_MOMENTS_F16, Batch, Lattice, LbError)
 
 
@@ -26,7 +27,8 @@ def capillary(storage):
 
 
 @pytest.mark.parametrize("storage", [STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS,
-                                     STORAGE_MOMENTS_F16, STORAGE_F32_GELIM])
+                                     STORAGE_MOMENTS_F16, STORAGE_F32_GELIM, STORAGE_F32_BLOCKED,
+                                     STORAGE_F16_BLOCKED])
 def test_lattice_checkpoint_resumes_bit_for_bit(storage, tmp_path):
     cap = capillary(storage)
     a = Lattice.from_workload(cap)

@@ -29,7 +29,7 @@ import numpy as np
 
 LG, BINARY = 0, 1
 STORAGE_F64, STORAGE_F32, STORAGE_F16DEV, STORAGE_MOMENTS = 0, 1, 2, 3
-STORAGE_MOMENTS_F16, STORAGE_F32_GELIM, STORAGE_F32_BLOCKED = 4, 5, 6
+STORAGE_MOMENTS_F16, STORAGE_F32_GELIM, STORAGE_F32_BLOCKED, STORAGE_F16_BLOCKED = 4, 5, 6, 7
 
 
 @dataclasses.dataclass
