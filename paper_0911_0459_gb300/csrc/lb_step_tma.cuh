@@ -13,8 +13,8 @@
 //     the planar ring;
 //   - BX/32 consumer warps work independently: each keeps rho/phi of rows
 //     y-1, y, y+1 for its 32 columns in registers, takes the neighbouring
-//     columns by warp shuffles (its edge lanes sum the halo columns from the
-//     stage themselves), collides row y from the stage and pushes the result to
+//     columns by warp shuffles (eight of its lanes share the sums of the two halo
+//     columns), collides row y from the stage and pushes the result to
 //     global memory, then arrives on the stage's "empty" mbarrier;
 //   - a consumer warp keeps the populations of a row in registers from the
 //     moment it sums that row, so it releases the stage right away; the
@@ -54,6 +54,11 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// A staged value in the arithmetic type.
+__device__ __forceinline__ float stage_val(float v) { return v; }
+__device__ __forceinline__ double stage_val(double v) { return v; }
+__device__ __forceinline__ float stage_val(__half v) { return __half2float(v); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -435,12 +440,37 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   struct Row {
     A rc, rl, rr, pc, pl, pr;
   };
-  // extra column summed by the edge lanes: left neighbour of lane 0, right of lane 31
+  // extra column of the edge lanes: left neighbour of lane 0, right of lane 31
   const int sx = lane == 0 ? sc - 1 : sc + 1;
-  const bool edge = lane == 0 || lane == 31;
-  // Sum this lane's column (f, g keep its populations for the collision); the edge
-  // lanes also sum the warp's halo column; then take the neighbours by shuffles.
-  // A row solid under all the warp's columns (skip) is left unread.
+  // One value of a staged row for the halo sums: population i >= 1 of f (isg false)
+  // or g (isg true) at stage column c, addressed so that f and g take one load.
+  auto halo_val = [&](int s, int c, bool isg, int i) -> A {
+    if constexpr (L::BLK) {
+      // g_i lies where f_{i+9} (FP32 blocks: g_0 first) or f_{i+8} (FP16 blocks) would
+      constexpr int GI = std::is_same<S, SF32B>::value ? 9 : 8;
+      return stage_val(R.f(s)[(c >> 5) * S::kBlock + 32 * (i + (isg ? GI : 0)) + (c & 31)]);
+    } else {
+      constexpr int GS = L::NG == 8 ? 1 : 0;  // planar FP16: g_1..g_8 in planes 0..7
+      const typename S::T* b = isg ? R.g(s) - GS * W : R.f(s);
+      return stage_val(b[i * W + c]);
+    }
+  };
+  // population 0 of f or g (the FP16 storages keep g_0 in FP32 apart)
+  auto halo_val0 = [&](int s, int c, bool isg) -> A {
+    if constexpr (dev_arith<S>::value)
+      return isg ? S::pg(R.g(s), R.g0(s), W, c, 0) : S::pfr(R.f(s), W, c, 0);
+    else if constexpr (L::BLK)
+      return stage_val(R.f(s)[(c >> 5) * S::kBlock + (isg ? 32 * 9 : 0) + (c & 31)]);
+    else
+      return stage_val((isg ? R.g(s) : R.f(s))[c]);
+  };
+  // Sum this lane's column (f, g keep its populations for the collision), and the
+  // warp's two halo columns: lanes 0..7 each take half of one of the four 9-value
+  // sums (f or g of the left or the right column; lane 2k values 1..4 and value 0,
+  // lane 2k + 1 values 5..8), in sum9's order, so that the halo sums equal the sums
+  // the neighbouring warp or kernel forms for those nodes bit for bit; then take
+  // the neighbours by shuffles.  A row solid under all the warp's columns (skip) is
+  // left unread.
   // Block storage with rows that start inside a block: this lane's stage columns
   // (own node, edge column) in the row of lattice row yr.  Elsewhere they are sc, sx.
   constexpr bool BR = L::BLK && UROWS;
@@ -466,13 +496,24 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     load_pop(s, co, f, g);
     const A r = sum9(f);
     const A p = BIN ? sum9(g) : A(0);
-    A re = A(0), pe = A(0);
-    if (edge) {
-      A fe[9], ge[9];
-      load_pop(s, ce, fe, ge);
-      re = sum9(fe);
-      pe = BIN ? sum9(ge) : A(0);
+    int cl = warp * 32 + L::HALO - 1, cr = warp * 32 + L::HALO + 32;  // the halo columns
+    if constexpr (BR) {
+      cl = __shfl_sync(0xffffffffu, ce, 0);
+      cr = __shfl_sync(0xffffffffu, ce, 31);
     }
+    const bool isg = (lane >> 1) & 1;
+    const bool part = lane < 8 && (BIN || !isg);
+    const int hc = lane < 4 ? cl : cr;
+    const int i0 = (lane & 1) ? 5 : 1;
+    A h = A(0);
+    if (part)
+      h = (halo_val(s, hc, isg, i0) + halo_val(s, hc, isg, i0 + 1)) +
+          (halo_val(s, hc, isg, i0 + 2) + halo_val(s, hc, isg, i0 + 3));
+    const A h2 = __shfl_down_sync(0xffffffffu, h, 1);
+    A t = A(0);
+    if (part && !(lane & 1)) t = halo_val0(s, hc, isg) + (h + h2);
+    const A re = __shfl_sync(0xffffffffu, t, lane == 31 ? 4 : 0);
+    const A pe = BIN ? __shfl_sync(0xffffffffu, t, lane == 31 ? 6 : 2) : A(0);
     const A rl = __shfl_up_sync(0xffffffffu, r, 1), rr = __shfl_down_sync(0xffffffffu, r, 1);
     Rw.rc = r;
     Rw.rl = lane == 0 ? re : rl;
