@@ -96,10 +96,10 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
  * LB_STORAGE_F32_BLOCKED (binary model only) keeps the eighteen FP32
  * populations, with the values and arithmetic of LB_STORAGE_F32 (the two give
  * identical results), in blocks of 32 consecutive nodes n = y nx + x: block
- * b = n / 32 holds f_0..f_8 and then g_0..g_8 of its nodes, 32 consecutive
- * values per population, so f_i of node n is float element
- * 576 b + 32 i + n % 32 of the state and g_i is 288 elements further; the last
- * block is padded, so the state holds 18 * 32 * ceil(nx ny / 32) floats
+ * b = n / 32 holds, for i = 0..8, the pairs (f_i, g_i) of its 32 nodes in node
+ * order, so f_i of node n is float element 576 b + 64 i + 2 (n % 32) of the
+ * state and g_i the element after it; the last block is padded, so the state
+ * holds 18 * 32 * ceil(nx ny / 32) floats
  * (lb_save_state writes this layout).  A row of a tile with its neighbour
  * columns is then one contiguous range of blocks, which the staged step kernel
  * fetches with one bulk copy per row (plus one block at an x-wrap) instead of one
@@ -109,10 +109,11 @@ typedef enum { LB_MODEL_LIQUID_GAS = 0, LB_MODEL_BINARY = 1 } lb_model;
  * LB_STORAGE_F16_BLOCKED (binary model only) keeps the values of
  * LB_STORAGE_F16DEV (FP16 f_i - w_i rho0 and g_1..g_8, FP32 g_0; the two give
  * identical results) in blocks of 32 consecutive nodes: block b = n / 32 is
- * 1216 bytes, f_0..f_8 less the offsets (FP16, 32 values each), then g_1..g_8
- * (FP16), then g_0 (FP32), so f_i of node n is half element 608 b + 32 i + n % 32
- * of the state, g_i (i >= 1) half 608 b + 288 + 32 (i - 1) + n % 32 and g_0
- * float 304 b + 272 + n % 32; the last block is padded (the state is
+ * 1216 bytes: f_0 less its offset (FP16, 32 values), then for i = 1..8 the pairs
+ * (f_i less its offset, g_i) of the 32 nodes (FP16), then g_0 (FP32), so f_0 of
+ * node n is half element 608 b + n % 32 of the state, f_i (i >= 1) half
+ * 608 b + 32 + 64 (i - 1) + 2 (n % 32), g_i the half after it and g_0 float
+ * 304 b + 272 + n % 32; the last block is padded (the state is
  * 1216 ceil(nx ny / 32) bytes; lb_save_state writes this layout).  One bulk copy
  * per staged row, as for LB_STORAGE_F32_BLOCKED; any nx.  At most 226050880 nodes
  * (19 * 32 * ceil(nx ny / 32) < 2^32). */

@@ -148,11 +148,11 @@ static OpArgs lattice_args(const lb_batch* b, int i, int k) {
   const size_t el = elem_size(b->storage);
   OpBufs ob;
   ob.f = (char*)b->f[k] + b->off_f[i] * el;
-  ob.g = b->storage == LB_STORAGE_F32_BLOCKED ? (char*)ob.f + 288 * el  // g beside f in every block
+  ob.g = b->storage == LB_STORAGE_F32_BLOCKED ? (char*)ob.f + el  // g_i after f_i in every block
                                               : (b->g[k] ? (char*)b->g[k] + b->off_g[i] * el : NULL);
   ob.g0 = b->g0[k] ? b->g0[k] + b->off_g0[i] : NULL;
-  if (b->storage == LB_STORAGE_F16_BLOCKED) {  // g_1..g_8 at byte 576 and g_0 at byte 1088 of every block
-    ob.g = (char*)ob.f + 576;
+  if (b->storage == LB_STORAGE_F16_BLOCKED) {  // g_i after f_i, g_0 at byte 1088 of every block
+    ob.g = (char*)ob.f + 2;
     ob.g0 = (float*)((char*)ob.f + 1088);
   }
   a.src = ob;

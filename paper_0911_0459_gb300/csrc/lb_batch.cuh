@@ -90,9 +90,9 @@ struct BatchArgs {
 template <class S>
 __device__ __forceinline__ Buf<S> cap_buf(typename S::T* f, typename S::T* g, float* g0,
                                           const CapDesc<typename S::A>& c) {
-  if constexpr (std::is_same<S, SF32B>::value)  // g beside f in every 32-node block
-    return Buf<S>{f + c.off_f, f + c.off_f + SF32B::kBlock / 2, nullptr, c.r};
-  if constexpr (std::is_same<S, SF16B>::value)  // g_1..g_8 and g_0 inside every 32-node block
+  if constexpr (std::is_same<S, SF32B>::value)  // g_i after f_i in every 32-node block
+    return Buf<S>{f + c.off_f, f + c.off_f + SF32B::kGOff, nullptr, c.r};
+  if constexpr (std::is_same<S, SF16B>::value)  // g_i after f_i, g_0 apart, in every 32-node block
     return Buf<S>{f + c.off_f, f + c.off_f + SF16B::kGOff, reinterpret_cast<float*>(f + c.off_f) + SF16B::kG0, c.r};
   return Buf<S>{f + c.off_f, g ? g + c.off_g : nullptr, g0 ? g0 + c.off_g0 : nullptr, c.r};
 }

@@ -355,10 +355,11 @@ lb_status lb_create(const lb_grid* grid, const lb_walls* walls, const lb_params*
     c->buf[k].g = gb ? dev_alloc_owned(c, gb) : NULL;
     c->buf[k].g0 = g0b ? (float*)dev_alloc_owned(c, g0b) : NULL;
     // the block storage keeps g beside f in every block
-    if (params->storage == LB_STORAGE_F32_BLOCKED && c->buf[k].f) c->buf[k].g = (float*)c->buf[k].f + 288;
-    // the FP16 block storage: g_1..g_8 at byte 576 and g_0 at byte 1088 of every block
+    // the block storages: g_i is the element after f_i; the FP16 blocks keep g_0 at
+    // byte 1088 of every block
+    if (params->storage == LB_STORAGE_F32_BLOCKED && c->buf[k].f) c->buf[k].g = (float*)c->buf[k].f + 1;
     if (params->storage == LB_STORAGE_F16_BLOCKED && c->buf[k].f) {
-      c->buf[k].g = (char*)c->buf[k].f + 576;
+      c->buf[k].g = (char*)c->buf[k].f + 2;
       c->buf[k].g0 = (float*)((char*)c->buf[k].f + 1088);
     }
     if (!c->buf[k].f || (gb && !c->buf[k].g) || (g0b && !c->buf[k].g0)) {

@@ -274,28 +274,36 @@ struct SF16 {
 };
 
 // FP32 populations of the binary model in blocks of 32 consecutive nodes: block
-// b = n / 32 holds f_0..f_8 and then g_0..g_8 of its nodes, each population as 32
-// consecutive values, so f_i of node n is element 576 b + 32 i + n % 32 of the
-// buffer and g_i lies 288 elements further (Buf::g = Buf::f + 288).  With
-// nx % 32 == 0 the nodes of a row segment of whole blocks, all eighteen
-// populations, are one contiguous range, which the staged step kernel copies
-// with a single bulk copy per row (other widths: the whole blocks over the
-// segment, and one more block at an x-wrap).  The last block is padded to 32
-// nodes.  Same values and arithmetic as SF32.
+// b = n / 32 holds, for i = 0..8, the pairs (f_i, g_i) of its 32 nodes in node
+// order, so f_i of node n is element 576 b + 64 i + 2 (n % 32) of the buffer and
+// g_i the element after it (Buf::g = Buf::f + 1).  A node's f_i and g_i always
+// stream to the same destination and direction, so the step kernels load and
+// store them as one 8-byte pair.  With nx % 32 == 0 the nodes of a row segment
+// of whole blocks, all eighteen populations, are one contiguous range, which the
+// staged step kernel copies with a single bulk copy per row (other widths: the
+// whole blocks over the segment, and one more block at an x-wrap).  The last
+// block is padded to 32 nodes.  Same values and arithmetic as SF32.
 struct SF32B {
   using T = float;
   using A = float;
   static constexpr int kBlock = 576;       // elements per block of 32 nodes
   static constexpr int kBlockBytes = 2304;
-  static constexpr int kGOff = 288;        // elements from a block's f_0 to its g_1 (g_0 here)
-  static constexpr int kG0 = 0;            // (g_0 lies among the g elements)
-  __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
-  __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  static constexpr int kGOff = 1;          // g_i is the element after f_i
+  static constexpr int kG0 = 0;            // (g_0 pairs with f_0)
+  __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 64 * i + 2 * (n & 31); }
+  __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 64 * i + 2 * (n & 31); }
   // elements of a state of N nodes (the last block padded)
   __device__ static unsigned long long lim(unsigned long long N) { return 18ull * ((N + 31) & ~31ull); }
   // shared-memory stage of whole blocks: stage column c lies in block c / 32
-  __device__ static A pf(const T* f, int, int c, int i, const Rest&) { return f[(c >> 5) * kBlock + 32 * i + (c & 31)]; }
-  __device__ static A pg(const T* g, const float*, int, int c, int i) { return g[(c >> 5) * kBlock + 32 * i + (c & 31)]; }
+  __device__ static int sat(int c, int i) { return (c >> 5) * kBlock + 64 * i + 2 * (c & 31); }
+  __device__ static A pf(const T* f, int, int c, int i, const Rest&) { return f[sat(c, i)]; }
+  __device__ static A pg(const T* g, const float*, int, int c, int i) { return g[sat(c, i)]; }
+  // the pair (f_i, g_i) of stage column c in one load (f: the stage's f base)
+  __device__ static void pfg(const T* f, const float*, int c, int i, A& fv, A& gv) {
+    const float2 v = *reinterpret_cast<const float2*>(f + sat(c, i));
+    fv = v.x;
+    gv = v.y;
+  }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest&) {
     LB_GUARD(at(n, i), lim(N), A(0));
     return __ldg(f + at(n, i));
@@ -305,11 +313,11 @@ struct SF32B {
     f[at(n, i)] = v;
   }
   __device__ static A lg(const T* __restrict__ g, const float* __restrict__, size_t N, size_t n, int i) {
-    LB_GUARD(at(n, i), lim(N) - 288, A(0));
+    LB_GUARD(at(n, i), lim(N) - 1, A(0));
     return __ldg(g + at(n, i));
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__, size_t N, size_t n, int i, A v) {
-    LB_GUARD(at(n, i), lim(N) - 288, );
+    LB_GUARD(at(n, i), lim(N) - 1, );
     g[at(n, i)] = v;
   }
   __device__ static A lfc(const T* f, size_t N, size_t n, int i, const Rest&) {
@@ -317,16 +325,16 @@ struct SF32B {
     return __ldcg(f + at(n, i));
   }
   __device__ static A lgc(const T* g, const float*, size_t N, size_t n, int i) {
-    LB_GUARD(at(n, i), lim(N) - 288, A(0));
+    LB_GUARD(at(n, i), lim(N) - 1, A(0));
     return __ldcg(g + at(n, i));
   }
-  // 32-bit element offsets (needs 18 N < 2^32)
+  // 32-bit element offsets (needs 18 * 32 * ceil(N / 32) < 2^32)
   __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest&) {
     LB_GUARD(at32(n, i), lim(N), );
     f[at32(n, i)] = v;
   }
   __device__ static void sgo(T* __restrict__ g, float* __restrict__, uint32_t N, uint32_t n, int i, A v) {
-    LB_GUARD(at32(n, i), lim(N) - 288, );
+    LB_GUARD(at32(n, i), lim(N) - 1, );
     g[at32(n, i)] = v;
   }
   __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
@@ -336,35 +344,43 @@ struct SF32B {
 };
 
 // The FP16 deviations of SF16 in blocks of 32 consecutive nodes: block b = n / 32
-// is 1216 bytes (608 halves): f_0..f_8 less the rest offsets (FP16, 32 values
-// each), then g_1..g_8 (FP16), then g_0 (FP32, 32 values at byte 1088).  So f_i of
-// node n is half 608 b + 32 i + n % 32 of the buffer, g_i (i >= 1) half
-// 608 b + 288 + 32 (i - 1) + n % 32 (Buf::g = Buf::f + 288 halves) and g_0 float
+// is 1216 bytes (608 halves): f_0 - w_0 of its 32 nodes (FP16, halves 0..31), then
+// for i = 1..8 the pairs (f_i - w_i, g_i) of its nodes in node order (FP16,
+// halves 32..543), then g_0 (FP32, floats 272..303).  So f_i of node n is half
+// 608 b + n % 32 (i = 0) or 608 b + 32 + 64 (i - 1) + 2 (n % 32) (i >= 1) of the
+// buffer, g_i (i >= 1) the half after it (Buf::g = Buf::f + 1 half) and g_0 float
 // 304 b + 272 + n % 32 (Buf::g0 = Buf::f + 1088 bytes).  A row segment of whole
 // blocks is again one contiguous range, which the staged kernel copies with one
-// bulk copy per row.  The last block is padded to 32 nodes.  Same values and
-// arithmetic as SF16.
+// bulk copy per row, and the pairs take one 4-byte load or store.  The last
+// block is padded to 32 nodes.  Same values and arithmetic as SF16.
 struct SF16B {
   using T = __half;
   using A = float;
   static constexpr int kBlock = 608;       // halves per block of 32 nodes
   static constexpr int kBlockBytes = 1216;
-  static constexpr int kGOff = 288;        // halves from a block's f_0 to its g_1
+  static constexpr int kGOff = 1;          // g_i (i >= 1) is the half after f_i
   static constexpr int kG0 = 272;          // floats from a block's start to its g_0
   static constexpr int kG0Stride = 304;    // floats per block
-  __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
-  __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + 32 * i + (n & 31); }
+  __device__ static int off(int r, int i) { return i == 0 ? r : 32 + 64 * (i - 1) + 2 * r; }
+  __device__ static size_t at(size_t n, int i) { return (n >> 5) * kBlock + off((int)(n & 31), i); }
+  __device__ static uint32_t at32(uint32_t n, int i) { return (n >> 5) * kBlock + off((int)(n & 31), i); }
   __device__ static size_t at0(size_t n) { return (n >> 5) * kG0Stride + (n & 31); }
   // halves of a state of N nodes (the last block padded)
   __device__ static unsigned long long lim(unsigned long long N) { return 19ull * ((N + 31) & ~31ull); }
   __device__ static unsigned long long lim0(unsigned long long N) { return lim(N) / 2 - kG0; }
   // shared-memory stage of whole blocks: stage column c lies in block c / 32
-  __device__ static A pf(const T* f, int, int c, int i, const Rest& r) {
-    return __half2float(f[(c >> 5) * kBlock + 32 * i + (c & 31)]) + rest_w(r, i);
-  }
-  __device__ static A pfr(const T* f, int, int c, int i) { return __half2float(f[(c >> 5) * kBlock + 32 * i + (c & 31)]); }
+  __device__ static int sat(int c, int i) { return (c >> 5) * kBlock + off(c & 31, i); }
+  __device__ static A pf(const T* f, int, int c, int i, const Rest& r) { return __half2float(f[sat(c, i)]) + rest_w(r, i); }
+  __device__ static A pfr(const T* f, int, int c, int i) { return __half2float(f[sat(c, i)]); }
   __device__ static A pg(const T* g, const float* g0, int, int c, int i) {
-    return i == 0 ? g0[(c >> 5) * kG0Stride + (c & 31)] : __half2float(g[(c >> 5) * kBlock + 32 * (i - 1) + (c & 31)]);
+    return i == 0 ? g0[(c >> 5) * kG0Stride + (c & 31)] : __half2float(g[sat(c, i)]);
+  }
+  // the pair (f_i - w_i, g_i), i >= 1, of stage column c in one load (f: the
+  // stage's f base)
+  __device__ static void pfg(const T* f, const float*, int c, int i, A& fv, A& gv) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(f + sat(c, i)));
+    fv = v.x;
+    gv = v.y;
   }
   __device__ static A lf(const T* __restrict__ f, size_t N, size_t n, int i, const Rest& r) {
     LB_GUARD(at(n, i), lim(N), A(0));
@@ -395,16 +411,16 @@ struct SF16B {
       LB_GUARD(at0(n), lim0(N), A(0));
       return __ldg(g0 + at0(n));
     }
-    LB_GUARD(at(n, i - 1), lim(N) - kGOff, A(0));
-    return __half2float(__ldg(g + at(n, i - 1)));
+    LB_GUARD(at(n, i), lim(N) - kGOff, A(0));
+    return __half2float(__ldg(g + at(n, i)));
   }
   __device__ static A lgc(const T* g, const float* g0, size_t N, size_t n, int i) {
     if (i == 0) {
       LB_GUARD(at0(n), lim0(N), A(0));
       return __ldcg(g0 + at0(n));
     }
-    LB_GUARD(at(n, i - 1), lim(N) - kGOff, A(0));
-    return __half2float(__ldcg(g + at(n, i - 1)));
+    LB_GUARD(at(n, i), lim(N) - kGOff, A(0));
+    return __half2float(__ldcg(g + at(n, i)));
   }
   __device__ static void sg(T* __restrict__ g, float* __restrict__ g0, size_t N, size_t n, int i, A v) {
     if (i == 0) {
@@ -412,8 +428,8 @@ struct SF16B {
       g0[at0(n)] = v;
       return;
     }
-    LB_GUARD(at(n, i - 1), lim(N) - kGOff, );
-    g[at(n, i - 1)] = __float2half_rn(v);
+    LB_GUARD(at(n, i), lim(N) - kGOff, );
+    g[at(n, i)] = __float2half_rn(v);
   }
   // 32-bit element offsets (needs 19 * 32 * ceil(N / 32) < 2^32)
   __device__ static void sfo(T* __restrict__ f, uint32_t N, uint32_t n, int i, A v, const Rest& r) {
@@ -431,8 +447,8 @@ struct SF16B {
       g0[o] = v;
       return;
     }
-    LB_GUARD(at32(n, i - 1), lim(N) - kGOff, );
-    g[at32(n, i - 1)] = __float2half_rn(v);
+    LB_GUARD(at32(n, i), lim(N) - kGOff, );
+    g[at32(n, i)] = __float2half_rn(v);
   }
   __device__ static void zf(T* __restrict__ f, size_t N, size_t n, int i) {
     LB_GUARD(at(n, i), lim(N), );

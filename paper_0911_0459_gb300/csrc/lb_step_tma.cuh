@@ -353,11 +353,13 @@ __device__ void drain_ring(const Ring<MODEL, S, BX, NS>& R, unsigned issued) {
 // Consumer warp `warp` (0 .. BX/32 - 1): collide rows y0 .. y1 - 1 of the tile
 // from ring rows kbase, kbase + 1, ... and push the results to dst.  Returns
 // false (in every lane of the warp) if a wait ran out of time.
-// Push streaming into the block storage when rows start on block boundaries
-// (nx % 32 == 0): node (x, y)'s populations start at rpart(y) + cpart(x), with
-// rpart = (y nx / 32) * 576 and cpart = (x / 32) * 576 + x % 32, so that every
-// destination costs one add; f_i lies 32 i further and g_i 288 + 32 i.  Bounce-back
-// as in push_node_u32.  lim: elements of the state.
+// Push streaming into the block storages when rows start on block boundaries
+// (nx % 32 == 0): node (x, y)'s pair addresses start at rpart(y) + cpart(x), with
+// rpart = (y nx / 32) * (elements per block) and cpart = (x / 32) * (elements per
+// block) + 2 (x % 32), so that every destination costs one add.  FP32 blocks
+// (SF32B): the pair (f_i, g_i) lies 64 i further and goes out as one 8-byte
+// store.  Bounce-back as in push_node_u32: f_i and g_i always share their
+// destination and direction.  lim: elements of the state.
 template <int MODEL>
 __device__ __forceinline__ void push_node_blk(float* __restrict__ f, unsigned long long lim, const uint32_t rpart[3],
                                               const uint32_t cpart[3], const bool sol[3][3], bool bnd,
@@ -369,36 +371,34 @@ __device__ __forceinline__ void push_node_blk(float* __restrict__ f, unsigned lo
     const bool back = bnd && sol[1 + ey][1 + ex];
     const uint32_t base = back ? rpart[1] + cpart[1] : rpart[1 + ey] + cpart[1 + ex];
     const int di = back ? OPPd(i) : i;
-    LB_GUARD((unsigned long long)base + 288 + 32 * di, lim, );
-    f[base + 32 * di] = fs[i];
-    f[base + 288 + 32 * di] = ge[i];
+    LB_GUARD((unsigned long long)base + 64 * di + 1, lim, );
+    *reinterpret_cast<float2*>(f + base + 64 * di) = make_float2(fs[i], ge[i]);
   }
 }
 
 // The same for the FP16 block storage (SF16B; elements are halves, 608 per
-// block): f_i (deviations, stored as they are) 32 i from the node's start, g_i
-// (i >= 1) 288 + 32 (i - 1), and g_0, which stays at the node (direction 0 never
-// bounces back), at float self0 of the g_0 base.  lim: halves of the state.
+// block): the pair (f_i - w_i, g_i), i >= 1, lies 32 + 64 (i - 1) from the node's
+// pair start and goes out as one 4-byte store of two halves; f_0 (at self_f0)
+// and g_0 (the FP32 float self_g0 of the g_0 base) stay at the node (direction 0
+// never bounces back).  lim: halves of the state.
 template <int MODEL>
 __device__ __forceinline__ void push_node_blk16(__half* __restrict__ f, float* __restrict__ g0, unsigned long long lim,
-                                                const uint32_t rpart[3], const uint32_t cpart[3], uint32_t self0,
-                                                const bool sol[3][3], bool bnd, const float fs[9], const float ge[9]) {
+                                                const uint32_t rpart[3], const uint32_t cpart[3], uint32_t self_f0,
+                                                uint32_t self_g0, const bool sol[3][3], bool bnd, const float fs[9],
+                                                const float ge[9]) {
   static_assert(MODEL == MODEL_BINARY, "the block storage holds the binary model");
+  LB_GUARD(self_f0, lim, );
+  f[self_f0] = __float2half_rn(fs[0]);
+  LB_GUARD(self_g0, lim / 2 - SF16B::kG0, );
+  g0[self_g0] = ge[0];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
+  for (int i = 1; i < 9; ++i) {
     const int ex = EXd(i), ey = EYd(i);
     const bool back = bnd && sol[1 + ey][1 + ex];
     const uint32_t base = back ? rpart[1] + cpart[1] : rpart[1 + ey] + cpart[1 + ex];
     const int di = back ? OPPd(i) : i;
-    LB_GUARD((unsigned long long)base + 32 * di, lim, );
-    f[base + 32 * di] = __float2half_rn(fs[i]);
-    if (i == 0) {
-      LB_GUARD(self0, lim / 2 - SF16B::kG0, );
-      g0[self0] = ge[0];
-    } else {
-      LB_GUARD((unsigned long long)base + SF16B::kGOff + 32 * (di - 1), lim, );
-      f[base + SF16B::kGOff + 32 * (di - 1)] = __float2half_rn(ge[i]);
-    }
+    LB_GUARD((unsigned long long)base + 32 + 64 * (di - 1) + 1, lim, );
+    *reinterpret_cast<__half2*>(f + base + 32 + 64 * (di - 1)) = __floats2half2_rn(fs[i], ge[i]);
   }
 }
 
@@ -423,6 +423,18 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   const int sc = x - xb + L::HALO;    // stage column of this lane's node
 
   auto load_pop = [&](int s, int c, A f[9], A g[9]) {
+    if constexpr (L::BLK) {
+      // the block storages keep (f_i, g_i) as adjacent pairs: one load each
+      if constexpr (std::is_same<S, SF32B>::value) {
+        S::pfg(R.f(s), nullptr, c, 0, f[0], g[0]);
+      } else {
+        f[0] = S::pfr(R.f(s), W, c, 0);
+        g[0] = S::pg(R.g(s), R.g0(s), W, c, 0);
+      }
+#pragma unroll
+      for (int i = 1; i < 9; ++i) S::pfg(R.f(s), nullptr, c, i, f[i], g[i]);
+      return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       if constexpr (RAW)
@@ -446,9 +458,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   // or g (isg true) at stage column c, addressed so that f and g take one load.
   auto halo_val = [&](int s, int c, bool isg, int i) -> A {
     if constexpr (L::BLK) {
-      // g_i lies where f_{i+9} (FP32 blocks: g_0 first) or f_{i+8} (FP16 blocks) would
-      constexpr int GI = std::is_same<S, SF32B>::value ? 9 : 8;
-      return stage_val(R.f(s)[(c >> 5) * S::kBlock + 32 * (i + (isg ? GI : 0)) + (c & 31)]);
+      return stage_val(R.f(s)[S::sat(c, i) + (isg ? 1 : 0)]);  // g_i follows f_i
     } else {
       constexpr int GS = L::NG == 8 ? 1 : 0;  // planar FP16: g_1..g_8 in planes 0..7
       const typename S::T* b = isg ? R.g(s) - GS * W : R.f(s);
@@ -460,7 +470,7 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
     if constexpr (dev_arith<S>::value)
       return isg ? S::pg(R.g(s), R.g0(s), W, c, 0) : S::pfr(R.f(s), W, c, 0);
     else if constexpr (L::BLK)
-      return stage_val(R.f(s)[(c >> 5) * S::kBlock + (isg ? 32 * 9 : 0) + (c & 31)]);
+      return stage_val(R.f(s)[S::sat(c, 0) + (isg ? 1 : 0)]);
     else
       return stage_val((isg ? R.g(s) : R.f(s))[c]);
   };
@@ -545,14 +555,18 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
   // destination columns' block addresses
   constexpr bool BA = L::BLK && !UROWS;
   [[maybe_unused]] uint32_t cpart[3] = {0u, 0u, 0u};
-  [[maybe_unused]] uint32_t cpart0 = 0u;  // SF16B: this lane's g_0 float, less its row's part
+  [[maybe_unused]] uint32_t cpart_f0 = 0u;  // SF16B: this lane's f_0 half, less its row's part
+  [[maybe_unused]] uint32_t cpart_g0 = 0u;  // SF16B: this lane's g_0 float, less its row's part
   [[maybe_unused]] unsigned long long blk_lim = 0;
   if constexpr (BA) {
     constexpr int B = S::kBlock;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) cpart[i] = (uint32_t)(col[i] >> 5) * B + (uint32_t)(col[i] & 31);
+    for (int i = 0; i < 3; ++i) cpart[i] = (uint32_t)(col[i] >> 5) * B + 2u * (uint32_t)(col[i] & 31);
     blk_lim = (unsigned long long)(N + 31) / 32 * B;
-    if constexpr (!std::is_same<S, SF32B>::value) cpart0 = (uint32_t)(x >> 5) * SF16B::kG0Stride + (uint32_t)(x & 31);
+    if constexpr (!std::is_same<S, SF32B>::value) {
+      cpart_f0 = (uint32_t)(x >> 5) * B + (uint32_t)(x & 31);
+      cpart_g0 = (uint32_t)(x >> 5) * SF16B::kG0Stride + (uint32_t)(x & 31);
+    }
   }
   auto push = [&](const int rowb[3], const bool sol[3][3], bool bnd, const A fs[9], const A ge[9]) {
     if constexpr (BA) {
@@ -562,8 +576,8 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       if constexpr (std::is_same<S, SF32B>::value)
         push_node_blk<MODEL>(reinterpret_cast<float*>(dst.f), blk_lim, rpart, cpart, sol, bnd, fs, ge);
       else
-        push_node_blk16<MODEL>(dst.f, dst.g0, blk_lim, rpart, cpart,
-                               (uint32_t)(rowb[1] >> 5) * SF16B::kG0Stride + cpart0, sol, bnd, fs, ge);
+        push_node_blk16<MODEL>(dst.f, dst.g0, blk_lim, rpart, cpart, rpart[1] + cpart_f0,
+                               (uint32_t)(rowb[1] >> 5) * SF16B::kG0Stride + cpart_g0, sol, bnd, fs, ge);
     } else {
       push_node_u32<MODEL, S, RAW>(dst, N32, rowb, col, sol, bnd, fs, ge);
     }

@@ -7,11 +7,11 @@ steps in every kernel variant and tile, through walls, the x-wrap and ragged las
 the reductions and the fields, for rows that start on a block boundary (nx % 32 == 0) and
 rows that do not (then a staged row is the whole blocks over its nodes, and the x-wrap
 neighbour's block is staged apart).
-  - FP32 blocks (LB_STORAGE_F32): f_i of node n at float 576 (n // 32) + 32 i + n % 32,
-    g_i 288 further.
-  - FP16 blocks (LB_STORAGE_F16DEV): 1216-byte blocks, f_i - w_i at half
-    608 (n // 32) + 32 i + n % 32, g_i (i >= 1) at half 608 (n // 32) + 288 + 32 (i - 1)
-    + n % 32, g_0 at float 304 (n // 32) + 272 + n % 32.
+  - FP32 blocks (values of LB_STORAGE_F32): f_i of node n at float
+    576 (n // 32) + 64 i + 2 (n % 32), g_i the float after it.
+  - FP16 blocks (values of LB_STORAGE_F16DEV): 1216-byte blocks, f_0 - w_0 at half
+    608 (n // 32) + n % 32, f_i - w_i (i >= 1) at half 608 (n // 32) + 32 + 64 (i - 1)
+    + 2 (n % 32), g_i the half after it, g_0 at float 304 (n // 32) + 272 + n % 32.
 One step from a random state also matches the FP64 oracle within the planar storage's
 tolerance per population (2e-6 for FP32, 1e-4 for FP16).
 """
@@ -64,12 +64,14 @@ def to_planes(state, nx, ny, prec):
     nb = (N + 31) // 32
     raw = np.frombuffer(state.tobytes(), dtype=np.uint8)
     if prec == "f32":
-        b = raw.view(np.uint32).reshape(nb, 18, 32)
-        return np.ascontiguousarray(b.transpose(1, 0, 2)).reshape(18, nb * 32)[:, :N].tobytes()
+        b = raw.view(np.uint32).reshape(nb, 9, 32, 2)          # block, i, node, (f, g)
+        return np.ascontiguousarray(b.transpose(3, 1, 0, 2)).reshape(18, nb * 32)[:, :N].tobytes()
     blk = raw.reshape(nb, 1216)
-    h = np.ascontiguousarray(blk[:, :1088]).view(np.uint16).reshape(nb, 17, 32)
+    h = np.ascontiguousarray(blk[:, :1088]).view(np.uint16).reshape(nb, 544)
+    pairs = h[:, 32:].reshape(nb, 8, 32, 2)                    # block, i - 1, node, (f, g)
+    h17 = np.concatenate([h[:, None, :32], pairs[..., 0], pairs[..., 1]], axis=1)   # f_0..f_8, g_1..g_8
     g0 = np.ascontiguousarray(blk[:, 1088:]).view(np.uint32).reshape(nb * 32)[:N]
-    planes = np.ascontiguousarray(h.transpose(1, 0, 2)).reshape(17, nb * 32)[:, :N]
+    planes = np.ascontiguousarray(h17.transpose(1, 0, 2)).reshape(17, nb * 32)[:, :N]
     return planes.tobytes() + g0.tobytes()
 
 
@@ -82,11 +84,12 @@ def assert_same_state(blk, ref, nx, ny, prec):
 
 
 def test_saved_state_follows_the_documented_layout():
-    """lb_save_state of the FP32 blocks holds f_i of node n at float 576 (n // 32) + 32 i +
-    n % 32 and g_i 288 floats further: read back against lb_get_populations.  That of the
-    FP16 blocks holds, after the same steps, the planar FP16 storage's f_i - w_i at half
-    608 (n // 32) + 32 i + n % 32, its g_i (i >= 1) at half 608 (n // 32) + 288 + 32 (i - 1)
-    + n % 32 and its FP32 g_0 at float 304 (n // 32) + 272 + n % 32."""
+    """lb_save_state of the FP32 blocks holds f_i of node n at float 576 (n // 32) + 64 i +
+    2 (n % 32) and g_i in the float after it: read back against lb_get_populations.  That
+    of the FP16 blocks holds, after the same steps, the planar FP16 storage's f_0 - w_0 at
+    half 608 (n // 32) + n % 32, its f_i - w_i (i >= 1) at half 608 (n // 32) + 32 +
+    64 (i - 1) + 2 (n % 32), its g_i in the half after that and its FP32 g_0 at float
+    304 (n // 32) + 272 + n % 32."""
     cap = GEOMS["unaligned_ragged"](W.binary_params(nu_l=0.7, nu_g=0.05))
     N = cap.nx * cap.ny
     n = np.arange(N)
@@ -96,8 +99,8 @@ def test_saved_state_follows_the_documented_layout():
     st = np.frombuffer(lat.save_state()[0].tobytes(), dtype=np.float32)
     assert st.size == 18 * 32 * ((N + 31) // 32)
     for i in range(9):
-        assert np.array_equal(st[576 * (n // 32) + 32 * i + n % 32].astype(np.float64), f[i].ravel())
-        assert np.array_equal(st[288 + 576 * (n // 32) + 32 * i + n % 32].astype(np.float64), g[i].ravel())
+        assert np.array_equal(st[576 * (n // 32) + 64 * i + 2 * (n % 32)].astype(np.float64), f[i].ravel())
+        assert np.array_equal(st[576 * (n // 32) + 64 * i + 2 * (n % 32) + 1].astype(np.float64), g[i].ravel())
 
     blk = Lattice.from_workload(cap, storage=STORAGE_F16_BLOCKED).step(37)
     ref = Lattice.from_workload(cap, storage=STORAGE_F16DEV).step(37)
@@ -109,10 +112,10 @@ def test_saved_state_follows_the_documented_layout():
     pf = np.frombuffer(pr[:18 * N], dtype=np.uint16).reshape(9, N)
     pg = np.frombuffer(pr[18 * N:34 * N], dtype=np.uint16).reshape(8, N)
     pg0 = np.frombuffer(pr[34 * N:], dtype=np.uint32)
-    for i in range(9):
-        assert np.array_equal(h[608 * (n // 32) + 32 * i + n % 32], pf[i])
+    assert np.array_equal(h[608 * (n // 32) + n % 32], pf[0])
     for i in range(1, 9):
-        assert np.array_equal(h[608 * (n // 32) + 288 + 32 * (i - 1) + n % 32], pg[i - 1])
+        assert np.array_equal(h[608 * (n // 32) + 32 + 64 * (i - 1) + 2 * (n % 32)], pf[i])
+        assert np.array_equal(h[608 * (n // 32) + 32 + 64 * (i - 1) + 2 * (n % 32) + 1], pg[i - 1])
     assert np.array_equal(s32[304 * (n // 32) + 272 + n % 32], pg0)
 
 
