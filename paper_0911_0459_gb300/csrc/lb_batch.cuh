@@ -161,8 +161,25 @@ __device__ __forceinline__ bool grid_barrier_checked(GridBarrier* b, unsigned in
 // finish the previous tile.  Every lattice's nx is a multiple of 8 (the copies'
 // 16-byte alignment).  Per-node arithmetic is the single-lattice kernels', so
 // results are bitwise those of lb_step with the staged kernel.
+// Resident CTAs per SM of the staged batch body: those of the single-lattice
+// kernel, except that the FP16 block storage keeps 80 registers per thread (its
+// batch body, which also walks the tile list, spilled at 72: 46.4 instead of
+// 43.6 GLUPS on the 256-capillary sweep with one CTA fewer per SM).
 template <class S, int BX, int NS>
-__global__ void __launch_bounds__(BX + 32, (tma_min_blocks_of<MODEL_BINARY, S, BX, NS>())) batch_tma_kernel(BatchArgs<S> a) {
+constexpr int batch_min_blocks() {
+  if constexpr (std::is_same<S, SF16B>::value) {
+    using L = TmaLayout<MODEL_BINARY, S, BX, NS>;
+    constexpr int by_smem = int(233472 / (L::BYTES + 1024));
+    constexpr int by_regs = 65536 / ((BX + 32) * 80);
+    constexpr int b = by_smem < by_regs ? by_smem : by_regs;
+    return b < 1 ? 1 : (b > 8 ? 8 : b);
+  } else {
+    return tma_min_blocks_of<MODEL_BINARY, S, BX, NS>();
+  }
+}
+
+template <class S, int BX, int NS>
+__global__ void __launch_bounds__(BX + 32, (batch_min_blocks<S, BX, NS>())) batch_tma_kernel(BatchArgs<S> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const Ring<MODEL_BINARY, S, BX, NS> R = ring_init<MODEL_BINARY, S, BX, NS>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
