@@ -374,7 +374,8 @@ def batched_vs_sequential(torch, Lattice, steps, n=256, storage=None):
         t_batch, t_seq, t_one, fluid = float(mx[0]), float(mx[1]), float(mx[2]), int(sm[3])
     cs_batch = n * steps / t_batch
     cs_seq = n * steps / t_seq
-    return {"storage": {None: "workload's", 1: "FP32 planes", 3: "FP32 moments", 6: "FP32 in 32-node blocks"}.get(storage),
+    return {"storage": {None: "workload's", 1: "FP32 planes", 3: "FP32 moments", 6: "FP32 in 32-node blocks",
+                        7: "FP16 deviations in 32-node blocks"}.get(storage),
             "speedup_vs_single_lattice_path": cs_batch / cs_seq,
             "speedup_vs_one_launch_per_run": t_one / t_batch,
             "capillary_steps_per_s": cs_batch, "sequential_capillary_steps_per_s": cs_seq,
@@ -721,6 +722,8 @@ def main():
                                                                           storage=STORAGE_F32_BLOCKED)
             secondary["batched_sweep_256_moments"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
                                                                            storage=STORAGE_MOMENTS)
+            secondary["batched_sweep_256_fp16_blocks"] = batched_vs_sequential(torch, Lattice, args.batch_steps,
+                                                                               storage=STORAGE_F16_BLOCKED)
         except Exception as ex:
             secondary["batched_error"] = repr(ex)
     if not args.no_surrogate:

@@ -231,7 +231,7 @@ def test_grid_barrier_timeout_is_reported_without_hanging(body):
     b2.close()
 
 
-@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_MOMENTS])
+@pytest.mark.parametrize("storage", [STORAGE_F32, STORAGE_F32_BLOCKED, STORAGE_MOMENTS, STORAGE_F16_BLOCKED])
 def test_full_sweep_of_256_capillaries_in_the_benchmarked_configuration(storage):
     """The seeded sweep at full size (256 capillaries, H 16..128, tubes 1024..8192,
     about 88 M fluid nodes), autotuned and run through sampled CUDA-graph launches as the
@@ -263,7 +263,9 @@ def test_full_sweep_of_256_capillaries_in_the_benchmarked_configuration(storage)
         if i == int(np.argmin(sizes)):
             orc = oracle.Oracle(caps[i]).init_default().step(b.time)
             g, o = lat.fields(), orc.fields()
-            assert max(np.abs(g[0] - o[0]).max(), np.abs(g[3] - o[3]).max()) < 1e-4
+            # FP16 deviations keep about 11 bits of each population
+            tol = 5e-4 if storage == STORAGE_F16_BLOCKED else 1e-4
+            assert max(np.abs(g[0] - o[0]).max(), np.abs(g[3] - o[3]).max()) < tol
             assert abs(lat.filled_length()["l"] - orc.filled_length()["l"]) < 0.05
         lat.close()
     b.close()
