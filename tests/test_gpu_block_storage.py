@@ -146,7 +146,8 @@ def test_one_step_random_state_matches_oracle_and_planes(geom, prec):
 @pytest.mark.parametrize("geom", sorted(GEOMS))
 def test_many_steps_bitwise_equal_to_planes(geom, prec):
     """300 steps from the default state (a meniscus moving along the tube), with the
-    l(t) reductions every 100 steps: every bit equal to the planar storage's run."""
+    l(t) reductions every 100 steps: every bit equal to the planar storage's run (state,
+    reductions, fields and exported moments)."""
     blocked, planar, _ = PREC[prec]
     cap = GEOMS[geom](W.binary_params(nu_l=0.83, nu_g=0.083))
     ref = Lattice.from_workload(cap, storage=planar)
@@ -155,6 +156,7 @@ def test_many_steps_bitwise_equal_to_planes(geom, prec):
         ref.step(100)
         ls_ref.append(ref.filled_length())
     rf = ref.fields()
+    rm = ref.moments()
     for variant, (tx, ty) in RUNS:
         lat = Lattice.from_workload(cap, storage=blocked)
         lat.set_kernel(variant)
@@ -167,6 +169,7 @@ def test_many_steps_bitwise_equal_to_planes(geom, prec):
         assert_same_state(lat, ref, cap.nx, cap.ny, prec)
         for a, b in zip(lat.fields(), rf):
             assert np.array_equal(a, b)
+        assert np.array_equal(lat.moments(), rm)
         lat.close()
 
 
