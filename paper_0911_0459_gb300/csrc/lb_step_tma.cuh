@@ -433,18 +433,18 @@ __device__ bool consume_tile(const Ring<MODEL, S, BX, NS>& R, const Geom& G, con
       }
 #pragma unroll
       for (int i = 1; i < 9; ++i) S::pfg(R.f(s), nullptr, c, i, f[i], g[i]);
-      return;
-    }
+    } else {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      if constexpr (RAW)
-        f[i] = S::pfr(R.f(s), W, c, i);
-      else
-        f[i] = S::pf(R.f(s), W, c, i, dst.r);  // the stage holds this lattice
-    }
-    if (BIN) {
+      for (int i = 0; i < 9; ++i) {
+        if constexpr (RAW)
+          f[i] = S::pfr(R.f(s), W, c, i);
+        else
+          f[i] = S::pf(R.f(s), W, c, i, dst.r);  // the stage holds this lattice
+      }
+      if (BIN) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = S::pg(R.g(s), R.g0(s), W, c, i);
+        for (int i = 0; i < 9; ++i) g[i] = S::pg(R.g(s), R.g0(s), W, c, i);
+      }
     }
   };
   // One row of the stencil window: this lane's rho/phi and its left/right
