@@ -402,8 +402,11 @@ const char *lb_batch_last_error(const lb_batch *b);
  * (LB_STORAGE_F32); for LB_STORAGE_F16DEV, f holds 9 FP16 planes of
  * f_i - w_i (w_i the rest weights of params->A, as for LB_STORAGE_F16DEV
  * above), g holds 8 FP16 planes g_1..g_8 and g0 one
- * FP32 plane of g_0.  g is ignored for the liquid-gas model, g0 unless the
- * storage is LB_STORAGE_F16DEV.  out is a device pointer to 4 doubles that
+ * FP32 plane of g_0; for the block storages (LB_STORAGE_F32_BLOCKED,
+ * LB_STORAGE_F16_BLOCKED) f holds the whole state in that storage's block
+ * layout (the bytes lb_save_state writes), at least 4-byte aligned, and g and g0
+ * are ignored.  g is ignored for the liquid-gas model, g0 unless the storage is
+ * LB_STORAGE_F16DEV.  out is a device pointer to 4 doubles that
  * receives {l_centre, l_vol, mass, phi_sum} (definitions as in
  * lb_filled_length).  nblocks is the number of blocks of the first reduction
  * pass, each of which leaves one partial sum in the scratch.

@@ -119,11 +119,17 @@ extern "C" lb_status lb_filled_length_noalloc(const lb_grid* grid, const lb_wall
   if (!geometry_ok(grid, walls)) return LB_ERR_ARG;
   const int bin = params->model == LB_MODEL_BINARY;
   if (!bin && params->model != LB_MODEL_LIQUID_GAS) return LB_ERR_ARG;
-  // population storages only (the moment storage keeps no populations); FP16 is binary only
+  // population storages only (the moment storage keeps no populations); FP16 and the
+  // 32-node blocks are binary only
+  const int blocked = params->storage == LB_STORAGE_F32_BLOCKED || params->storage == LB_STORAGE_F16_BLOCKED;
   const int st_ok = params->storage == LB_STORAGE_F64 || params->storage == LB_STORAGE_F32 ||
-                    (bin && params->storage == LB_STORAGE_F16DEV);
+                    (bin && (params->storage == LB_STORAGE_F16DEV || blocked));
   if (!st_ok) return LB_ERR_ARG;
-  if (bin && !g) return LB_ERR_ARG;
+  if (bin && !blocked && !g) return LB_ERR_ARG;
+  // the block storages' node limits (as lb_create)
+  const unsigned long long n32 = ((unsigned long long)grid->nx * grid->ny + 31) / 32 * 32;
+  if (params->storage == LB_STORAGE_F32_BLOCKED && 18ull * n32 >= (1ull << 32)) return LB_ERR_ARG;
+  if (params->storage == LB_STORAGE_F16_BLOCKED && 19ull * n32 >= (1ull << 32)) return LB_ERR_ARG;
   if (bin && params->storage == LB_STORAGE_F16DEV && !g0) return LB_ERR_ARG;
   // the liquid fraction of the liquid-gas model divides by rho_l - rho_g
   if (!bin && !(isfinite(params->rho_l) && isfinite(params->rho_g) && params->rho_l > params->rho_g))
@@ -151,6 +157,17 @@ extern "C" lb_status lb_filled_length_noalloc(const lb_grid* grid, const lb_wall
   } else if (bin && params->storage == LB_STORAGE_F16DEV) {
     // the stored deviations are taken from the bulk rest weights of this lattice's A
     lbk::Buf<lbk::SF16> B{(__half*)f, (__half*)g, g0f, lbk::rest_offsets_binary(params->A)};
+    e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else if (bin && params->storage == LB_STORAGE_F32_BLOCKED) {
+    // g_i is the element after f_i in every block
+    float* ff = static_cast<float*>(const_cast<void*>(f));
+    lbk::Buf<lbk::SF32B> B{ff, ff + lbk::SF32B::kGOff, nullptr};
+    e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
+  } else if (bin && params->storage == LB_STORAGE_F16_BLOCKED) {
+    // g_i is the half after f_i and g_0 an FP32 run at byte 1088 of every block
+    __half* fh = static_cast<__half*>(const_cast<void*>(f));
+    lbk::Buf<lbk::SF16B> B{fh, fh + lbk::SF16B::kGOff, reinterpret_cast<float*>(fh) + lbk::SF16B::kG0,
+                           lbk::rest_offsets_binary(params->A)};
     e = reduce<lbk::MODEL_BINARY>(G, B, params->rho_l, params->rho_g, thr, nblocks, partials, out, s);
   } else {
     return LB_ERR_ARG;

@@ -216,7 +216,7 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
     """lb_filled_length_noalloc checks its arguments on the host and returns LB_ERR_ARG
     before its first CUDA call (so this runs without a GPU; the device pointers below are
     never dereferenced): NULL pointers, block counts outside [1, LB_NOALLOC_MAX_BLOCKS],
-    the moment storage (it keeps no populations), the 32-node block storages (another layout), a liquid-gas lattice in FP16, a binary
+    the moment storage (it keeps no populations), a liquid-gas lattice in FP16 or in 32-node blocks, block lattices above their node limits, a binary
     call without g, an FP16 call without g0, and liquid-gas densities that are not finite
     with rho_l > rho_g (its liquid fraction divides by rho_l - rho_g)."""
     import workloads as W
@@ -243,8 +243,8 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "no blocks": call(binary, nblocks=0),
         "too many blocks": call(binary, nblocks=2049),
         "moment storage": call(binary, storage=lb.STORAGE_MOMENTS),
-        "block storage": call(binary, storage=lb.STORAGE_F32_BLOCKED),
-        "FP16 block storage": call(binary, storage=lb.STORAGE_F16_BLOCKED),
+        "liquid-gas in blocks": call(lg, storage=lb.STORAGE_F32_BLOCKED),
+        "liquid-gas in FP16 blocks": call(lg, storage=lb.STORAGE_F16_BLOCKED),
         "unknown storage": call(binary, storage=8),
         "liquid-gas in FP16": call(lg, storage=lb.STORAGE_F16DEV),
         "binary without g": call(binary, g=None),
@@ -254,6 +254,10 @@ def test_noalloc_rejects_invalid_arguments_before_any_cuda_call(libpath):
         "rho_l NaN": call(lg, rho_l=float("nan")),
         "rho_g infinite": call(lg, rho_g=float("-inf")),
         "unknown model": call(binary, model=5),
+        "FP32 blocks above 238609280 nodes": call(W.periodic_box(65536, 3641, W.binary_params()), g=None,
+                                                  storage=lb.STORAGE_F32_BLOCKED),
+        "FP16 blocks above 226050880 nodes": call(W.periodic_box(65536, 3450, W.binary_params()), g=None,
+                                                  storage=lb.STORAGE_F16_BLOCKED),
     }
     bad = {k: v for k, v in cases.items() if v != lb.LB_ERR_ARG}
     assert not bad, bad

@@ -155,3 +155,26 @@ def test_noalloc_wrapped_liquid_gas_tube_and_argument_errors():
     torch.cuda.synchronize()
     assert (sentinel.cpu().numpy() == 7.0).all()
     b.close()
+
+
+@pytest.mark.parametrize("storage_name", ["STORAGE_F32_BLOCKED", "STORAGE_F16_BLOCKED"])
+def test_noalloc_reads_the_block_layouts(storage_name):
+    """A caller-owned state in a block storage's layout: the bytes lb_save_state writes,
+    copied into a device buffer the caller owns, with g and g0 not passed (the layout
+    places them).  The same values as lb_filled_length, up to the order of the partial sums."""
+    from paper_0911_0459_gb300 import lb as L
+    storage = getattr(L, storage_name)
+    cap = W.Capillary("nb", 203, 36, 61, 130, 4, 28, 20, 10,
+                      W.binary_params(nu_l=0.5, nu_g=0.05, storage=storage), theta_deg=50.0)
+    lat = Lattice.from_workload(cap)
+    lat.step(120)
+    buf, _ = lat.save_state()
+    fd = torch.tensor(np.frombuffer(buf.tobytes(), dtype=np.uint8), device="cuda")
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    fn = noalloc_fn()
+    st = fn(C.byref(lat.grid), C.byref(lat.walls), C.byref(lat.params), C.c_void_p(fd.data_ptr()), None, None,
+            97, C.c_void_p(out.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == lbmod.LB_OK
+    torch.cuda.synchronize()
+    check(out.cpu().numpy(), lat.filled_length())
+    lat.close()
