@@ -29,9 +29,12 @@ if ROOT not in sys.path:
 
 import workloads as W  # noqa: E402
 
-from .lb import STORAGE_F16DEV, STORAGE_F32, STORAGE_F64, STORAGE_MOMENTS, Lattice  # noqa: E402
+from .lb import (STORAGE_F16_BLOCKED, STORAGE_F16DEV, STORAGE_F32, STORAGE_F32_BLOCKED,  # noqa: E402
+                 STORAGE_F32_GELIM, STORAGE_F64, STORAGE_MOMENTS, STORAGE_MOMENTS_F16, Lattice)
 
-STORAGES = {"f64": STORAGE_F64, "f32": STORAGE_F32, "f16dev": STORAGE_F16DEV, "moments": STORAGE_MOMENTS}
+STORAGES = {"f64": STORAGE_F64, "f32": STORAGE_F32, "f32b": STORAGE_F32_BLOCKED, "f16dev": STORAGE_F16DEV,
+            "f16b": STORAGE_F16_BLOCKED, "moments": STORAGE_MOMENTS, "moments_f16": STORAGE_MOMENTS_F16,
+            "gelim": STORAGE_F32_GELIM}
 
 
 def paper_700x40(storage, theta=60.0, M=0.1):
@@ -68,7 +71,9 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--config", default="binary_2048x64",
                     choices=["lg_256x32", "binary_2048x64", "binary_16384x256", "binary_crop_1024x64", "paper_700x40"])
-    ap.add_argument("--storage", choices=sorted(STORAGES), default=None)
+    ap.add_argument("--storage", choices=sorted(STORAGES), default=None,
+                    help="state storage (default f64 for lg_256x32, f32 otherwise; f32b holds the same "
+                         "values in 32-node blocks, the same bits and faster)")
     ap.add_argument("--theta", type=float, default=None, help="equilibrium contact angle (binary), degrees")
     ap.add_argument("--mobility", type=float, default=None, help="mobility M (binary)")
     ap.add_argument("--steps", type=int, default=2000, help="run until this step count")
